@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of the hybrid LU-QR solver on one or more GB300 GPUs.
+
+Workload (default): N = 32768, nb = 256, A = U diag(s) V^T with s geometric from 1 to
+1/kappa (kappa = 1e5) and U, V random orthogonal, b = A * ones; Max criterion,
+alpha = 100, binary TT elimination tree.  One step = one solve to a normwise backward
+error <= 1e-13: FP32 hybrid LU-QR factorization plus FP64 iterative refinement, all
+in the library's CUDA kernels.  The metric is the solve time and the normalized
+GFLOP/s (2N^3/3 per solve), next to the plain FP64 GPU solve of the same system.
+
+One JSON line is printed by rank 0.  Under torchrun every rank solves its own
+system (replicas, weak scaling); value aggregates all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "N=32768 solve time & GFLOP/s (2N^3/3) vs plain FP64 GPU at equal backward error"
+FP32_FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FFMA lanes x 2 x max clock
+FP64_DFMA_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # SMs x DFMA/clk x 2 x max clock
+
+
+def parse(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="luqr", choices=["luqr", "reference"])
+    p.add_argument("--N", type=int, default=32768)
+    p.add_argument("--nb", type=int, default=256)
+    p.add_argument("--kappa", type=float, default=1e5)
+    p.add_argument("--criterion", default="max")
+    p.add_argument("--alpha", type=float, default=100.0)
+    p.add_argument("--tree", default="binary_tt")
+    p.add_argument("--precision", default="fp32")
+    p.add_argument("--tol", type=float, default=1e-13)
+    p.add_argument("--fp64-baseline", type=int, default=1, help="also time one plain FP64 solve")
+    p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--cpu-N", type=int, default=2048, help="oracle sample size")
+    p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--seed", type=int, default=0)
+    return p.parse_args(argv)
+
+
+# ------------------------------------------------------------------ flop model
+def step_kernel_flops(dec, n, nb, tree, ncols_extra, replay=False):
+    """Algorithmic flops per kernel class for one factorization (replay=False) or one
+    second-pass solve on a single right-hand side (replay=True).  Per Table I:
+    GEMM 2 nb^3 per tile pair, UNMQR 2 nb^3 per tile, TSMQR 4 nb^3, TTMQR 2 nb^3
+    (triangular V), GEQRT 4/3 nb^3, TSQRT 2 nb^3, TTQRT 2/3 nb^3, TRSM nb^3."""
+    out = {}
+
+    def add(k, v):
+        out[k] = out.get(k, 0.0) + v
+
+    nb3 = float(nb) ** 3
+    for k in range(n):
+        m = n - 1 - k
+        cols = 1.0 if replay else m * nb + ncols_extra
+        if dec[k] == 1:
+            if not replay:
+                add("k_trsm", m * nb3)
+            add("k_swptrsm", cols * nb * nb)
+            add("k_gemm_update", 2.0 * m * nb * cols * nb)
+        else:
+            if tree == "binary_tt":
+                if not replay:
+                    add("k_geqrt", (m + 1) * 4.0 / 3.0 * nb3)
+                    add("k_ttqrt", m * 2.0 / 3.0 * nb3)
+                add("k_unmqr", (m + 1) * 2.0 * nb * nb * cols)
+                add("k_ttmqr", m * 2.0 * nb * nb * cols)
+            else:   # flat TS (grouped counted as flat for the model)
+                if not replay:
+                    add("k_geqrt", 4.0 / 3.0 * nb3)
+                    add("k_tsqrt", m * 2.0 * nb3)
+                add("k_unmqr", 2.0 * nb * nb * cols)
+                add("k_tsmqr", m * 4.0 * nb * nb * cols)
+        if not replay:
+            add("k_getrf", 2.0 / 3.0 * nb3)
+    return out
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def cpu_worker(args):
+    """Times the CPU oracle (as it stands) on a bounded sample of the same workload:
+    the full FP32-factorization + FP64-refinement solve at N = cpu_N."""
+    import numpy as np
+    from oracle import luqr_oracle as O
+    from paper_1401_5522_gb300 import inputs
+    N, nb = args.cpu_N, args.nb
+    A = inputs.conditioned(N, args.kappa, seed=args.seed).numpy()
+    b = A @ np.ones(N)
+    crit = {"max": O.CRIT_MAX, "sum": O.CRIT_SUM, "mumps": O.CRIT_MUMPS}[args.criterion]
+    tree = {"flat_ts": O.TREE_FLAT_TS, "binary_tt": O.TREE_BINARY_TT, "grouped": O.TREE_GROUPED}[args.tree]
+    dt = np.float32 if args.precision == "fp32" else np.float64
+    t0 = time.perf_counter()
+    f = O.factor(A, None, nb, crit, args.alpha, tree=tree, dtype=dt)
+    x = O.replay_solve(f, b).ravel()
+    eta = O.backward_error(A, x, b)
+    its = 1
+    while eta > args.tol and its < 30:
+        r = b - A @ x
+        x = x + O.replay_solve(f, r).ravel()
+        eta = O.backward_error(A, x, b)
+        its += 1
+    t = time.perf_counter() - t0
+    return {"value": O.normalized_gflops(N, t), "seconds": t, "eta": eta, "iters": its, "N": N}
+
+
+def run_cpu_baseline(args):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--cpu-N", str(args.cpu_N),
+           "--nb", str(args.nb), "--kappa", str(args.kappa), "--criterion", args.criterion,
+           "--alpha", str(args.alpha), "--tree", args.tree, "--precision", args.precision,
+           "--tol", str(args.tol), "--seed", str(args.seed)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        return {"error": r.stderr[-400:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_dict(res, args):
+    return {"value": res.get("value"), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": (f"full oracle solve (FP32 hybrid factorization + FP64 refinement to "
+                       f"eta <= {args.tol:g}) of the same recipe at N={res.get('N')}, nb={args.nb}; "
+                       f"{res.get('seconds', 0):.1f} s, {res.get('iters')} solves, "
+                       f"eta={res.get('eta', float('nan')):.2e}; GFLOP/s = (2/3)N^3/t"),
+            }
+
+
+# ------------------------------------------------------------------ main GPU leg
+def main():
+    args = parse()
+    if args.cpu_worker:
+        print(json.dumps(cpu_worker(args)))
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    config = {"workload": (f"hybrid LU-QR solve, N={args.N}, nb={args.nb}, A=U diag(s) V^T "
+                           f"kappa={args.kappa:g}, b=A*1, {args.criterion} alpha={args.alpha:g}, "
+                           f"{args.tree} tree, {args.precision} factorization + FP64 refinement to "
+                           f"eta<={args.tol:g}"),
+              "N": args.N, "nb": args.nb, "kappa": args.kappa, "criterion": args.criterion,
+              "alpha": args.alpha, "tree": args.tree, "factor_precision": args.precision,
+              "refinement": "fp64", "parallelism": f"replicas x{args.gpus}",
+              "l2": "inputs larger than L2 (A is N^2 float64)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        res = run_cpu_baseline(args)
+        line = {"metric": METRIC, "impl": "reference", "value": res.get("value"), "unit": "GFLOP/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64", "data": "synthetic", "config": config,
+                "cpu_baseline": cpu_baseline_dict(res, args),
+                "e2e": {"value": res.get("value"), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1401_5522_gb300 import build as B
+    B.build()
+    from paper_1401_5522_gb300 import inputs, luqr
+
+    N, nb = args.N, args.nb
+    A = inputs.conditioned(N, args.kappa, seed=args.seed + rank, device="cuda")
+    b = (A @ torch.ones(N, 1, dtype=torch.float64, device="cuda")).reshape(-1).contiguous()
+    x = torch.zeros(N, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    info = {}
+
+    def one_solve():
+        h = luqr.factor(A, nb, args.criterion, args.alpha, tree=args.tree, precision=args.precision)
+        st, its, eta = h.refine(A, b, x, tol=args.tol, max_iter=30)
+        dec, _ = h.decisions()
+        h.close()
+        info["iters"] = its
+        info["eta"] = eta
+        info["status"] = st
+        info["dec"] = dec
+        return st
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        one_solve()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    luqr.profile(True, True)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    statuses, iters = [], []
+    for _ in range(args.steps):
+        statuses.append(one_solve())
+        iters.append(info["iters"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = luqr.profile_read()
+    luqr.profile(False, True)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    flops = (2.0 / 3.0) * float(N) ** 3
+    value = flops * world / (ms / 1e3) / 1e9
+    eta_gpu = info["eta"]
+    dec = info["dec"]
+    n = len(dec)
+
+    # ---------------- roofline of the dominant kernel (CUDA events inside the timed region)
+    fac = step_kernel_flops(dec, n, nb, args.tree, 0, replay=False)
+    rep = step_kernel_flops(dec, n, nb, args.tree, 0, replay=True)
+    total_alg = {k: args.steps * fac.get(k, 0.0) + sum(iters) * rep.get(k, 0.0)
+                 for k in set(fac) | set(rep)}
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roofline = None
+    if dom is not None:
+        name, (launches, tot_ms) = dom
+        alg = total_alg.get(name)
+        peak = FP32_FFMA_PEAK_TFLOPS if args.precision == "fp32" else FP64_DFMA_PEAK_TFLOPS
+        if alg:
+            achieved = alg / (tot_ms / 1e3) / 1e12
+            roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
+                        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                        "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+                                        if args.precision == "fp32" else
+                                        "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"),
+                        "launches": launches, "avg_launch_ms": tot_ms / launches,
+                        "share_of_step": tot_ms / (ms * args.steps)}
+    gpu_launches = int(sum(v[0] for v in prof.values())) if prof else 0
+    kernel_table = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in
+                    sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    # ---------------- end to end through the C interface with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        hA = torch.empty((N, N), dtype=torch.float64, pin_memory=True).t()
+        hA.copy_(A)
+        hb = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        hb.copy_(b)
+        hx = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        dA2 = torch.empty_like(A)
+        db2 = torch.empty_like(b)
+        dx2 = torch.empty_like(x)
+        torch.cuda.synchronize()
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.e2e_steps):
+            dA2.copy_(hA, non_blocking=True)
+            db2.copy_(hb, non_blocking=True)
+            h = luqr.factor(dA2, nb, args.criterion, args.alpha, tree=args.tree,
+                            precision=args.precision)
+            h.refine(dA2, db2, dx2, tol=args.tol, max_iter=30)
+            h.close()
+            hx.copy_(dx2, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = f0.elapsed_time(f1) / args.e2e_steps
+        e2e = {"value": flops * world / (e2e_ms / 1e3) / 1e9, "unit": "GFLOP/s",
+               "ms_per_step": e2e_ms, "h2d_bytes_per_step": 8 * N * N + 8 * N,
+               "d2h_bytes_per_step": 8 * N}
+        del hA, dA2
+
+    # ---------------- plain FP64 GPU solve (the denominator), one timed solve
+    plain = None
+    if args.fp64_baseline:
+        small = inputs.conditioned(1024, args.kappa, seed=1, device="cuda")
+        sb = (small @ torch.ones(1024, 1, dtype=torch.float64, device="cuda")).reshape(-1).contiguous()
+        luqr.factor(small, nb, args.criterion, args.alpha, b=sb, tree=args.tree,
+                    precision="fp64").close()                    # loads the FP64 kernels
+        bb = b.clone()
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        h = luqr.factor(A, nb, args.criterion, args.alpha, b=bb, tree=args.tree, precision="fp64")
+        g1.record(stream)
+        torch.cuda.synchronize()
+        st64, _, _ = h.info()
+        dec64, _ = h.decisions()
+        h.close()
+        p_ms = g0.elapsed_time(g1)
+        r = b - A @ bb
+        eta64 = float(r.abs().max() / (A.abs().sum(dim=1).max() * bb.abs().max() + b.abs().max()))
+        plain = {"ms_per_solve": p_ms, "gflops": flops / (p_ms / 1e3) / 1e9, "eta": eta64,
+                 "status": st64, "decisions_equal_to_fp32_path": bool(np.array_equal(dec64, dec)),
+                 "speedup_of_headline": p_ms / ms}
+
+    if rank != 0:
+        return
+    cpu = run_cpu_baseline(args)
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic", "config": config,
+            "eta": eta_gpu, "ir_iters": iters, "status": statuses,
+            "lu_fraction": float(np.mean(dec == 1)),
+            "plain_fp64": plain, "roofline": roofline, "gpu_launches": gpu_launches,
+            "kernels": kernel_table, "e2e": e2e, "clocks": clk,
+            "cpu_baseline": cpu_baseline_dict(cpu, args)}
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * luqr.h - C interface of the GB300 hybrid LU-QR dense solver.
+ *
+ * Method: Faverge, Herrmann, Langou, Lowery, Robert, Dongarra, "Designing LU-QR
+ * hybrid solvers for performance and stability" (arXiv 1401.5522).  A square
+ * matrix of order N is split into n = ceil(N/nb) tile rows/columns of nb x nb
+ * tiles.  At every step k (Alg. 1) the diagonal tile is LU-factored with partial
+ * pivoting inside the tile, a robustness criterion (Sec. III: Eq. 2 Max, Eq. 3 Sum,
+ * Eq. 4 MUMPS) decides between an LU step (Alg. 2, variant A1: GETRF, TRSM,
+ * SWPTRSM, GEMM) and a QR step (Alg. 3 with the TS/TT kernels of Alg. 4), and the
+ * transformations are applied to [A | b] before one N x N triangular solve
+ * (Sec. II-D).
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices are column-major FP64 device arrays with a leading dimension.
+ *  - Device pointers are caller-owned; the library never frees them.  A handle
+ *    owns all of its own device workspace and releases it in luqr_destroy.
+ *  - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as void*;
+ *    NULL = legacy default stream).  Entry points that return device results to
+ *    the host (luqr_decisions, luqr_info, luqr_sync, luqr_refine) synchronise
+ *    that stream.
+ *  - Every call returns an luqr_status code; nothing is thrown across the ABI.
+ *    Errors found on the device (singular pivot, non-finite panel) are recorded
+ *    in the handle and reported by the next synchronising call.
+ *  - N not a multiple of nb is handled by padding the last tile with an identity
+ *    block (Sec. II-D, "No restriction on N"); results equal those of native
+ *    ragged tiles.
+ *  - nb must be a multiple of 32 with 32 <= nb <= 512.
+ *  - Distinct handles may be used from distinct host threads.
+ */
+#ifndef LUQR_H
+#define LUQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LUQR_OK = 0,
+  LUQR_ERR_INVALID = -1,       /* bad argument (N, nb, lda, alpha, criterion, pointer) */
+  LUQR_ERR_NOMEM = -2,         /* device allocation failed */
+  LUQR_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+  LUQR_ERR_SINGULAR = -4,      /* exact zero pivot where an LU step/back solve needs one */
+  LUQR_ERR_NONFINITE = -5,     /* NaN or Inf met in a panel */
+  LUQR_ERR_TIMEOUT = -6,       /* a bounded device wait expired */
+  LUQR_ERR_NOT_CONVERGED = -7  /* iterative refinement did not reach the tolerance */
+} luqr_status;
+
+/* Per-step decision codes returned by luqr_decisions. */
+enum { LUQR_DEC_QR = 0, LUQR_DEC_LU = 1, LUQR_DEC_ABORTED = 2 };
+
+/* Robustness criteria (Sec. III).  FORCE_LU is the alpha = infinity limit and
+ * FORCE_QR the alpha = 0 limit of Sec. V-B. */
+enum { LUQR_MAX = 0, LUQR_SUM = 1, LUQR_MUMPS = 2, LUQR_FORCE_LU = 3, LUQR_FORCE_QR = 4 };
+
+/* QR elimination trees (Alg. 3: the eliminator of each tile is free). */
+enum {
+  LUQR_TREE_FLAT_TS = 0,   /* eliminator(i,k) = k, TS kernels (Alg. 4a) */
+  LUQR_TREE_BINARY_TT = 1, /* binary reduction with TT kernels (Alg. 4b) */
+  LUQR_TREE_GROUPED = 2    /* flat TS inside groups of `group` tiles, binary TT across heads */
+};
+
+/* Arithmetic of the factorization.  The criterion's norms and comparison are
+ * always evaluated in FP64. */
+enum {
+  LUQR_PREC_FP64 = 0,      /* FP64 tiles and kernels */
+  LUQR_PREC_FP32 = 1       /* FP32 tiles and kernels (use luqr_refine for FP64 accuracy) */
+};
+
+/* Options; a zero-initialised struct selects the defaults. */
+typedef struct luqr_options {
+  int tree;                /* LUQR_TREE_*, default flat TS */
+  int group;               /* group size for LUQR_TREE_GROUPED (default 4) */
+  int precision;           /* LUQR_PREC_* */
+  int mumps_mode;          /* 0: est(j) = away(j)*pivot(j)/local(j); 1: cumulative product */
+  const uint8_t* forced;   /* optional HOST array of n decisions replacing the criterion */
+  const int* inject;       /* optional HOST list of steps whose tile row of [A^(k)|b^(k)] is
+                              scaled by 2^-27 before the criterion (run-time injection) */
+  int n_inject;
+  int reserved[9];
+} luqr_options;
+
+typedef struct luqr_handle* luqr_handle_t;
+
+/*
+ * luqr_factor - hybrid LU-QR factorization (Alg. 1-4, Eq. 1-4).
+ *   dA        device, column-major N x N FP64, leading dimension lda >= N; read only.
+ *   db        device FP64 vector of length N or NULL.  When given, b is carried as an
+ *             augmented column through every step (Sec. II-D) and, after the N x N
+ *             triangular solve, overwritten in place with the solution x.
+ *   criterion LUQR_MAX / SUM / MUMPS / FORCE_LU / FORCE_QR; alpha >= 0 (may be +inf).
+ *             alpha = 0 selects QR at every step.
+ *   opt       may be NULL.
+ *   stream    CUDA stream; all work is enqueued, nothing is synchronised.
+ *   out       receives the new handle (also on device-side errors, which surface later).
+ * Returns LUQR_ERR_INVALID for N < 1, nb not in {32,64,...,512}, lda < N, dA NULL,
+ * alpha < 0 or NaN, unknown criterion/tree/precision; LUQR_ERR_NOMEM or
+ * LUQR_ERR_CUDA when the workspace cannot be set up (then *out is NULL).
+ */
+int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb,
+                int criterion, double alpha, const luqr_options* opt, void* stream,
+                luqr_handle_t* out);
+
+/*
+ * luqr_solve - second-pass solve (Sec. II-D): replays every stored LU/QR step on
+ * nrhs right-hand sides and back-substitutes.  db: device, column-major N x nrhs
+ * FP64 (ldb >= N), overwritten with X.  Work is enqueued on `stream`.
+ */
+int luqr_solve(luqr_handle_t h, double* db, int nrhs, int64_t ldb, void* stream);
+
+/*
+ * luqr_refine - iterative refinement on the original matrix: x <- x + solve(b - A x)
+ * with the residual, the update and the backward error in FP64.
+ *   dA, lda   the matrix that was factored (device, FP64, read only).
+ *   db        device right-hand side (length N, read only).
+ *   dx        device output solution (length N).
+ *   tol       target normwise backward error ||b-Ax||_inf/(||A||_inf||x||_inf+||b||_inf).
+ *   max_iter  maximum number of corrections.
+ *   iters     (host, nullable) corrections applied; eta (host, nullable) final error.
+ * Synchronises the stream once per iteration.  Returns LUQR_ERR_NOT_CONVERGED when
+ * tol was not reached (dx still holds the best iterate).
+ */
+int luqr_refine(luqr_handle_t h, const double* dA, int64_t lda, const double* db,
+                double* dx, double tol, int max_iter, int* iters, double* eta,
+                void* stream);
+
+/*
+ * luqr_decisions - copies the per-step decisions (LUQR_DEC_*) and margins
+ * log2(lhs/rhs) of the criterion (minimum over columns for MUMPS; +-inf for forced
+ * steps) to HOST arrays of length n = ceil(N/nb).  margin may be NULL.  *n_out = n.
+ * Synchronises the factorization stream; returns the device status.
+ */
+int luqr_decisions(luqr_handle_t h, uint8_t* dec, double* margin, int* n_out);
+
+/*
+ * luqr_step_stats - copies per-step criterion quantities to HOST arrays of length n:
+ * lhs = alpha/||A_kk^-1||_1 and rhs = max or sum of ||A_ik||_1 (Max/Sum; NaN otherwise).
+ * Either pointer may be NULL.  Synchronises.
+ */
+int luqr_step_stats(luqr_handle_t h, double* lhs, double* rhs);
+
+/* luqr_factor_data - copies the transformed padded workspace (column-major, n*nb rows,
+ * n*nb columns, converted to FP64) to a HOST array with leading dimension ld >= n*nb.
+ * Synchronises.  Intended for tests and inspection. */
+int luqr_factor_data(luqr_handle_t h, double* host, int64_t ld);
+
+/* luqr_sync - waits for the handle's work and returns its device status. */
+int luqr_sync(luqr_handle_t h);
+
+/* luqr_info - device status of the handle and where it was raised (0-based step and
+ * row; -1 when not applicable).  Synchronises. */
+int luqr_info(luqr_handle_t h, int* status, int* step, int* row);
+
+/* luqr_dims - n (tiles), padded order and the handle's precision. */
+int luqr_dims(luqr_handle_t h, int* n, int64_t* npad, int* precision);
+
+/* luqr_destroy - frees the handle's workspace (synchronises its stream first).
+ * NULL is accepted. */
+void luqr_destroy(luqr_handle_t h);
+
+/*
+ * luqr_profile - launch profiler for benchmarks.  With enable != 0 every kernel launch
+ * of the library is bracketed by CUDA events recorded on the launch's own stream and
+ * attributed to the kernel's name; enable == 0 stops recording.  reset != 0 clears
+ * the table.  Process-wide; not meant for concurrent use from several host threads.
+ */
+int luqr_profile(int enable, int reset);
+
+/*
+ * luqr_profile_read - waits for the recorded events, then writes up to cap entries
+ * (host arrays): kernel names (static strings owned by the library), launch counts
+ * and total device milliseconds.  Any array may be NULL.  Returns the entry count.
+ */
+int luqr_profile_read(const char** names, int64_t* launches, double* total_ms, int cap);
+
+/* luqr_status_string - static text for a status code. */
+const char* luqr_status_string(int status);
+
+/* luqr_version - library version string. */
+const char* luqr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LUQR_H */

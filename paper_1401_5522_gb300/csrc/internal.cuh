@@ -1,0 +1,158 @@
+// Internal declarations of the hybrid LU-QR library (not part of the C interface).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+namespace luqr {
+
+constexpr int IB = 32;              // inner block of the Householder kernels (T is IB x IB per block)
+constexpr int NT = 256;             // threads of the tile kernels
+constexpr int SMEM_MAX = 232448;    // opt-in dynamic shared memory per block (227 KB)
+
+enum : uint8_t { DEC_QR = 0, DEC_LU = 1, DEC_ABORT = 2 };
+
+// Device status word of a handle: {code, step, row, nonfinite, zero_row, ...}
+enum { ST_CODE = 0, ST_STEP = 1, ST_ROW = 2, ST_NONFINITE = 3, ST_ZERO_ROW = 4, ST_WORDS = 8 };
+
+// A column-major matrix view.
+template <typename T>
+struct Mat {
+  T* p;
+  int64_t ld;
+  __host__ __device__ T& operator()(int64_t r, int64_t c) const { return p[r + c * ld]; }
+};
+
+// Rows [i0 + t*istride, +nb) for t < count; eliminator rows i - eoff.
+struct TileList {
+  int i0, istride, count, eoff;
+};
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v);
+template <>
+__device__ __forceinline__ double warp_sum<double>(double v) { return warp_sum_d(v); }
+template <>
+__device__ __forceinline__ float warp_sum<float>(float v) { return warp_sum_f(v); }
+
+__device__ __forceinline__ double warp_max_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Sum over the whole block (blockDim.x multiple of 32); result valid in every thread.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red /* >= 32 */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum<T>(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  T s = (T)0;
+  for (int w = 0; w < nw; ++w) s += red[w];
+  return s;
+}
+
+// ---------------------------------------------------------------- launch profiler
+void prof_begin(const char* name, cudaStream_t s);
+void prof_end(cudaStream_t s);
+struct ProfScope {
+  cudaStream_t s;
+  ProfScope(const char* name, cudaStream_t st) : s(st) { prof_begin(name, st); }
+  ~ProfScope() { prof_end(s); }
+};
+
+// ---------------------------------------------------------------- launchers
+template <typename T>
+void launch_pack(const double* A, int64_t lda, const double* b, int64_t N, int64_t Npad,
+                 int64_t Wc, T* W, int64_t ldw, cudaStream_t s);
+template <typename T>
+void launch_scale_rows(T* W, int64_t ldw, int64_t row0, int rows, int64_t col0, int64_t col1,
+                       double scale, cudaStream_t s);
+template <typename T>
+void launch_panel_stats(const T* W, int64_t ldw, int k, int n, int nb, double* norms_k,
+                        unsigned long long* local, unsigned long long* away, int* status,
+                        cudaStream_t s);
+template <typename T>
+void launch_getrf(const T* W, int64_t ldw, int k, int nb, T* S, int* piv_s, int* status,
+                  cudaStream_t s);
+template <typename T>
+void launch_invnorm(const T* S, int nb, const int* piv_s, double* colsum, const int* status,
+                    cudaStream_t s);
+
+struct DecideArgs {
+  int k, n, nb, criterion, mumps_mode;
+  double alpha;
+  const double* norms_k;             // indexed by tile row i
+  const double* colsum;              // nb column sums of |A_kk^-1|
+  const unsigned long long* local;   // nb column maxima of |A_kk| (double bits)
+  const unsigned long long* away;    // nb column maxima of |A_ik|, i > k (double bits)
+  const uint8_t* forced;             // device, may be null
+  uint8_t* dec;
+  double* margin;
+  double* lhs;
+  double* rhs;
+  int* status;
+};
+template <typename T>
+void launch_decide(const DecideArgs& a, const T* S, cudaStream_t s);
+
+template <typename T>
+void launch_lu_commit(T* W, int64_t ldw, int k, int nb, const T* S, const int* piv_s,
+                      int* piv_k, const uint8_t* dec, cudaStream_t s);
+// C rows [row0, row0+nb), columns [c0, c1) <- L^-1 P C with L, P of the LU-factored tile LU.
+template <typename T>
+void launch_swptrsm(Mat<const T> LU, int nb, const int* piv_k, Mat<T> C, int64_t row0, int64_t c0,
+                    int64_t c1, const uint8_t* dec, int k, cudaStream_t s);
+// X rows [r0, r1), columns [xc, xc+nb) <- X U^-1.
+template <typename T>
+void launch_trsm(Mat<const T> LU, int nb, Mat<T> X, int64_t r0, int64_t r1, int64_t xc,
+                 const uint8_t* dec, int k, cudaStream_t s);
+// C[r0:r1, c0:c1] -= A[r0:r1, 0:K] * B[0:K, c0:c1]   (A, B given at their (r0,0)/(0,c0) origins)
+template <typename T>
+void launch_gemm_update(Mat<const T> A, Mat<const T> B, Mat<T> C, int64_t M, int64_t Ncols, int K,
+                        const uint8_t* dec, int k, uint8_t want, cudaStream_t s);
+
+// QR kernels; the V tiles live in the factored panel column kc of F.
+template <typename T>
+void launch_geqrt(Mat<T> F, int k, int nb, TileList tl, T* Tk, int n, const uint8_t* dec,
+                  cudaStream_t s);
+template <typename T>
+void launch_unmqr(Mat<const T> F, int k, int nb, TileList tl, const T* Tk, int n, Mat<T> C,
+                  int64_t c0, int64_t c1, const uint8_t* dec, cudaStream_t s);
+template <typename T>
+void launch_pair_qrt(Mat<T> F, int k, int nb, TileList tl, bool tri, T* Tk, int n,
+                     const uint8_t* dec, cudaStream_t s);
+template <typename T>
+void launch_pair_apply(Mat<const T> F, int k, int nb, TileList tl, bool tri, const T* Tk, int n,
+                       Mat<T> C, int64_t c0, int64_t c1, const uint8_t* dec, cudaStream_t s);
+
+// Solves and refinement helpers.
+template <typename T>
+void launch_trsv_diag(Mat<const T> U, int k, int nb, Mat<T> X, int nrhs, int* status,
+                      cudaStream_t s);
+template <typename T>
+void launch_trsv_update(Mat<const T> U, int k, int nb, Mat<T> X, int nrhs, cudaStream_t s);
+template <typename T>
+void launch_convert_in(const double* src, int64_t lds, int64_t N, int64_t Npad, int nrhs,
+                       const double* scale, T* dst, int64_t ldd, cudaStream_t s);
+template <typename T>
+void launch_convert_out(const T* src, int64_t lds, int64_t N, int nrhs, double* dst, int64_t ldd,
+                        cudaStream_t s);
+void launch_residual(const double* A, int64_t lda, int64_t N, const double* x, const double* b,
+                     double* r, double* partial, int nchunk, cudaStream_t s);
+void launch_row_abs_sum_max(const double* A, int64_t lda, int64_t N, double* partial, int nchunk,
+                            double* out, cudaStream_t s);
+void launch_vec_absmax(const double* v, int64_t N, double* out, cudaStream_t s);
+template <typename T>
+void launch_axpy_update(double* x, const T* d, int64_t N, const double* scale, cudaStream_t s);
+
+}  // namespace luqr

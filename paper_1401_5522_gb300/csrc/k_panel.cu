@@ -1,0 +1,352 @@
+// Panel-side kernels of one step of the hybrid LU-QR factorization:
+// pack/pad, run-time injection, criterion inputs (Sec. III-D), the diagonal GETRF on
+// a scratch copy (Alg. 1 "Factor"), ||A_kk^-1||_1 from the L and U factors, and the
+// robustness test (Eq. 2, 3, 4) that writes the step's decision to device memory.
+#include "internal.cuh"
+
+namespace luqr {
+
+// ---------------------------------------------------------------- pack / pad
+// W (Npad x Wc, column-major) <- [A, b] padded with an identity block (Sec. II-D).
+template <typename T>
+__global__ void k_pack(const double* __restrict__ A, int64_t lda, const double* __restrict__ b,
+                       int64_t N, int64_t Npad, int64_t Wc, T* __restrict__ W, int64_t ldw) {
+  for (int64_t c = blockIdx.y; c < Wc; c += gridDim.y)
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < Npad;
+         r += (int64_t)gridDim.x * blockDim.x) {
+      double v;
+      if (c < Npad)
+        v = (r < N && c < N) ? A[r + c * lda] : (r == c ? 1.0 : 0.0);
+      else
+        v = (b != nullptr && r < N) ? b[r] : 0.0;
+      W[r + c * ldw] = (T)v;
+    }
+}
+
+template <typename T>
+void launch_pack(const double* A, int64_t lda, const double* b, int64_t N, int64_t Npad,
+                 int64_t Wc, T* W, int64_t ldw, cudaStream_t s) {
+  int bx = (int)((Npad + 255) / 256);
+  if (bx > 64) bx = 64;
+  dim3 grid(bx, (unsigned)(Wc < 65535 ? Wc : 65535));
+  {
+    ProfScope ps_("k_pack", s);
+    k_pack<T><<<grid, 256, 0, s>>>(A, lda, b, N, Npad, Wc, W, ldw);
+  }
+}
+
+// ---------------------------------------------------------------- injection
+template <typename T>
+__global__ void k_scale_rows(T* W, int64_t ldw, int64_t row0, int rows, int64_t col0,
+                             int64_t col1, double scale) {
+  for (int64_t c = col0 + blockIdx.x; c < col1; c += gridDim.x)
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+      T* p = &W[row0 + r + c * ldw];
+      *p = (T)((double)*p * scale);
+    }
+}
+
+template <typename T>
+void launch_scale_rows(T* W, int64_t ldw, int64_t row0, int rows, int64_t col0, int64_t col1,
+                       double scale, cudaStream_t s) {
+  int64_t nc = col1 - col0;
+  if (nc <= 0) return;
+  int g = (int)(nc < 4096 ? nc : 4096);
+  {
+    ProfScope ps_("k_scale_rows", s);
+    k_scale_rows<T><<<g, 256, 0, s>>>(W, ldw, row0, rows, col0, col1, scale);
+  }
+}
+
+// ---------------------------------------------------------------- criterion inputs
+// Block i-k: ||A_ik||_1 (max column abs sum, FP64 accumulation) and the column maxima
+// used by the MUMPS criterion (local for i = k, away for i > k).  Non-finite entries
+// raise the status' nonfinite flag.
+template <typename T>
+__global__ void k_panel_stats(const T* __restrict__ W, int64_t ldw, int k, int nb,
+                              double* __restrict__ norms_k, unsigned long long* __restrict__ local,
+                              unsigned long long* __restrict__ away, int* status) {
+  const int i = k + blockIdx.x;
+  const T* tile = W + (int64_t)i * nb + (int64_t)k * nb * ldw;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double best = 0.0;
+  bool bad = false;
+  for (int c = warp; c < nb; c += nw) {
+    const T* col = tile + (int64_t)c * ldw;
+    double sum = 0.0, mx = 0.0;
+    for (int r = lane; r < nb; r += 32) {
+      double v = fabs((double)col[r]);
+      if (!isfinite(v)) bad = true;
+      sum += v;
+      mx = fmax(mx, v);
+    }
+    sum = warp_sum_d(sum);
+    mx = warp_max_d(mx);
+    if (lane == 0) {
+      best = fmax(best, sum);
+      unsigned long long bits = (unsigned long long)__double_as_longlong(mx);
+      if (i == k)
+        local[c] = bits;
+      else
+        atomicMax(&away[c], bits);   // non-negative doubles order like their bit patterns
+    }
+  }
+  if (bad) atomicOr(&status[ST_NONFINITE], 1);
+  __shared__ double red[32];
+  if (lane == 0) red[warp] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < nw; ++w) m = fmax(m, red[w]);
+    norms_k[i] = m;
+  }
+}
+
+template <typename T>
+void launch_panel_stats(const T* W, int64_t ldw, int k, int n, int nb, double* norms_k,
+                        unsigned long long* local, unsigned long long* away, int* status,
+                        cudaStream_t s) {
+  cudaMemsetAsync(away, 0, sizeof(unsigned long long) * nb, s);
+  {
+    ProfScope ps_("k_panel_stats", s);
+    k_panel_stats<T><<<n - k, 256, 0, s>>>(W, ldw, k, nb, norms_k, local, away, status);
+  }
+}
+
+// ---------------------------------------------------------------- diagonal GETRF
+// S <- A_kk, then P S = L U in place with partial pivoting inside the tile: the pivot
+// of column r is the first row of maximal |S[r:, r]|.  An exact zero pivot leaves the
+// column unscaled and is recorded (first one) in status[ST_ZERO_ROW].
+template <typename T>
+__global__ void __launch_bounds__(1024) k_getrf(const T* __restrict__ W, int64_t ldw, int k,
+                                                int nb, T* __restrict__ S, int* __restrict__ piv,
+                                                int* status) {
+  const T* A = W + (int64_t)k * nb + (int64_t)k * nb * ldw;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int idx = tid; idx < nb * nb; idx += nt) {
+    int r = idx % nb, c = idx / nb;
+    S[idx] = A[r + (int64_t)c * ldw];
+  }
+  __shared__ double s_val[32];
+  __shared__ int s_idx[32];
+  __shared__ int s_piv;
+  __shared__ int s_zero;
+  if (tid == 0) s_zero = -1;
+  __syncthreads();
+  for (int r = 0; r < nb; ++r) {
+    double bv = -1.0;
+    int bi = nb;
+    for (int rr = r + tid; rr < nb; rr += nt) {
+      double v = fabs((double)S[rr + r * nb]);
+      if (v > bv) { bv = v; bi = rr; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { s_val[warp] = bv; s_idx[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+      bv = lane < nw ? s_val[lane] : -1.0;
+      bi = lane < nw ? s_idx[lane] : nb;
+      for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+      }
+      if (bi >= nb) bi = r;   // no comparable entry (all NaN): keep the row in place
+      if (lane == 0) { s_piv = bi; piv[r] = bi; }
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p != r)
+      for (int c = tid; c < nb; c += nt) {
+        T t = S[r + c * nb];
+        S[r + c * nb] = S[p + c * nb];
+        S[p + c * nb] = t;
+      }
+    __syncthreads();
+    const T d = S[r + r * nb];
+    if (d != (T)0) {
+      for (int rr = r + 1 + tid; rr < nb; rr += nt) S[rr + r * nb] = S[rr + r * nb] / d;
+      __syncthreads();
+      const int m = nb - r - 1;
+      for (int idx = tid; idx < m * m; idx += nt) {
+        int rr = r + 1 + idx % m, cc = r + 1 + idx / m;
+        S[rr + cc * nb] -= S[rr + r * nb] * S[r + cc * nb];
+      }
+    } else if (tid == 0 && s_zero < 0) {
+      s_zero = r;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) status[ST_ZERO_ROW] = s_zero;
+}
+
+template <typename T>
+void launch_getrf(const T* W, int64_t ldw, int k, int nb, T* S, int* piv_s, int* status,
+                  cudaStream_t s) {
+  {
+    ProfScope ps_("k_getrf", s);
+    k_getrf<T><<<1, 1024, 0, s>>>(W, ldw, k, nb, S, piv_s, status);
+  }
+}
+
+// ---------------------------------------------------------------- ||A_kk^-1||_1
+// One warp per column c of X = U^-1 L^-1 P (FP64 arithmetic on the stored factors);
+// colsum[c] = sum_r |X[r, c]|.  Skipped when the tile has a zero pivot.
+template <typename T>
+__global__ void k_invnorm(const T* __restrict__ S, int nb, const int* __restrict__ piv,
+                          double* __restrict__ colsum, const int* status) {
+  extern __shared__ __align__(16) double ys_all[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  const int c = blockIdx.x * wpb + warp;
+  if (c >= nb) return;
+  if (status[ST_ZERO_ROW] >= 0) {
+    if (lane == 0) colsum[c] = INFINITY;
+    return;
+  }
+  double* ys = ys_all + warp * nb;
+  int pos = c;   // row of the single 1 of column c of P
+  for (int r = 0; r < nb; ++r) {
+    int p = piv[r];
+    if (pos == r) pos = p;
+    else if (pos == p) pos = r;
+  }
+  for (int row = lane; row < nb; row += 32) ys[row] = (row == pos) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int r = pos; r < nb - 1; ++r) {          // y <- L^-1 y (unit lower)
+    const double yr = ys[r];
+    if (yr != 0.0)
+      for (int row = r + 1 + lane; row < nb; row += 32) ys[row] -= (double)S[row + r * nb] * yr;
+    __syncwarp();
+  }
+  for (int r = nb - 1; r >= 0; --r) {           // x <- U^-1 y
+    if (lane == 0) ys[r] = ys[r] / (double)S[r + r * nb];
+    __syncwarp();
+    const double xr = ys[r];
+    if (xr != 0.0)
+      for (int row = lane; row < r; row += 32) ys[row] -= (double)S[row + r * nb] * xr;
+    __syncwarp();
+  }
+  double sum = 0.0;
+  for (int row = lane; row < nb; row += 32) sum += fabs(ys[row]);
+  sum = warp_sum_d(sum);
+  if (lane == 0) colsum[c] = sum;
+}
+
+template <typename T>
+void launch_invnorm(const T* S, int nb, const int* piv_s, double* colsum, const int* status,
+                    cudaStream_t s) {
+  const int wpb = 4;
+  {
+    ProfScope ps_("k_invnorm", s);
+    k_invnorm<T><<<(nb + wpb - 1) / wpb, 32 * wpb, wpb * nb * sizeof(double), s>>>(S, nb, piv_s,
+                                                                                  colsum, status);
+  }
+}
+
+// ---------------------------------------------------------------- decision
+__device__ double log2_ratio(double lhs, double rhs) {
+  if (rhs == 0.0) return lhs > 0.0 ? INFINITY : (lhs == 0.0 ? 0.0 : -INFINITY);
+  if (lhs == 0.0) return -INFINITY;
+  if (isinf(lhs)) return INFINITY;
+  return log2(lhs / rhs);
+}
+
+// Single thread: Eq. 2 (Max), Eq. 3 (Sum), Eq. 4 (MUMPS) with the readings listed in the
+// oracle (">=" selects LU, alpha = 0 or a zero pivot selects QR, last step compares to 0).
+template <typename T>
+__global__ void k_decide(DecideArgs a, const T* __restrict__ S) {
+  if (threadIdx.x != 0) return;
+  int* st = a.status;
+  const int k = a.k;
+  if (st[ST_CODE] != 0) { a.dec[k] = DEC_ABORT; return; }
+  if (st[ST_NONFINITE]) {
+    st[ST_CODE] = -5; st[ST_STEP] = k; st[ST_ROW] = -1;
+    a.dec[k] = DEC_ABORT;
+    return;
+  }
+  const int zr = st[ST_ZERO_ROW];
+  uint8_t d;
+  double mg, L = NAN, R = NAN;
+  const int crit = a.criterion;
+  if (a.forced) {
+    d = a.forced[k];
+    mg = (d == DEC_LU) ? INFINITY : -INFINITY;
+  } else if (crit == 3) {
+    d = DEC_LU; mg = INFINITY;
+  } else if (crit == 4 || a.alpha == 0.0) {
+    d = DEC_QR; mg = -INFINITY;
+  } else if (zr >= 0) {
+    d = DEC_QR; mg = -INFINITY; L = 0.0;
+  } else if (crit == 0 || crit == 1) {
+    double inv = 0.0;
+    for (int c = 0; c < a.nb; ++c) inv = fmax(inv, a.colsum[c]);
+    L = a.alpha * (1.0 / inv);
+    R = 0.0;
+    if (crit == 0) {
+      for (int i = k + 1; i < a.n; ++i) R = fmax(R, a.norms_k[i]);
+    } else {
+      for (int i = k + 1; i < a.n; ++i) R = R + a.norms_k[i];
+    }
+    d = (L >= R) ? DEC_LU : DEC_QR;
+    mg = log2_ratio(L, R);
+  } else {   // MUMPS, Eq. 4
+    bool ok = true;
+    mg = INFINITY;
+    double gprod = 1.0;
+    d = DEC_LU;
+    for (int j = 0; j < a.nb; ++j) {
+      const double pj = fabs((double)S[j + j * a.nb]);
+      const double lj = __longlong_as_double((long long)a.local[j]);
+      const double aj = __longlong_as_double((long long)a.away[j]);
+      if (lj == 0.0) { ok = false; mg = -INFINITY; break; }
+      double est;
+      if (a.mumps_mode == 0) {
+        est = aj * (pj / lj);
+      } else {
+        est = aj * gprod;
+        gprod = gprod * (pj / lj);
+      }
+      const double lhs = a.alpha * pj;
+      if (!(lhs >= est)) ok = false;
+      mg = fmin(mg, log2_ratio(lhs, est));
+    }
+    d = ok ? DEC_LU : DEC_QR;
+  }
+  if (d == DEC_LU && zr >= 0) {
+    st[ST_CODE] = -4; st[ST_STEP] = k; st[ST_ROW] = k * a.nb + zr;
+    d = DEC_ABORT;
+  }
+  a.dec[k] = d;
+  a.margin[k] = mg;
+  a.lhs[k] = L;
+  a.rhs[k] = R;
+}
+
+template <typename T>
+void launch_decide(const DecideArgs& a, const T* S, cudaStream_t s) {
+  {
+    ProfScope ps_("k_decide", s);
+    k_decide<T><<<1, 32, 0, s>>>(a, S);
+  }
+}
+
+#define INST(T)                                                                                  \
+  template void launch_pack<T>(const double*, int64_t, const double*, int64_t, int64_t, int64_t, \
+                               T*, int64_t, cudaStream_t);                                       \
+  template void launch_scale_rows<T>(T*, int64_t, int64_t, int, int64_t, int64_t, double,        \
+                                     cudaStream_t);                                              \
+  template void launch_panel_stats<T>(const T*, int64_t, int, int, int, double*,                 \
+                                      unsigned long long*, unsigned long long*, int*,            \
+                                      cudaStream_t);                                             \
+  template void launch_getrf<T>(const T*, int64_t, int, int, T*, int*, int*, cudaStream_t);      \
+  template void launch_invnorm<T>(const T*, int, const int*, double*, const int*, cudaStream_t); \
+  template void launch_decide<T>(const DecideArgs&, const T*, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace luqr

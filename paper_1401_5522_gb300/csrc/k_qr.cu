@@ -1,0 +1,566 @@
+// QR step (Alg. 3) with the kernels of Alg. 4: GEQRT / UNMQR on single tiles and
+// TSQRT-TSMQR (square eliminated tile) or TTQRT-TTMQR (triangular eliminated tile) on
+// tile pairs.  Reflectors follow the LAPACK dlarfg convention and are kept in
+// compact-WY form per inner block of IB columns: Q_b = I - V T V^T with T (IB x IB)
+// upper triangular (Schreiber-Van Loan forward recurrence); Q^T is applied as
+// C <- C - V (T^T (V^T C)).  T blocks are stored IB x nb per tile for the second pass.
+#include "internal.cuh"
+
+#include <type_traits>
+
+namespace luqr {
+
+constexpr int VST = IB + 1;   // row stride of V / panel blocks in shared memory
+constexpr int TST = IB + 1;   // row stride of T and Gram blocks
+
+template <int SW>
+struct Cst { static constexpr int v = SW + 1; };
+
+// ---------------------------------------------------------------- block application
+// [Ctop; Cbot] <- (I - V T V^T)^T [Ctop; Cbot] for V = [Vtop; Vbot].
+// Vtop is unit lower triangular (entries below its diagonal) when unit_top, else I.
+template <typename T, int SW>
+__device__ void apply_block(const T* Vtop, const T* Vbot, int nbot, const T* Ts, T* Ctop, T* Cbot,
+                            int w, T* Ws, T* W2s, bool unit_top) {
+  constexpr int CST = Cst<SW>::v;
+  constexpr int JR = IB * SW / NT;
+  static_assert(JR >= 1, "slab too narrow");
+  const int tid = threadIdx.x;
+  const int c = tid % SW, jg = tid / SW;
+  if (c < w) {
+    T acc[JR];
+#pragma unroll
+    for (int q = 0; q < JR; ++q) acc[q] = Ctop[(jg * JR + q) * CST + c];
+    if (unit_top) {
+      for (int a = 1; a < IB; ++a) {
+        const T ca = Ctop[a * CST + c];
+#pragma unroll
+        for (int q = 0; q < JR; ++q) {
+          const int j = jg * JR + q;
+          if (a > j) acc[q] += Vtop[a * VST + j] * ca;
+        }
+      }
+    }
+    for (int r = 0; r < nbot; ++r) {
+      const T cr = Cbot[r * CST + c];
+      const T* vr = Vbot + r * VST + jg * JR;
+#pragma unroll
+      for (int q = 0; q < JR; ++q) acc[q] += vr[q] * cr;
+    }
+#pragma unroll
+    for (int q = 0; q < JR; ++q) Ws[(jg * JR + q) * CST + c] = acc[q];
+  }
+  __syncthreads();
+  if (c < w) {
+#pragma unroll
+    for (int q = 0; q < JR; ++q) {
+      const int j = jg * JR + q;
+      T s = (T)0;
+      for (int a = 0; a <= j; ++a) s += Ts[a * TST + j] * Ws[a * CST + c];
+      W2s[j * CST + c] = s;
+    }
+  }
+  __syncthreads();
+  constexpr int G = NT / SW;
+  if (c < w) {
+    for (int a = jg; a < IB; a += G) {
+      T s = W2s[a * CST + c];
+      if (unit_top)
+        for (int j = 0; j < a; ++j) s += Vtop[a * VST + j] * W2s[j * CST + c];
+      Ctop[a * CST + c] -= s;
+    }
+    for (int r = jg; r < nbot; r += G) {
+      const T* vr = Vbot + r * VST;
+      T s = (T)0;
+#pragma unroll 8
+      for (int j = 0; j < IB; ++j) s += vr[j] * W2s[j * CST + c];
+      Cbot[r * CST + c] -= s;
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- Householder helpers
+// Thread 0 forms the reflector of [a0; x] with sum(x^2) = ss (dlarfg convention).
+template <typename T>
+__device__ __forceinline__ void make_reflector(T a0, T ss, T* beta, T* tau, T* denom) {
+  if (ss == (T)0) {
+    *beta = a0; *tau = (T)0; *denom = (T)1;
+  } else {
+    const T nrm = sqrt(a0 * a0 + ss);
+    const T b = (a0 >= (T)0) ? -nrm : nrm;
+    *beta = b;
+    *tau = (b - a0) / b;
+    *denom = a0 - b;
+  }
+}
+
+// Unblocked QR of an IB-column panel P (nrows x IB) in shared memory (GEQRT panel).
+template <typename T>
+__device__ void panel_single(T* Ps, int nrows, T* tau_s, T* red, T* bc) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
+  for (int j = 0; j < IB; ++j) {
+    T part = (T)0;
+    for (int r = j + 1 + tid; r < nrows; r += NT) {
+      const T v = Ps[r * VST + j];
+      part += v * v;
+    }
+    const T ss = block_sum<T>(part, red);
+    if (tid == 0) {
+      T beta, tau, denom;
+      make_reflector<T>(Ps[j * VST + j], ss, &beta, &tau, &denom);
+      tau_s[j] = tau;
+      bc[0] = denom;
+      bc[1] = ss;
+      Ps[j * VST + j] = beta;
+    }
+    __syncthreads();
+    const T tau = tau_s[j];
+    const T denom = bc[0];
+    for (int r = j + 1 + tid; r < nrows; r += NT)
+      Ps[r * VST + j] = (tau == (T)0) ? (T)0 : Ps[r * VST + j] / denom;
+    __syncthreads();
+    if (tau != (T)0) {
+      for (int c = j + 1 + warp; c < IB; c += nw) {
+        T s = (T)0;
+        for (int r = j + 1 + lane; r < nrows; r += 32) s += Ps[r * VST + j] * Ps[r * VST + c];
+        s = warp_sum<T>(s);
+        const T wc = Ps[j * VST + c] + s;
+        __syncwarp();
+        if (lane == 0) Ps[j * VST + c] -= tau * wc;
+        for (int r = j + 1 + lane; r < nrows; r += 32) Ps[r * VST + c] -= tau * Ps[r * VST + j] * wc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Unblocked QR of [Rs; Ps] for a TS/TT pair: Rs is the IB x IB upper block of the
+// eliminator rows jb.., Ps (nrows x IB) the eliminated tile's columns.  For TT the
+// reflector of column j only involves rows < jb + j + 1 of Ps.
+template <typename T>
+__device__ void panel_pair(T* Rs, T* Ps, int nrows, bool tri, int jb, T* tau_s, T* red, T* bc) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
+  for (int j = 0; j < IB; ++j) {
+    const int rows = tri ? min(jb + j + 1, nrows) : nrows;
+    T part = (T)0;
+    for (int r = tid; r < rows; r += NT) {
+      const T v = Ps[r * VST + j];
+      part += v * v;
+    }
+    const T ss = block_sum<T>(part, red);
+    if (tid == 0) {
+      T beta, tau, denom;
+      make_reflector<T>(Rs[j * VST + j], ss, &beta, &tau, &denom);
+      tau_s[j] = tau;
+      bc[0] = denom;
+      Rs[j * VST + j] = beta;
+    }
+    __syncthreads();
+    const T tau = tau_s[j];
+    const T denom = bc[0];
+    for (int r = tid; r < rows; r += NT)
+      Ps[r * VST + j] = (tau == (T)0) ? (T)0 : Ps[r * VST + j] / denom;
+    __syncthreads();
+    if (tau != (T)0) {
+      for (int c = j + 1 + warp; c < IB; c += nw) {
+        T s = (T)0;
+        for (int r = lane; r < rows; r += 32) s += Ps[r * VST + j] * Ps[r * VST + c];
+        s = warp_sum<T>(s);
+        const T wc = Rs[j * VST + c] + s;
+        __syncwarp();
+        if (lane == 0) Rs[j * VST + c] -= tau * wc;
+        for (int r = lane; r < rows; r += 32) Ps[r * VST + c] -= tau * Ps[r * VST + j] * wc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// T of one inner block: G[b][j] = v_b . v_j (b < j), then the forward recurrence
+// T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j], T[j][j] = tau_j.
+// single: v_j = [0..0, 1 (row j), Ps[j+1:, j]];  pair: v_j = [e_j; Ps[:, j]].
+template <typename T>
+__device__ void build_T(const T* Ps, int nrows, bool single, const T* tau_s, T* Gs, T* Ts) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
+  for (int p = warp; p < IB * IB; p += nw) {
+    const int b = p % IB, j = p / IB;
+    if (b >= j) continue;
+    T s = (T)0;
+    const int r0 = single ? j + 1 : 0;
+    for (int r = r0 + lane; r < nrows; r += 32) s += Ps[r * VST + b] * Ps[r * VST + j];
+    s = warp_sum<T>(s);
+    if (lane == 0) Gs[b * TST + j] = single ? s + Ps[j * VST + b] : s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int j = 0; j < IB; ++j) {
+      const T tj = tau_s[j];
+      T val = (T)0;
+      if (lane < j) {
+        T s = (T)0;
+        for (int b = lane; b < j; ++b) s += Ts[lane * TST + b] * Gs[b * TST + j];
+        val = -tj * s;
+      }
+      __syncwarp();
+      if (lane < j) Ts[lane * TST + j] = val;
+      else if (lane == j) Ts[j * TST + j] = tj;
+      else Ts[lane * TST + j] = (T)0;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- shared memory plans
+template <typename T, int SW>
+struct Plan {
+  static constexpr int CST = SW + 1;
+  static size_t geqrt(int nb) {
+    return sizeof(T) * ((size_t)nb * VST + (size_t)nb * CST + 2 * IB * TST + 2 * IB * CST + IB + 32 + 4);
+  }
+  static size_t unmqr(int nb) {
+    return sizeof(T) * ((size_t)nb * CST + (size_t)nb * VST + IB * TST + 2 * IB * CST);
+  }
+  static size_t pair_qrt(int nb) {
+    return sizeof(T) * ((size_t)IB * VST + (size_t)nb * VST + IB * CST + (size_t)nb * CST +
+                        2 * IB * TST + 2 * IB * CST + IB + 32 + 4);
+  }
+  static size_t pair_apply(int nb) {
+    return sizeof(T) * (2 * (size_t)nb * CST + (size_t)nb * VST + IB * TST + 2 * IB * CST);
+  }
+};
+
+// ---------------------------------------------------------------- GEQRT
+template <typename T, int SW>
+__global__ void __launch_bounds__(NT) k_geqrt(Mat<T> F, int k, int nb, TileList tl, T* Tk,
+                                              const uint8_t* __restrict__ dec) {
+  if (dec[k] != DEC_QR) return;
+  constexpr int CST = SW + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ps = reinterpret_cast<T*>(smem_raw);
+  T* Cs = Ps + (size_t)nb * VST;
+  T* Ts = Cs + (size_t)nb * CST;
+  T* Gs = Ts + IB * TST;
+  T* Ws = Gs + IB * TST;
+  T* W2s = Ws + IB * CST;
+  T* tau_s = W2s + IB * CST;
+  T* red = tau_s + IB;
+  T* bc = red + 32;
+  const int i = tl.i0 + blockIdx.x * tl.istride;
+  T* tile = F.p + (int64_t)i * nb + (int64_t)k * nb * F.ld;
+  T* Tslot = Tk + ((size_t)i * 2 + 0) * IB * nb;
+  const int tid = threadIdx.x;
+  for (int jb = 0; jb < nb; jb += IB) {
+    const int nrows = nb - jb;
+    for (int idx = tid; idx < nrows * IB; idx += NT) {
+      const int r = idx % nrows, j = idx / nrows;
+      Ps[r * VST + j] = tile[(jb + r) + (int64_t)(jb + j) * F.ld];
+    }
+    __syncthreads();
+    panel_single<T>(Ps, nrows, tau_s, red, bc);
+    build_T<T>(Ps, nrows, true, tau_s, Gs, Ts);
+    for (int idx = tid; idx < nrows * IB; idx += NT) {
+      const int r = idx % nrows, j = idx / nrows;
+      tile[(jb + r) + (int64_t)(jb + j) * F.ld] = Ps[r * VST + j];
+    }
+    for (int idx = tid; idx < IB * IB; idx += NT) {
+      const int a = idx % IB, j = idx / IB;
+      Tslot[a + (size_t)(jb + j) * IB] = Ts[a * TST + j];
+    }
+    for (int cc = jb + IB; cc < nb; cc += SW) {
+      const int w = min(SW, nb - cc);
+      __syncthreads();
+      for (int idx = tid; idx < nrows * SW; idx += NT) {
+        const int r = idx % nrows, c = idx / nrows;
+        if (c < w) Cs[r * CST + c] = tile[(jb + r) + (int64_t)(cc + c) * F.ld];
+      }
+      __syncthreads();
+      apply_block<T, SW>(Ps, Ps + IB * VST, nrows - IB, Ts, Cs, Cs + IB * CST, w, Ws, W2s, true);
+      for (int idx = tid; idx < nrows * SW; idx += NT) {
+        const int r = idx % nrows, c = idx / nrows;
+        if (c < w) tile[(jb + r) + (int64_t)(cc + c) * F.ld] = Cs[r * CST + c];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- UNMQR
+template <typename T, int SW>
+__global__ void __launch_bounds__(NT) k_unmqr(Mat<const T> F, int k, int nb, TileList tl,
+                                              const T* Tk, Mat<T> C, int64_t c0, int64_t c1,
+                                              const uint8_t* __restrict__ dec) {
+  if (dec[k] != DEC_QR) return;
+  constexpr int CST = SW + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Cs = reinterpret_cast<T*>(smem_raw);
+  T* Vs = Cs + (size_t)nb * CST;
+  T* Ts = Vs + (size_t)nb * VST;
+  T* Ws = Ts + IB * TST;
+  T* W2s = Ws + IB * CST;
+  const int i = tl.i0 + blockIdx.y * tl.istride;
+  const int64_t cb = c0 + (int64_t)blockIdx.x * SW;
+  const int w = (int)min((int64_t)SW, c1 - cb);
+  const T* V = F.p + (int64_t)i * nb + (int64_t)k * nb * F.ld;
+  const T* Tslot = Tk + ((size_t)i * 2 + 0) * IB * nb;
+  const int tid = threadIdx.x;
+  T* Cg = C.p + (int64_t)i * nb + cb * C.ld;
+  for (int idx = tid; idx < nb * SW; idx += NT) {
+    const int r = idx % nb, c = idx / nb;
+    if (c < w) Cs[r * CST + c] = Cg[r + (int64_t)c * C.ld];
+  }
+  for (int jb = 0; jb < nb; jb += IB) {
+    const int nrows = nb - jb;
+    for (int idx = tid; idx < nrows * IB; idx += NT) {
+      const int r = idx % nrows, j = idx / nrows;
+      Vs[r * VST + j] = V[(jb + r) + (int64_t)(jb + j) * F.ld];
+    }
+    for (int idx = tid; idx < IB * IB; idx += NT) {
+      const int a = idx % IB, j = idx / IB;
+      Ts[a * TST + j] = Tslot[a + (size_t)(jb + j) * IB];
+    }
+    __syncthreads();
+    apply_block<T, SW>(Vs, Vs + IB * VST, nrows - IB, Ts, Cs + jb * CST, Cs + (jb + IB) * CST, w,
+                       Ws, W2s, true);
+  }
+  for (int idx = tid; idx < nb * SW; idx += NT) {
+    const int r = idx % nb, c = idx / nb;
+    if (c < w) Cg[r + (int64_t)c * C.ld] = Cs[r * CST + c];
+  }
+}
+
+// ---------------------------------------------------------------- TSQRT / TTQRT
+template <typename T, int SW>
+__global__ void __launch_bounds__(NT) k_pair_qrt(Mat<T> F, int k, int nb, TileList tl, bool tri,
+                                                 T* Tk, const uint8_t* __restrict__ dec) {
+  if (dec[k] != DEC_QR) return;
+  constexpr int CST = SW + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Rs = reinterpret_cast<T*>(smem_raw);
+  T* Ps = Rs + IB * VST;
+  T* Ct = Ps + (size_t)nb * VST;
+  T* Cb = Ct + IB * CST;
+  T* Ts = Cb + (size_t)nb * CST;
+  T* Gs = Ts + IB * TST;
+  T* Ws = Gs + IB * TST;
+  T* W2s = Ws + IB * CST;
+  T* tau_s = W2s + IB * CST;
+  T* red = tau_s + IB;
+  T* bc = red + 32;
+  const int i = tl.i0 + blockIdx.x * tl.istride;
+  const int e = i - tl.eoff;
+  T* R = F.p + (int64_t)e * nb + (int64_t)k * nb * F.ld;
+  T* A = F.p + (int64_t)i * nb + (int64_t)k * nb * F.ld;
+  T* Tslot = Tk + ((size_t)i * 2 + 1) * IB * nb;
+  const int tid = threadIdx.x;
+  for (int jb = 0; jb < nb; jb += IB) {
+    const int rl = tri ? jb + IB : nb;
+    for (int idx = tid; idx < IB * IB; idx += NT) {
+      const int a = idx % IB, j = idx / IB;
+      Rs[a * VST + j] = (a <= j) ? R[(jb + a) + (int64_t)(jb + j) * F.ld] : (T)0;
+    }
+    for (int idx = tid; idx < rl * IB; idx += NT) {
+      const int r = idx % rl, j = idx / rl;
+      Ps[r * VST + j] = (!tri || r <= jb + j) ? A[r + (int64_t)(jb + j) * F.ld] : (T)0;
+    }
+    __syncthreads();
+    panel_pair<T>(Rs, Ps, rl, tri, jb, tau_s, red, bc);
+    build_T<T>(Ps, rl, false, tau_s, Gs, Ts);
+    for (int idx = tid; idx < IB * IB; idx += NT) {
+      const int a = idx % IB, j = idx / IB;
+      if (a <= j) R[(jb + a) + (int64_t)(jb + j) * F.ld] = Rs[a * VST + j];
+      Tslot[a + (size_t)(jb + j) * IB] = Ts[a * TST + j];
+    }
+    for (int idx = tid; idx < rl * IB; idx += NT) {
+      const int r = idx % rl, j = idx / rl;
+      if (!tri || r <= jb + j) A[r + (int64_t)(jb + j) * F.ld] = Ps[r * VST + j];
+    }
+    for (int cc = jb + IB; cc < nb; cc += SW) {
+      const int w = min(SW, nb - cc);
+      __syncthreads();
+      for (int idx = tid; idx < IB * SW; idx += NT) {
+        const int a = idx % IB, c = idx / IB;
+        if (c < w) Ct[a * CST + c] = R[(jb + a) + (int64_t)(cc + c) * F.ld];
+      }
+      for (int idx = tid; idx < rl * SW; idx += NT) {
+        const int r = idx % rl, c = idx / rl;
+        if (c < w) Cb[r * CST + c] = A[r + (int64_t)(cc + c) * F.ld];
+      }
+      __syncthreads();
+      apply_block<T, SW>(nullptr, Ps, rl, Ts, Ct, Cb, w, Ws, W2s, false);
+      for (int idx = tid; idx < IB * SW; idx += NT) {
+        const int a = idx % IB, c = idx / IB;
+        if (c < w) R[(jb + a) + (int64_t)(cc + c) * F.ld] = Ct[a * CST + c];
+      }
+      for (int idx = tid; idx < rl * SW; idx += NT) {
+        const int r = idx % rl, c = idx / rl;
+        if (c < w) A[r + (int64_t)(cc + c) * F.ld] = Cb[r * CST + c];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- TSMQR / TTMQR
+template <typename T, int SW>
+__global__ void __launch_bounds__(NT) k_pair_apply(Mat<const T> F, int k, int nb, TileList tl,
+                                                   bool tri, const T* Tk, Mat<T> C, int64_t c0,
+                                                   int64_t c1, const uint8_t* __restrict__ dec) {
+  if (dec[k] != DEC_QR) return;
+  constexpr int CST = SW + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* C1s = reinterpret_cast<T*>(smem_raw);
+  T* C2s = C1s + (size_t)nb * CST;
+  T* Vs = C2s + (size_t)nb * CST;
+  T* Ts = Vs + (size_t)nb * VST;
+  T* Ws = Ts + IB * TST;
+  T* W2s = Ws + IB * CST;
+  const int i = tl.i0 + blockIdx.y * tl.istride;
+  const int e = i - tl.eoff;
+  const int64_t cb = c0 + (int64_t)blockIdx.x * SW;
+  const int w = (int)min((int64_t)SW, c1 - cb);
+  const T* V = F.p + (int64_t)i * nb + (int64_t)k * nb * F.ld;
+  const T* Tslot = Tk + ((size_t)i * 2 + 1) * IB * nb;
+  T* C1g = C.p + (int64_t)e * nb + cb * C.ld;
+  T* C2g = C.p + (int64_t)i * nb + cb * C.ld;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < nb * SW; idx += NT) {
+    const int r = idx % nb, c = idx / nb;
+    if (c < w) {
+      C1s[r * CST + c] = C1g[r + (int64_t)c * C.ld];
+      C2s[r * CST + c] = C2g[r + (int64_t)c * C.ld];
+    }
+  }
+  for (int jb = 0; jb < nb; jb += IB) {
+    const int rl = tri ? jb + IB : nb;
+    for (int idx = tid; idx < rl * IB; idx += NT) {
+      const int r = idx % rl, j = idx / rl;
+      Vs[r * VST + j] = (!tri || r <= jb + j) ? V[r + (int64_t)(jb + j) * F.ld] : (T)0;
+    }
+    for (int idx = tid; idx < IB * IB; idx += NT) {
+      const int a = idx % IB, j = idx / IB;
+      Ts[a * TST + j] = Tslot[a + (size_t)(jb + j) * IB];
+    }
+    __syncthreads();
+    apply_block<T, SW>(nullptr, Vs, rl, Ts, C1s + jb * CST, C2s, w, Ws, W2s, false);
+  }
+  for (int idx = tid; idx < nb * SW; idx += NT) {
+    const int r = idx % nb, c = idx / nb;
+    if (c < w) {
+      C1g[r + (int64_t)c * C.ld] = C1s[r * CST + c];
+      C2g[r + (int64_t)c * C.ld] = C2s[r * CST + c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+// The slab width SW is the widest of {64, 32, 16, 8} whose shared-memory plan fits.
+enum PlanKind { PLAN_GEQRT, PLAN_UNMQR, PLAN_PAIR_QRT, PLAN_PAIR_APPLY };
+
+template <typename T, int SW>
+static size_t plan_bytes(PlanKind kind, int nb) {
+  switch (kind) {
+    case PLAN_GEQRT: return Plan<T, SW>::geqrt(nb);
+    case PLAN_UNMQR: return Plan<T, SW>::unmqr(nb);
+    case PLAN_PAIR_QRT: return Plan<T, SW>::pair_qrt(nb);
+    default: return Plan<T, SW>::pair_apply(nb);
+  }
+}
+
+template <typename T, typename Fn>
+static void pick_sw(PlanKind kind, int nb, Fn&& fn) {
+  if (plan_bytes<T, 64>(kind, nb) <= (size_t)SMEM_MAX) fn(std::integral_constant<int, 64>{});
+  else if (plan_bytes<T, 32>(kind, nb) <= (size_t)SMEM_MAX) fn(std::integral_constant<int, 32>{});
+  else if (plan_bytes<T, 16>(kind, nb) <= (size_t)SMEM_MAX) fn(std::integral_constant<int, 16>{});
+  else fn(std::integral_constant<int, 8>{});
+}
+
+// Raises the dynamic shared-memory limit of kernel K once per process (the template
+// parameter is the kernel itself, so every instantiation keeps its own flag).
+template <auto K>
+static void set_smem() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAX);
+    done = true;
+  }
+}
+
+template <typename T>
+void launch_geqrt(Mat<T> F, int k, int nb, TileList tl, T* Tk, int n, const uint8_t* dec,
+                  cudaStream_t s) {
+  if (tl.count <= 0) return;
+  (void)n;
+  pick_sw<T>(PLAN_GEQRT, nb, [&](auto tag) {
+    constexpr int SW = decltype(tag)::value;
+    set_smem<k_geqrt<T, SW>>();
+    {
+      ProfScope ps_("k_geqrt", s);
+      k_geqrt<T, SW><<<tl.count, NT, Plan<T, SW>::geqrt(nb), s>>>(F, k, nb, tl, Tk, dec);
+    }
+  });
+}
+
+template <typename T>
+void launch_unmqr(Mat<const T> F, int k, int nb, TileList tl, const T* Tk, int n, Mat<T> C,
+                  int64_t c0, int64_t c1, const uint8_t* dec, cudaStream_t s) {
+  if (tl.count <= 0 || c1 <= c0) return;
+  (void)n;
+  pick_sw<T>(PLAN_UNMQR, nb, [&](auto tag) {
+    constexpr int SW = decltype(tag)::value;
+    set_smem<k_unmqr<T, SW>>();
+    dim3 grid((unsigned)((c1 - c0 + SW - 1) / SW), (unsigned)tl.count);
+    {
+      ProfScope ps_("k_unmqr", s);
+      k_unmqr<T, SW><<<grid, NT, Plan<T, SW>::unmqr(nb), s>>>(F, k, nb, tl, Tk, C, c0, c1, dec);
+    }
+  });
+}
+
+template <typename T>
+void launch_pair_qrt(Mat<T> F, int k, int nb, TileList tl, bool tri, T* Tk, int n,
+                     const uint8_t* dec, cudaStream_t s) {
+  if (tl.count <= 0) return;
+  (void)n;
+  pick_sw<T>(PLAN_PAIR_QRT, nb, [&](auto tag) {
+    constexpr int SW = decltype(tag)::value;
+    set_smem<k_pair_qrt<T, SW>>();
+    {
+      ProfScope ps_(tri ? "k_ttqrt" : "k_tsqrt", s);
+      k_pair_qrt<T, SW><<<tl.count, NT, Plan<T, SW>::pair_qrt(nb), s>>>(F, k, nb, tl, tri, Tk, dec);
+    }
+  });
+}
+
+template <typename T>
+void launch_pair_apply(Mat<const T> F, int k, int nb, TileList tl, bool tri, const T* Tk, int n,
+                       Mat<T> C, int64_t c0, int64_t c1, const uint8_t* dec, cudaStream_t s) {
+  if (tl.count <= 0 || c1 <= c0) return;
+  (void)n;
+  pick_sw<T>(PLAN_PAIR_APPLY, nb, [&](auto tag) {
+    constexpr int SW = decltype(tag)::value;
+    set_smem<k_pair_apply<T, SW>>();
+    dim3 grid((unsigned)((c1 - c0 + SW - 1) / SW), (unsigned)tl.count);
+    {
+      ProfScope ps_(tri ? "k_ttmqr" : "k_tsmqr", s);
+      k_pair_apply<T, SW><<<grid, NT, Plan<T, SW>::pair_apply(nb), s>>>(F, k, nb, tl, tri, Tk, C, c0,
+                                                                       c1, dec);
+    }
+  });
+}
+
+#define INST(T)                                                                                  \
+  template void launch_geqrt<T>(Mat<T>, int, int, TileList, T*, int, const uint8_t*,             \
+                                cudaStream_t);                                                   \
+  template void launch_unmqr<T>(Mat<const T>, int, int, TileList, const T*, int, Mat<T>,         \
+                                int64_t, int64_t, const uint8_t*, cudaStream_t);                 \
+  template void launch_pair_qrt<T>(Mat<T>, int, int, TileList, bool, T*, int, const uint8_t*,    \
+                                   cudaStream_t);                                                \
+  template void launch_pair_apply<T>(Mat<const T>, int, int, TileList, bool, const T*, int,      \
+                                     Mat<T>, int64_t, int64_t, const uint8_t*, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace luqr

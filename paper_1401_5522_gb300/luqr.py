@@ -1,0 +1,267 @@
+"""Python binding of libluqr.so (the C interface declared in include/luqr.h).
+
+Argument marshalling only: every step of the solver runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the current CUDA stream.  If the
+library has not been built this module raises; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libluqr.so")
+
+# constants mirrored from include/luqr.h
+OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_SINGULAR, ERR_NONFINITE, ERR_TIMEOUT, ERR_NOT_CONVERGED = \
+    0, -1, -2, -3, -4, -5, -6, -7
+DEC_QR, DEC_LU, DEC_ABORTED = 0, 1, 2
+MAX, SUM, MUMPS, FORCE_LU, FORCE_QR = 0, 1, 2, 3, 4
+TREE_FLAT_TS, TREE_BINARY_TT, TREE_GROUPED = 0, 1, 2
+PREC_FP64, PREC_FP32 = 0, 1
+
+CRITERIA = {"max": MAX, "sum": SUM, "mumps": MUMPS, "force_lu": FORCE_LU, "force_qr": FORCE_QR}
+TREES = {"flat_ts": TREE_FLAT_TS, "binary_tt": TREE_BINARY_TT, "grouped": TREE_GROUPED}
+PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32}
+
+
+class LuqrError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})" if what else
+                         f"{status_string(status)} ({status})")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tree", ctypes.c_int), ("group", ctypes.c_int), ("precision", ctypes.c_int),
+                ("mumps_mode", ctypes.c_int), ("forced", ctypes.POINTER(ctypes.c_uint8)),
+                ("inject", ctypes.POINTER(ctypes.c_int)), ("n_inject", ctypes.c_int),
+                ("reserved", ctypes.c_int * 9)]
+
+
+_lib = None
+
+# name -> (restype, argtypes); every symbol of include/luqr.h
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_SIGS = {
+    "luqr_factor": (ctypes.c_int, [_P, _I64, _P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                   ctypes.POINTER(Options), _P, ctypes.POINTER(_P)]),
+    "luqr_solve": (ctypes.c_int, [_P, _P, ctypes.c_int, _I64, _P]),
+    "luqr_refine": (ctypes.c_int, [_P, _P, _I64, _P, _P, ctypes.c_double, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _P]),
+    "luqr_decisions": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
+    "luqr_step_stats": (ctypes.c_int, [_P, _P, _P]),
+    "luqr_factor_data": (ctypes.c_int, [_P, _P, _I64]),
+    "luqr_sync": (ctypes.c_int, [_P]),
+    "luqr_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_int)]),
+    "luqr_dims": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64),
+                                 ctypes.POINTER(ctypes.c_int)]),
+    "luqr_destroy": (None, [_P]),
+    "luqr_profile": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    "luqr_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    "luqr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "luqr_version": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """Load libluqr.so (built in-tree by paper_1401_5522_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_1401_5522_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(status):
+    return lib().luqr_status_string(int(status)).decode()
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check_matrix(A):
+    import torch
+    if not (isinstance(A, torch.Tensor) and A.is_cuda and A.dtype == torch.float64 and A.dim() == 2):
+        raise TypeError("A must be a 2-D float64 CUDA tensor")
+    if A.shape[0] != A.shape[1]:
+        raise ValueError("A must be square")
+    if A.stride(0) != 1:
+        raise ValueError("A must be column-major (stride(0) == 1); use inputs.* or A.t().contiguous().t()")
+    return A.stride(1) if A.shape[1] > 1 else A.shape[0]
+
+
+class Handle:
+    """A factorization living on the GPU (owns the library handle)."""
+
+    def __init__(self, ptr, N, nb, stream):
+        self._h = ctypes.c_void_p(ptr)
+        self.N = N
+        self.nb = nb
+        self._stream = stream
+        n = ctypes.c_int()
+        npad = ctypes.c_int64()
+        prec = ctypes.c_int()
+        lib().luqr_dims(self._h, ctypes.byref(n), ctypes.byref(npad), ctypes.byref(prec))
+        self.n, self.npad, self.precision = n.value, npad.value, prec.value
+
+    def _ptr(self):
+        if not self._h:
+            raise RuntimeError("handle already destroyed")
+        return self._h
+
+    def decisions(self):
+        """(dec uint8[n], margin float64[n]); synchronises."""
+        dec = np.zeros(self.n, dtype=np.uint8)
+        mg = np.zeros(self.n, dtype=np.float64)
+        nout = ctypes.c_int()
+        st = lib().luqr_decisions(self._ptr(), dec.ctypes.data_as(_P), mg.ctypes.data_as(_P),
+                                  ctypes.byref(nout))
+        if st not in (OK,):
+            raise LuqrError(st, "luqr_decisions")
+        return dec, mg
+
+    def step_stats(self):
+        lhs = np.zeros(self.n)
+        rhs = np.zeros(self.n)
+        st = lib().luqr_step_stats(self._ptr(), lhs.ctypes.data_as(_P), rhs.ctypes.data_as(_P))
+        if st != OK:
+            raise LuqrError(st, "luqr_step_stats")
+        return lhs, rhs
+
+    def factor_data(self):
+        """The transformed padded workspace as a float64 numpy array (npad x npad)."""
+        out = np.zeros((self.npad, self.npad), dtype=np.float64, order="F")
+        st = lib().luqr_factor_data(self._ptr(), out.ctypes.data_as(_P), self.npad)
+        if st != OK:
+            raise LuqrError(st, "luqr_factor_data")
+        return out
+
+    def info(self):
+        st = ctypes.c_int()
+        step = ctypes.c_int()
+        row = ctypes.c_int()
+        r = lib().luqr_info(self._ptr(), ctypes.byref(st), ctypes.byref(step), ctypes.byref(row))
+        if r != OK:
+            raise LuqrError(r, "luqr_info")
+        return st.value, step.value, row.value
+
+    def sync(self):
+        return lib().luqr_sync(self._ptr())
+
+    def solve(self, B, stream=None):
+        """Second-pass solve in place on B (N or N x nrhs float64 CUDA, column-major)."""
+        import torch
+        if not (B.is_cuda and B.dtype == torch.float64):
+            raise TypeError("B must be a float64 CUDA tensor")
+        if B.dim() == 1:
+            if not B.is_contiguous():
+                raise ValueError("B must be contiguous")
+            nrhs, ldb = 1, B.shape[0]
+        else:
+            if B.stride(0) != 1:
+                raise ValueError("B must be column-major")
+            nrhs, ldb = B.shape[1], max(B.stride(1), B.shape[0])
+        st = lib().luqr_solve(self._ptr(), ctypes.c_void_p(B.data_ptr()), nrhs, ldb,
+                              _stream_ptr(stream))
+        if st != OK:
+            raise LuqrError(st, "luqr_solve")
+        return B
+
+    def refine(self, A, b, x, tol=1e-13, max_iter=30, stream=None):
+        """Iterative refinement; returns (status, iterations, eta)."""
+        lda = _check_matrix(A)
+        it = ctypes.c_int()
+        eta = ctypes.c_double()
+        st = lib().luqr_refine(self._ptr(), ctypes.c_void_p(A.data_ptr()), lda,
+                               ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                               float(tol), int(max_iter), ctypes.byref(it), ctypes.byref(eta),
+                               _stream_ptr(stream))
+        return st, it.value, eta.value
+
+    def close(self):
+        if self._h:
+            lib().luqr_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
+           precision="fp64", mumps_mode=0, forced=None, inject=None, stream=None):
+    """luqr_factor on a column-major float64 CUDA matrix; b (if given) is overwritten by x."""
+    N = A.shape[0]
+    lda = _check_matrix(A)
+    crit = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
+    opt = Options()
+    opt.tree = TREES[tree] if isinstance(tree, str) else int(tree)
+    opt.group = int(group)
+    opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    opt.mumps_mode = int(mumps_mode)
+    keep = []
+    if forced is not None:
+        fa = np.ascontiguousarray(np.asarray(forced, dtype=np.uint8))
+        keep.append(fa)
+        opt.forced = fa.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    if inject:
+        ia = np.ascontiguousarray(np.asarray(list(inject), dtype=np.int32))
+        keep.append(ia)
+        opt.inject = ia.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        opt.n_inject = len(ia)
+    bptr = None
+    if b is not None:
+        import torch
+        if not (b.is_cuda and b.dtype == torch.float64 and b.is_contiguous() and b.numel() == N):
+            raise TypeError("b must be a contiguous float64 CUDA vector of length N")
+        bptr = ctypes.c_void_p(b.data_ptr())
+    out = ctypes.c_void_p()
+    st = lib().luqr_factor(ctypes.c_void_p(A.data_ptr()), lda, bptr, N, int(nb), crit,
+                           float(alpha), ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(out))
+    if st != OK:
+        raise LuqrError(st, "luqr_factor")
+    return Handle(out.value, N, nb, stream)
+
+
+def version():
+    return lib().luqr_version().decode()
+
+
+def profile(enable=True, reset=True):
+    """Start (or stop) the library's per-launch CUDA-event profiler."""
+    return lib().luqr_profile(1 if enable else 0, 1 if reset else 0)
+
+
+def profile_read(cap=64):
+    """{kernel name: (launches, total_ms)} recorded since the last reset (synchronises)."""
+    L = lib()
+    names = (ctypes.c_char_p * cap)()
+    launches = (ctypes.c_int64 * cap)()
+    ms = (ctypes.c_double * cap)()
+    n = L.luqr_profile_read(names, launches, ms, cap)
+    return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(n)}
