@@ -80,7 +80,10 @@ typedef struct luqr_options {
   const int* inject;       /* optional HOST list of steps whose tile row of [A^(k)|b^(k)] is
                               scaled by 2^-27 before the criterion (run-time injection) */
   int n_inject;
-  int reserved[9];
+  int fp32_kernels;        /* FP32 only: 0 = default (tcgen05 GEMM for LU updates, fused
+                              shared-memory QR updates), 1 = no tcgen05 kernels,
+                              2 = tcgen05 for the LU and the QR trailing updates */
+  int reserved[8];
 } luqr_options;
 
 typedef struct luqr_handle* luqr_handle_t;
@@ -126,6 +129,23 @@ int luqr_solve(luqr_handle_t h, double* db, int nrhs, int64_t ldb, void* stream)
 int luqr_refine(luqr_handle_t h, const double* dA, int64_t lda, const double* db,
                 double* dx, double tol, int max_iter, int* iters, double* eta,
                 void* stream);
+
+/*
+ * luqr_refine_gmres - GMRES-based iterative refinement (GMRES-IR, Carson and Higham):
+ * each correction solves A d = r by restarted GMRES in FP64, left-preconditioned by the
+ * handle's factorization applied in its own precision (second pass + back substitution);
+ * then x <- x + d and r = b - A x in FP64.  It converges where classic refinement
+ * (luqr_refine) stagnates, i.e. when kappa(A) times the factorization's unit roundoff
+ * is near or above 1 (for instance FP32 factors of kappa = 1e8 systems).
+ *   restart   Krylov basis size per GMRES cycle, 1..200.
+ *   max_iter  maximum number of outer corrections.
+ *   iters     (host, nullable) total preconditioned GMRES iterations; eta (nullable) final
+ *             normwise backward error.
+ * Other arguments and errors as luqr_refine.  Synchronises once per GMRES iteration.
+ */
+int luqr_refine_gmres(luqr_handle_t h, const double* dA, int64_t lda, const double* db,
+                      double* dx, double tol, int max_iter, int restart, int* iters, double* eta,
+                      void* stream);
 
 /*
  * luqr_decisions - copies the per-step decisions (LUQR_DEC_*) and margins
@@ -175,6 +195,19 @@ int luqr_profile(int enable, int reset);
  * and total device milliseconds.  Any array may be NULL.  Returns the entry count.
  */
 int luqr_profile_read(const char** names, int64_t* launches, double* total_ms, int cap);
+
+/*
+ * luqr_gemm_sub_f32 - the library's tensor-core update kernel on its own:
+ * C <- C - A B for FP32 column-major device matrices (C: M x N, ldc >= M; A: M x K,
+ * lda >= M; B: K x N, ldb >= K).  The product runs on the tcgen05 tensor cores with
+ * 3xTF32 splitting and FP32 accumulation (about FP32 accuracy).  This is the contraction
+ * the factorization uses for its FP32 GEMM trailing updates (Alg. 2, Update).  dstatus
+ * (device int[8], nullable) receives LUQR_ERR_TIMEOUT if a bounded internal wait
+ * expires.  Enqueued on `stream`; returns LUQR_ERR_INVALID or LUQR_ERR_CUDA on bad
+ * arguments or a failed launch.
+ */
+int luqr_gemm_sub_f32(float* C, int64_t ldc, const float* A, int64_t lda, const float* B,
+                      int64_t ldb, int64_t M, int64_t N, int64_t K, int* dstatus, void* stream);
 
 /* luqr_status_string - static text for a status code. */
 const char* luqr_status_string(int status);

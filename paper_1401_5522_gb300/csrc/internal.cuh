@@ -61,6 +61,33 @@ __device__ __forceinline__ T block_sum(T v, T* red /* >= 32 */) {
   return s;
 }
 
+// Asynchronous global -> shared copy of one element (cp.async, no register staging);
+// many copies stay in flight per thread until cp_async_wait_all().
+template <typename T>
+__device__ __forceinline__ void cp_async(T* smem_dst, const T* gsrc) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(saddr), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Raises kernel K's dynamic shared-memory limit to `bytes` when a launch needs more
+// than the current limit (one record per kernel instantiation).  The request is the
+// launch's own size, so kernels that also use static shared memory stay within the
+// per-block maximum.
+template <auto K>
+inline void ensure_dyn_smem(size_t bytes) {
+  static size_t cur = 48 * 1024;
+  if (bytes > cur) {
+    cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cur = bytes;
+  }
+}
+
 // ---------------------------------------------------------------- launch profiler
 void prof_begin(const char* name, cudaStream_t s);
 void prof_end(cudaStream_t s);
@@ -135,6 +162,27 @@ template <typename T>
 void launch_pair_apply(Mat<const T> F, int k, int nb, TileList tl, bool tri, const T* Tk, int n,
                        Mat<T> C, int64_t c0, int64_t c1, const uint8_t* dec, cudaStream_t s);
 
+// Tensor-core (tcgen05, 3xTF32) contraction D = A B (FP32 in, FP32 accumulate) with a
+// batch index z: operand t of the batch starts at base + t * stride (elements).
+enum { TC_MASK_NONE = 0, TC_MASK_UNIT_LOWER = 1, TC_MASK_UPPER = 2 };
+enum { TC_EPI_SUB = 0, TC_EPI_OUT = 1, TC_EPI_ADD_OUT = 2 };   // C -= D | C = D | C = D + C1
+struct TcArgs {
+  const float* A; int64_t lda; int64_t sA; int a_trans; int a_mask;
+  const float* B; int64_t ldb; int64_t sB; int b_trans; int b_mask;
+  float* C; int64_t ldc; int64_t sC;
+  const float* C1; int64_t ldc1; int64_t sC1;
+  int64_t M, N; int K; int epi;
+  const uint8_t* dec; int k_step; uint8_t want;
+  int* status;
+};
+void launch_tc(const TcArgs& a, int batch, const char* name, cudaStream_t s);
+void launch_tfull(const float* G, int64_t sG, const float* Tslots, int64_t sT, float* Tf,
+                  int64_t sTf, int nb, int batch, const uint8_t* dec, int k, cudaStream_t s);
+// C[M x N] -= A[M x K] B[K x N], FP32 column-major (single matrix).
+void launch_gemm_tc(const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
+                    int64_t ldc, int64_t M, int64_t N, int K, const uint8_t* dec, int k,
+                    uint8_t want, int* status, cudaStream_t s);
+
 // Solves and refinement helpers.
 template <typename T>
 void launch_trsv_diag(Mat<const T> U, int k, int nb, Mat<T> X, int nrhs, int* status,
@@ -154,5 +202,11 @@ void launch_row_abs_sum_max(const double* A, int64_t lda, int64_t N, double* par
 void launch_vec_absmax(const double* v, int64_t N, double* out, cudaStream_t s);
 template <typename T>
 void launch_axpy_update(double* x, const T* d, int64_t N, const double* scale, cudaStream_t s);
+void launch_matvec(const double* A, int64_t lda, int64_t N, const double* v, double* out,
+                   double* partial, int nchunk, cudaStream_t s);
+void launch_multidot(const double* V, int64_t ldv, int64_t N, int cnt, const double* w,
+                     double* dots, cudaStream_t s);
+void launch_multiaxpy(const double* V, int64_t ldv, int64_t N, int cnt, const double* coef,
+                      double* w, double alpha, cudaStream_t s);
 
 }  // namespace luqr

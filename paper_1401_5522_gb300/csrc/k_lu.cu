@@ -46,8 +46,9 @@ __global__ void __launch_bounds__(256) k_swptrsm(Mat<const T> LU, int nb, const 
   for (int r = tid; r < nb; r += blockDim.x) spiv[r] = piv[r];
   for (int idx = tid; idx < nb * w; idx += blockDim.x) {
     int r = idx % nb, c = idx / nb;
-    Cs[r * ST + c] = C(row0 + r, cb + c);
+    cp_async(&Cs[r * ST + c], &C(row0 + r, cb + c));
   }
+  cp_async_wait_all();
   __syncthreads();
   if (tid < w)
     for (int r = 0; r < nb; ++r) {
@@ -79,11 +80,7 @@ void launch_swptrsm(Mat<const T> LU, int nb, const int* piv_k, Mat<T> C, int64_t
   if (c1 <= c0) return;
   const int nblk = (int)((c1 - c0 + SWW - 1) / SWW);
   const size_t smem = (size_t)nb * (SWW + 1) * sizeof(T) + (size_t)nb * sizeof(int);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_swptrsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAX);
-    attr_set = true;
-  }
+  ensure_dyn_smem<k_swptrsm<T>>(smem);
   {
     ProfScope ps_("k_swptrsm", s);
     k_swptrsm<T><<<nblk, 256, smem, s>>>(LU, nb, piv_k, C, row0, c0, c1, dec, k);
@@ -109,8 +106,10 @@ __global__ void __launch_bounds__(256) k_trsm(Mat<const T> LU, int nb, Mat<T> X,
   const int tid = threadIdx.x;
   for (int idx = tid; idx < TRB * nb; idx += blockDim.x) {
     int r = idx % TRB, c = idx / TRB;
-    Xs[r * ST + c] = (r < h) ? X(rb + r, xc + c) : (T)0;
+    if (r < h) cp_async(&Xs[r * ST + c], &X(rb + r, xc + c));
+    else Xs[r * ST + c] = (T)0;
   }
+  cp_async_wait_all();
   __syncthreads();
   const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int c = 0; c < nb; ++c) {
@@ -136,11 +135,7 @@ void launch_trsm(Mat<const T> LU, int nb, Mat<T> X, int64_t r0, int64_t r1, int6
   if (r1 <= r0) return;
   const int nblk = (int)((r1 - r0 + TRB - 1) / TRB);
   const size_t smem = ((size_t)TRB * (nb + 1) + nb) * sizeof(T);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAX);
-    attr_set = true;
-  }
+  ensure_dyn_smem<k_trsm<T>>(smem);
   {
     ProfScope ps_("k_trsm", s);
     k_trsm<T><<<nblk, 256, smem, s>>>(LU, nb, X, r0, r1, xc, dec, k);

@@ -117,79 +117,186 @@ void launch_panel_stats(const T* W, int64_t ldw, int k, int n, int nb, double* n
 // S <- A_kk, then P S = L U in place with partial pivoting inside the tile: the pivot
 // of column r is the first row of maximal |S[r:, r]|.  An exact zero pivot leaves the
 // column unscaled and is recorded (first one) in status[ST_ZERO_ROW].
+//
+// Blocked right-looking order (same operations per element as the column loop, up to
+// the summation order of the trailing update): for each panel of GP columns
+//   (a) the panel rows jb.. are factored in shared memory (warp 0 searches the pivot),
+//   (b) the panel's row exchanges are applied to the other columns as one gather,
+//   (c) U12 <- L11^-1 A12 (one thread per column),
+//   (d) A22 <- A22 - L21 U12 with U12 staged in shared memory per column chunk.
+constexpr int GP = 32;        // panel width
+constexpr int GT = 512;       // threads
+constexpr int GCH = 64;       // column chunk of the trailing update
+constexpr int GCG = 32;       // column chunk of the row gather: 2*GP moved rows x GCG <= GP*GCH
+static_assert(2 * GP * GCG <= GP * GCH, "gather buffer must fit in the U12 staging area");
+
 template <typename T>
-__global__ void __launch_bounds__(1024) k_getrf(const T* __restrict__ W, int64_t ldw, int k,
-                                                int nb, T* __restrict__ S, int* __restrict__ piv,
-                                                int* status) {
+__global__ void __launch_bounds__(GT) k_getrf(const T* __restrict__ W, int64_t ldw, int k, int nb,
+                                              T* __restrict__ S, int* __restrict__ piv,
+                                              int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* P = reinterpret_cast<T*>(smem_raw);          // nb x GP panel, row stride GP+1
+  T* U12 = P + (size_t)nb * (GP + 1);              // GP x GCH chunk, row stride GCH
+  int* perm = reinterpret_cast<int*>(U12 + GP * GCH);   // nb
+  int* moved = perm + nb;                          // <= 2*GP moved rows
+  __shared__ int s_nmoved, s_zero;
+  __shared__ T s_piv_val;
   const T* A = W + (int64_t)k * nb + (int64_t)k * nb * ldw;
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  for (int idx = tid; idx < nb * nb; idx += nt) {
-    int r = idx % nb, c = idx / nb;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int PST = GP + 1;
+  for (int idx = tid; idx < nb * nb; idx += GT) {
+    const int r = idx % nb, c = idx / nb;
     S[idx] = A[r + (int64_t)c * ldw];
   }
-  __shared__ double s_val[32];
-  __shared__ int s_idx[32];
-  __shared__ int s_piv;
-  __shared__ int s_zero;
   if (tid == 0) s_zero = -1;
   __syncthreads();
-  for (int r = 0; r < nb; ++r) {
-    double bv = -1.0;
-    int bi = nb;
-    for (int rr = r + tid; rr < nb; rr += nt) {
-      double v = fabs((double)S[rr + r * nb]);
-      if (v > bv) { bv = v; bi = rr; }
+  for (int jb = 0; jb < nb; jb += GP) {
+    const int nr = nb - jb;
+    // ---- (a) panel factorization in shared memory
+    for (int idx = tid; idx < nr * GP; idx += GT) {
+      const int r = idx % nr, j = idx / nr;
+      P[r * PST + j] = S[(jb + r) + (jb + j) * nb];
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-    }
-    if (lane == 0) { s_val[warp] = bv; s_idx[warp] = bi; }
+    for (int i = tid; i < nr; i += GT) perm[i] = i;
     __syncthreads();
-    if (warp == 0) {
-      bv = lane < nw ? s_val[lane] : -1.0;
-      bi = lane < nw ? s_idx[lane] : nb;
-      for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    for (int j = 0; j < GP; ++j) {
+      if (warp == 0) {
+        double bv = -1.0;
+        int bi = nr;
+        for (int r = j + lane; r < nr; r += 32) {
+          const double v = fabs((double)P[r * PST + j]);
+          if (v > bv) { bv = v; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        }
+        if (bi >= nr) bi = j;                 // no comparable entry (NaN): keep the row
+        if (bi != j)
+          for (int c = lane; c < GP; c += 32) {
+            const T tmp = P[j * PST + c];
+            P[j * PST + c] = P[bi * PST + c];
+            P[bi * PST + c] = tmp;
+          }
+        __syncwarp();
+        if (lane == 0) {
+          piv[jb + j] = jb + bi;
+          const int tmp = perm[j];
+          perm[j] = perm[bi];
+          perm[bi] = tmp;
+          s_piv_val = P[j * PST + j];
+          if (P[j * PST + j] == (T)0 && s_zero < 0) s_zero = jb + j;
+        }
       }
-      if (bi >= nb) bi = r;   // no comparable entry (all NaN): keep the row in place
-      if (lane == 0) { s_piv = bi; piv[r] = bi; }
-    }
-    __syncthreads();
-    const int p = s_piv;
-    if (p != r)
-      for (int c = tid; c < nb; c += nt) {
-        T t = S[r + c * nb];
-        S[r + c * nb] = S[p + c * nb];
-        S[p + c * nb] = t;
-      }
-    __syncthreads();
-    const T d = S[r + r * nb];
-    if (d != (T)0) {
-      for (int rr = r + 1 + tid; rr < nb; rr += nt) S[rr + r * nb] = S[rr + r * nb] / d;
       __syncthreads();
-      const int m = nb - r - 1;
-      for (int idx = tid; idx < m * m; idx += nt) {
-        int rr = r + 1 + idx % m, cc = r + 1 + idx / m;
-        S[rr + cc * nb] -= S[rr + r * nb] * S[r + cc * nb];
+      const T d = s_piv_val;
+      if (d != (T)0) {
+        for (int r = j + 1 + tid; r < nr; r += GT) P[r * PST + j] = P[r * PST + j] / d;
+        __syncthreads();
+        const int mr = nr - j - 1, mc = GP - j - 1;
+        for (int idx = tid; idx < mr * mc; idx += GT) {
+          const int r = j + 1 + idx % mr, c = j + 1 + idx / mr;
+          P[r * PST + c] -= P[r * PST + j] * P[j * PST + c];
+        }
       }
-    } else if (tid == 0 && s_zero < 0) {
-      s_zero = r;
+      __syncthreads();
+    }
+    for (int idx = tid; idx < nr * GP; idx += GT) {
+      const int r = idx % nr, j = idx / nr;
+      S[(jb + r) + (jb + j) * nb] = P[r * PST + j];
+    }
+    // ---- (b) gather the moved rows of the columns outside the panel
+    if (tid == 0) {
+      int cnt = 0;
+      for (int i = 0; i < nr && cnt < 2 * GP; ++i)
+        if (perm[i] != i) moved[cnt++] = i;
+      s_nmoved = cnt;
     }
     __syncthreads();
+    const int nm = s_nmoved;
+    const int nother = nb - GP;   // columns outside the panel
+    for (int c0 = 0; c0 < nother; c0 += GCG) {
+      const int cw = min(GCG, nother - c0);
+      T* buf = U12;   // reuse of the staging area: nm x cw <= 2*GP x GCG values
+      for (int idx = tid; idx < nm * cw; idx += GT) {
+        const int a = idx % nm, cc = idx / nm;
+        int col = c0 + cc;
+        col = col < jb ? col : col + GP;
+        buf[idx] = S[(jb + perm[moved[a]]) + col * nb];
+      }
+      __syncthreads();
+      for (int idx = tid; idx < nm * cw; idx += GT) {
+        const int a = idx % nm, cc = idx / nm;
+        int col = c0 + cc;
+        col = col < jb ? col : col + GP;
+        S[(jb + moved[a]) + col * nb] = buf[idx];
+      }
+      __syncthreads();
+    }
+    // ---- (c) U12 <- L11^-1 A12 and (d) A22 -= L21 U12, per chunk of trailing columns
+    for (int c0 = jb + GP; c0 < nb; c0 += GCH) {
+      const int cw = min(GCH, nb - c0);
+      if (tid < cw) {
+        T u[GP];
+#pragma unroll
+        for (int r = 0; r < GP; ++r) u[r] = S[(jb + r) + (c0 + tid) * nb];
+#pragma unroll
+        for (int r = 0; r < GP; ++r) {
+#pragma unroll
+          for (int q = r + 1; q < GP; ++q) u[q] -= P[q * PST + r] * u[r];
+        }
+#pragma unroll
+        for (int r = 0; r < GP; ++r) {
+          S[(jb + r) + (c0 + tid) * nb] = u[r];
+          U12[r * GCH + tid] = u[r];
+        }
+      }
+      __syncthreads();
+      const int mr = nr - GP;
+      const int rt = (mr + 3) / 4, ct = (cw + 3) / 4;
+      for (int idx = tid; idx < rt * ct; idx += GT) {
+        const int rb = (idx % rt) * 4, cb = (idx / rt) * 4;
+        T acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) acc[i][jj] = (T)0;
+        for (int q = 0; q < GP; ++q) {
+          T a[4], bq[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = (rb + i < mr) ? P[(GP + rb + i) * PST + q] : (T)0;
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) bq[jj] = (cb + jj < cw) ? U12[q * GCH + cb + jj] : (T)0;
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) acc[i][jj] += a[i] * bq[jj];
+        }
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (rb + i < mr && cb + jj < cw) S[(jb + GP + rb + i) + (c0 + cb + jj) * nb] -= acc[i][jj];
+      }
+      __syncthreads();
+    }
   }
   if (tid == 0) status[ST_ZERO_ROW] = s_zero;
 }
 
 template <typename T>
+size_t getrf_smem(int nb) {
+  return sizeof(T) * ((size_t)nb * (GP + 1) + (size_t)GP * GCH) + sizeof(int) * (size_t)(nb + 2 * GP);
+}
+
+template <typename T>
 void launch_getrf(const T* W, int64_t ldw, int k, int nb, T* S, int* piv_s, int* status,
                   cudaStream_t s) {
+  ensure_dyn_smem<k_getrf<T>>(getrf_smem<T>(nb));
   {
     ProfScope ps_("k_getrf", s);
-    k_getrf<T><<<1, 1024, 0, s>>>(W, ldw, k, nb, S, piv_s, status);
+    k_getrf<T><<<1, GT, getrf_smem<T>(nb), s>>>(W, ldw, k, nb, S, piv_s, status);
   }
 }
 

@@ -16,12 +16,171 @@ constexpr int TST = IB + 1;   // row stride of T and Gram blocks
 template <int SW>
 struct Cst { static constexpr int v = SW + 1; };
 
+// ---------------------------------------------------------------- FP32 tensor-core path
+// For FP32 tiles the three products of apply_block run on the tensor cores with 3xTF32
+// splitting: x = hi + lo with hi = tf32(x), lo = tf32(x - hi); a*b ~ ah*bh + ah*bl + al*bh
+// (al*bl dropped), FP32 accumulation.  mma.sync m16n8k8 fragments (A row-major 16x8,
+// B column-major 8x8): a0=(g,t) a1=(g+8,t) a2=(g,t+4) a3=(g+8,t+4); b0=(t,g) b1=(t+4,g);
+// c0=(g,2t) c1=(g,2t+1) c2=(g+8,2t) c3=(g+8,2t+1) with g = lane/4, t = lane%4.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split3(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// d += a b with 3xTF32 (small terms first).
+__device__ __forceinline__ void mma3(float* d, const float* a, const float* b) {
+  uint32_t ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) split3(a[i], ah[i], al[i]);
+  split3(b[0], bh[0], bl[0]);
+  split3(b[1], bh[1], bl[1]);
+  mma_tf32(d, al, bh);
+  mma_tf32(d, ah, bl);
+  mma_tf32(d, ah, bh);
+}
+
+// Stacked-operand helpers: rows 0..IB-1 come from the top block, rows IB.. from the bottom.
+__device__ __forceinline__ float vstk(const float* Vtop, const float* Vbot, bool unit_top, int k,
+                                      int j) {
+  if (k >= IB) return Vbot[(k - IB) * VST + j];
+  if (k == j) return 1.0f;
+  return (unit_top && k > j) ? Vtop[k * VST + j] : 0.0f;
+}
+
+template <int SW>
+__device__ void apply_block_mma(const float* Vtop, const float* Vbot, int nbot, const float* Ts,
+                                float* Ctop, float* Cbot, float* Ws, float* W2s, bool unit_top) {
+  constexpr int CST = SW + 1;
+  constexpr int NTN = SW / 8;          // n-tiles of 8 columns
+  constexpr int NPW = NTN / 4;         // n-tiles per warp in the 32-row products
+  static_assert(NPW >= 1, "tensor-core path needs SW >= 32");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int K1 = IB + nbot;
+  auto cstk = [&](int k, int c) -> float {
+    return k < IB ? Ctop[k * CST + c] : Cbot[(k - IB) * CST + c];
+  };
+  // ---- W (IB x SW) = [Vtop; Vbot]^T [Ctop; Cbot]
+  {
+    const int m0 = (warp & 1) * 16;
+    const int nbase = (warp >> 1) * NPW;
+    float acc[NPW][4];
+#pragma unroll
+    for (int q = 0; q < NPW; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+    for (int k0 = 0; k0 < K1; k0 += 8) {
+      float a[4];
+      a[0] = vstk(Vtop, Vbot, unit_top, k0 + t, m0 + g);
+      a[1] = vstk(Vtop, Vbot, unit_top, k0 + t, m0 + g + 8);
+      a[2] = vstk(Vtop, Vbot, unit_top, k0 + t + 4, m0 + g);
+      a[3] = vstk(Vtop, Vbot, unit_top, k0 + t + 4, m0 + g + 8);
+#pragma unroll
+      for (int q = 0; q < NPW; ++q) {
+        const int n0 = (nbase + q) * 8;
+        float b[2] = {cstk(k0 + t, n0 + g), cstk(k0 + t + 4, n0 + g)};
+        mma3(acc[q], a, b);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NPW; ++q) {
+      const int n0 = (nbase + q) * 8;
+      Ws[(m0 + g) * CST + n0 + 2 * t] = acc[q][0];
+      Ws[(m0 + g) * CST + n0 + 2 * t + 1] = acc[q][1];
+      Ws[(m0 + g + 8) * CST + n0 + 2 * t] = acc[q][2];
+      Ws[(m0 + g + 8) * CST + n0 + 2 * t + 1] = acc[q][3];
+    }
+  }
+  __syncthreads();
+  // ---- W2 = T^T W (T upper triangular, stored with zeros below the diagonal)
+  {
+    const int m0 = (warp & 1) * 16;
+    const int nbase = (warp >> 1) * NPW;
+    float acc[NPW][4];
+#pragma unroll
+    for (int q = 0; q < NPW; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+#pragma unroll
+    for (int k0 = 0; k0 < IB; k0 += 8) {
+      float a[4] = {Ts[(k0 + t) * TST + m0 + g], Ts[(k0 + t) * TST + m0 + g + 8],
+                    Ts[(k0 + t + 4) * TST + m0 + g], Ts[(k0 + t + 4) * TST + m0 + g + 8]};
+#pragma unroll
+      for (int q = 0; q < NPW; ++q) {
+        const int n0 = (nbase + q) * 8;
+        float b[2] = {Ws[(k0 + t) * CST + n0 + g], Ws[(k0 + t + 4) * CST + n0 + g]};
+        mma3(acc[q], a, b);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NPW; ++q) {
+      const int n0 = (nbase + q) * 8;
+      W2s[(m0 + g) * CST + n0 + 2 * t] = acc[q][0];
+      W2s[(m0 + g) * CST + n0 + 2 * t + 1] = acc[q][1];
+      W2s[(m0 + g + 8) * CST + n0 + 2 * t] = acc[q][2];
+      W2s[(m0 + g + 8) * CST + n0 + 2 * t + 1] = acc[q][3];
+    }
+  }
+  __syncthreads();
+  // ---- [Ctop; Cbot] -= [Vtop; Vbot] W2   (accumulator starts from C, A negated)
+  {
+    const int MT = K1 / 16;
+    for (int mt = warp; mt < MT; mt += NT / 32) {
+      const int m0 = mt * 16;
+      float* rowA = (m0 < IB) ? Ctop + m0 * CST : Cbot + (m0 - IB) * CST;
+      float acc[NTN][4];
+#pragma unroll
+      for (int q = 0; q < NTN; ++q) {
+        const int n0 = q * 8;
+        acc[q][0] = rowA[g * CST + n0 + 2 * t];
+        acc[q][1] = rowA[g * CST + n0 + 2 * t + 1];
+        acc[q][2] = rowA[(g + 8) * CST + n0 + 2 * t];
+        acc[q][3] = rowA[(g + 8) * CST + n0 + 2 * t + 1];
+      }
+#pragma unroll
+      for (int k0 = 0; k0 < IB; k0 += 8) {
+        float a[4] = {-vstk(Vtop, Vbot, unit_top, m0 + g, k0 + t),
+                      -vstk(Vtop, Vbot, unit_top, m0 + g + 8, k0 + t),
+                      -vstk(Vtop, Vbot, unit_top, m0 + g, k0 + t + 4),
+                      -vstk(Vtop, Vbot, unit_top, m0 + g + 8, k0 + t + 4)};
+#pragma unroll
+        for (int q = 0; q < NTN; ++q) {
+          const int n0 = q * 8;
+          float b[2] = {W2s[(k0 + t) * CST + n0 + g], W2s[(k0 + t + 4) * CST + n0 + g]};
+          mma3(acc[q], a, b);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NTN; ++q) {
+        const int n0 = q * 8;
+        rowA[g * CST + n0 + 2 * t] = acc[q][0];
+        rowA[g * CST + n0 + 2 * t + 1] = acc[q][1];
+        rowA[(g + 8) * CST + n0 + 2 * t] = acc[q][2];
+        rowA[(g + 8) * CST + n0 + 2 * t + 1] = acc[q][3];
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------- block application
 // [Ctop; Cbot] <- (I - V T V^T)^T [Ctop; Cbot] for V = [Vtop; Vbot].
 // Vtop is unit lower triangular (entries below its diagonal) when unit_top, else I.
 template <typename T, int SW>
 __device__ void apply_block(const T* Vtop, const T* Vbot, int nbot, const T* Ts, T* Ctop, T* Cbot,
                             int w, T* Ws, T* W2s, bool unit_top) {
+  if constexpr (std::is_same<T, float>::value && SW >= 32) {
+    (void)w;
+    apply_block_mma<SW>(Vtop, Vbot, nbot, Ts, Ctop, Cbot, Ws, W2s, unit_top);
+    return;
+  }
   constexpr int CST = Cst<SW>::v;
   constexpr int JR = IB * SW / NT;
   static_assert(JR >= 1, "slab too narrow");
@@ -96,36 +255,40 @@ __device__ __forceinline__ void make_reflector(T a0, T ss, T* beta, T* tau, T* d
 }
 
 // Unblocked QR of an IB-column panel P (nrows x IB) in shared memory (GEQRT panel).
+// Warp 0 forms each reflector (norm, beta, tau, scaling by 1/(a0 - beta)); then every
+// warp applies it to its share of the remaining panel columns: two barriers per column.
 template <typename T>
 __device__ void panel_single(T* Ps, int nrows, T* tau_s, T* red, T* bc) {
+  (void)red; (void)bc;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
+  (void)tid;
   for (int j = 0; j < IB; ++j) {
-    T part = (T)0;
-    for (int r = j + 1 + tid; r < nrows; r += NT) {
-      const T v = Ps[r * VST + j];
-      part += v * v;
-    }
-    const T ss = block_sum<T>(part, red);
-    if (tid == 0) {
+    if (warp == 0) {
+      T part = (T)0;
+      for (int r = j + 1 + lane; r < nrows; r += 32) {
+        const T v = Ps[r * VST + j];
+        part += v * v;
+      }
+      const T ss = warp_sum<T>(part);
       T beta, tau, denom;
       make_reflector<T>(Ps[j * VST + j], ss, &beta, &tau, &denom);
-      tau_s[j] = tau;
-      bc[0] = denom;
-      bc[1] = ss;
-      Ps[j * VST + j] = beta;
+      const T inv = (T)1 / denom;
+      for (int r = j + 1 + lane; r < nrows; r += 32)
+        Ps[r * VST + j] = (tau == (T)0) ? (T)0 : Ps[r * VST + j] * inv;
+      __syncwarp();
+      if (lane == 0) {
+        Ps[j * VST + j] = beta;
+        tau_s[j] = tau;
+      }
     }
     __syncthreads();
     const T tau = tau_s[j];
-    const T denom = bc[0];
-    for (int r = j + 1 + tid; r < nrows; r += NT)
-      Ps[r * VST + j] = (tau == (T)0) ? (T)0 : Ps[r * VST + j] / denom;
-    __syncthreads();
     if (tau != (T)0) {
       for (int c = j + 1 + warp; c < IB; c += nw) {
-        T s = (T)0;
-        for (int r = j + 1 + lane; r < nrows; r += 32) s += Ps[r * VST + j] * Ps[r * VST + c];
-        s = warp_sum<T>(s);
-        const T wc = Ps[j * VST + c] + s;
+        T sum = (T)0;
+        for (int r = j + 1 + lane; r < nrows; r += 32) sum += Ps[r * VST + j] * Ps[r * VST + c];
+        sum = warp_sum<T>(sum);
+        const T wc = Ps[j * VST + c] + sum;
         __syncwarp();
         if (lane == 0) Ps[j * VST + c] -= tau * wc;
         for (int r = j + 1 + lane; r < nrows; r += 32) Ps[r * VST + c] -= tau * Ps[r * VST + j] * wc;
@@ -140,34 +303,37 @@ __device__ void panel_single(T* Ps, int nrows, T* tau_s, T* red, T* bc) {
 // reflector of column j only involves rows < jb + j + 1 of Ps.
 template <typename T>
 __device__ void panel_pair(T* Rs, T* Ps, int nrows, bool tri, int jb, T* tau_s, T* red, T* bc) {
+  (void)red; (void)bc;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
+  (void)tid;
   for (int j = 0; j < IB; ++j) {
     const int rows = tri ? min(jb + j + 1, nrows) : nrows;
-    T part = (T)0;
-    for (int r = tid; r < rows; r += NT) {
-      const T v = Ps[r * VST + j];
-      part += v * v;
-    }
-    const T ss = block_sum<T>(part, red);
-    if (tid == 0) {
+    if (warp == 0) {
+      T part = (T)0;
+      for (int r = lane; r < rows; r += 32) {
+        const T v = Ps[r * VST + j];
+        part += v * v;
+      }
+      const T ss = warp_sum<T>(part);
       T beta, tau, denom;
       make_reflector<T>(Rs[j * VST + j], ss, &beta, &tau, &denom);
-      tau_s[j] = tau;
-      bc[0] = denom;
-      Rs[j * VST + j] = beta;
+      const T inv = (T)1 / denom;
+      for (int r = lane; r < rows; r += 32)
+        Ps[r * VST + j] = (tau == (T)0) ? (T)0 : Ps[r * VST + j] * inv;
+      __syncwarp();
+      if (lane == 0) {
+        Rs[j * VST + j] = beta;
+        tau_s[j] = tau;
+      }
     }
     __syncthreads();
     const T tau = tau_s[j];
-    const T denom = bc[0];
-    for (int r = tid; r < rows; r += NT)
-      Ps[r * VST + j] = (tau == (T)0) ? (T)0 : Ps[r * VST + j] / denom;
-    __syncthreads();
     if (tau != (T)0) {
       for (int c = j + 1 + warp; c < IB; c += nw) {
-        T s = (T)0;
-        for (int r = lane; r < rows; r += 32) s += Ps[r * VST + j] * Ps[r * VST + c];
-        s = warp_sum<T>(s);
-        const T wc = Rs[j * VST + c] + s;
+        T sum = (T)0;
+        for (int r = lane; r < rows; r += 32) sum += Ps[r * VST + j] * Ps[r * VST + c];
+        sum = warp_sum<T>(sum);
+        const T wc = Rs[j * VST + c] + sum;
         __syncwarp();
         if (lane == 0) Rs[j * VST + c] -= tau * wc;
         for (int r = lane; r < rows; r += 32) Ps[r * VST + c] -= tau * Ps[r * VST + j] * wc;
@@ -255,8 +421,9 @@ __global__ void __launch_bounds__(NT) k_geqrt(Mat<T> F, int k, int nb, TileList 
     const int nrows = nb - jb;
     for (int idx = tid; idx < nrows * IB; idx += NT) {
       const int r = idx % nrows, j = idx / nrows;
-      Ps[r * VST + j] = tile[(jb + r) + (int64_t)(jb + j) * F.ld];
+      cp_async(&Ps[r * VST + j], &tile[(jb + r) + (int64_t)(jb + j) * F.ld]);
     }
+    cp_async_wait_all();
     __syncthreads();
     panel_single<T>(Ps, nrows, tau_s, red, bc);
     build_T<T>(Ps, nrows, true, tau_s, Gs, Ts);
@@ -273,8 +440,9 @@ __global__ void __launch_bounds__(NT) k_geqrt(Mat<T> F, int k, int nb, TileList 
       __syncthreads();
       for (int idx = tid; idx < nrows * SW; idx += NT) {
         const int r = idx % nrows, c = idx / nrows;
-        if (c < w) Cs[r * CST + c] = tile[(jb + r) + (int64_t)(cc + c) * F.ld];
+        if (c < w) cp_async(&Cs[r * CST + c], &tile[(jb + r) + (int64_t)(cc + c) * F.ld]);
       }
+      cp_async_wait_all();
       __syncthreads();
       apply_block<T, SW>(Ps, Ps + IB * VST, nrows - IB, Ts, Cs, Cs + IB * CST, w, Ws, W2s, true);
       for (int idx = tid; idx < nrows * SW; idx += NT) {
@@ -308,18 +476,19 @@ __global__ void __launch_bounds__(NT) k_unmqr(Mat<const T> F, int k, int nb, Til
   T* Cg = C.p + (int64_t)i * nb + cb * C.ld;
   for (int idx = tid; idx < nb * SW; idx += NT) {
     const int r = idx % nb, c = idx / nb;
-    if (c < w) Cs[r * CST + c] = Cg[r + (int64_t)c * C.ld];
+    if (c < w) cp_async(&Cs[r * CST + c], &Cg[r + (int64_t)c * C.ld]);
   }
   for (int jb = 0; jb < nb; jb += IB) {
     const int nrows = nb - jb;
     for (int idx = tid; idx < nrows * IB; idx += NT) {
       const int r = idx % nrows, j = idx / nrows;
-      Vs[r * VST + j] = V[(jb + r) + (int64_t)(jb + j) * F.ld];
+      cp_async(&Vs[r * VST + j], &V[(jb + r) + (int64_t)(jb + j) * F.ld]);
     }
     for (int idx = tid; idx < IB * IB; idx += NT) {
       const int a = idx % IB, j = idx / IB;
-      Ts[a * TST + j] = Tslot[a + (size_t)(jb + j) * IB];
+      cp_async(&Ts[a * TST + j], &Tslot[a + (size_t)(jb + j) * IB]);
     }
+    cp_async_wait_all();
     __syncthreads();
     apply_block<T, SW>(Vs, Vs + IB * VST, nrows - IB, Ts, Cs + jb * CST, Cs + (jb + IB) * CST, w,
                        Ws, W2s, true);
@@ -358,12 +527,15 @@ __global__ void __launch_bounds__(NT) k_pair_qrt(Mat<T> F, int k, int nb, TileLi
     const int rl = tri ? jb + IB : nb;
     for (int idx = tid; idx < IB * IB; idx += NT) {
       const int a = idx % IB, j = idx / IB;
-      Rs[a * VST + j] = (a <= j) ? R[(jb + a) + (int64_t)(jb + j) * F.ld] : (T)0;
+      if (a <= j) cp_async(&Rs[a * VST + j], &R[(jb + a) + (int64_t)(jb + j) * F.ld]);
+      else Rs[a * VST + j] = (T)0;
     }
     for (int idx = tid; idx < rl * IB; idx += NT) {
       const int r = idx % rl, j = idx / rl;
-      Ps[r * VST + j] = (!tri || r <= jb + j) ? A[r + (int64_t)(jb + j) * F.ld] : (T)0;
+      if (!tri || r <= jb + j) cp_async(&Ps[r * VST + j], &A[r + (int64_t)(jb + j) * F.ld]);
+      else Ps[r * VST + j] = (T)0;
     }
+    cp_async_wait_all();
     __syncthreads();
     panel_pair<T>(Rs, Ps, rl, tri, jb, tau_s, red, bc);
     build_T<T>(Ps, rl, false, tau_s, Gs, Ts);
@@ -381,12 +553,13 @@ __global__ void __launch_bounds__(NT) k_pair_qrt(Mat<T> F, int k, int nb, TileLi
       __syncthreads();
       for (int idx = tid; idx < IB * SW; idx += NT) {
         const int a = idx % IB, c = idx / IB;
-        if (c < w) Ct[a * CST + c] = R[(jb + a) + (int64_t)(cc + c) * F.ld];
+        if (c < w) cp_async(&Ct[a * CST + c], &R[(jb + a) + (int64_t)(cc + c) * F.ld]);
       }
       for (int idx = tid; idx < rl * SW; idx += NT) {
         const int r = idx % rl, c = idx / rl;
-        if (c < w) Cb[r * CST + c] = A[r + (int64_t)(cc + c) * F.ld];
+        if (c < w) cp_async(&Cb[r * CST + c], &A[r + (int64_t)(cc + c) * F.ld]);
       }
+      cp_async_wait_all();
       __syncthreads();
       apply_block<T, SW>(nullptr, Ps, rl, Ts, Ct, Cb, w, Ws, W2s, false);
       for (int idx = tid; idx < IB * SW; idx += NT) {
@@ -428,20 +601,22 @@ __global__ void __launch_bounds__(NT) k_pair_apply(Mat<const T> F, int k, int nb
   for (int idx = tid; idx < nb * SW; idx += NT) {
     const int r = idx % nb, c = idx / nb;
     if (c < w) {
-      C1s[r * CST + c] = C1g[r + (int64_t)c * C.ld];
-      C2s[r * CST + c] = C2g[r + (int64_t)c * C.ld];
+      cp_async(&C1s[r * CST + c], &C1g[r + (int64_t)c * C.ld]);
+      cp_async(&C2s[r * CST + c], &C2g[r + (int64_t)c * C.ld]);
     }
   }
   for (int jb = 0; jb < nb; jb += IB) {
     const int rl = tri ? jb + IB : nb;
     for (int idx = tid; idx < rl * IB; idx += NT) {
       const int r = idx % rl, j = idx / rl;
-      Vs[r * VST + j] = (!tri || r <= jb + j) ? V[r + (int64_t)(jb + j) * F.ld] : (T)0;
+      if (!tri || r <= jb + j) cp_async(&Vs[r * VST + j], &V[r + (int64_t)(jb + j) * F.ld]);
+      else Vs[r * VST + j] = (T)0;
     }
     for (int idx = tid; idx < IB * IB; idx += NT) {
       const int a = idx % IB, j = idx / IB;
-      Ts[a * TST + j] = Tslot[a + (size_t)(jb + j) * IB];
+      cp_async(&Ts[a * TST + j], &Tslot[a + (size_t)(jb + j) * IB]);
     }
+    cp_async_wait_all();
     __syncthreads();
     apply_block<T, SW>(nullptr, Vs, rl, Ts, C1s + jb * CST, C2s, w, Ws, W2s, false);
   }
@@ -476,17 +651,6 @@ static void pick_sw(PlanKind kind, int nb, Fn&& fn) {
   else fn(std::integral_constant<int, 8>{});
 }
 
-// Raises the dynamic shared-memory limit of kernel K once per process (the template
-// parameter is the kernel itself, so every instantiation keeps its own flag).
-template <auto K>
-static void set_smem() {
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAX);
-    done = true;
-  }
-}
-
 template <typename T>
 void launch_geqrt(Mat<T> F, int k, int nb, TileList tl, T* Tk, int n, const uint8_t* dec,
                   cudaStream_t s) {
@@ -494,7 +658,7 @@ void launch_geqrt(Mat<T> F, int k, int nb, TileList tl, T* Tk, int n, const uint
   (void)n;
   pick_sw<T>(PLAN_GEQRT, nb, [&](auto tag) {
     constexpr int SW = decltype(tag)::value;
-    set_smem<k_geqrt<T, SW>>();
+    ensure_dyn_smem<k_geqrt<T, SW>>(Plan<T, SW>::geqrt(nb));
     {
       ProfScope ps_("k_geqrt", s);
       k_geqrt<T, SW><<<tl.count, NT, Plan<T, SW>::geqrt(nb), s>>>(F, k, nb, tl, Tk, dec);
@@ -509,7 +673,7 @@ void launch_unmqr(Mat<const T> F, int k, int nb, TileList tl, const T* Tk, int n
   (void)n;
   pick_sw<T>(PLAN_UNMQR, nb, [&](auto tag) {
     constexpr int SW = decltype(tag)::value;
-    set_smem<k_unmqr<T, SW>>();
+    ensure_dyn_smem<k_unmqr<T, SW>>(Plan<T, SW>::unmqr(nb));
     dim3 grid((unsigned)((c1 - c0 + SW - 1) / SW), (unsigned)tl.count);
     {
       ProfScope ps_("k_unmqr", s);
@@ -525,7 +689,7 @@ void launch_pair_qrt(Mat<T> F, int k, int nb, TileList tl, bool tri, T* Tk, int 
   (void)n;
   pick_sw<T>(PLAN_PAIR_QRT, nb, [&](auto tag) {
     constexpr int SW = decltype(tag)::value;
-    set_smem<k_pair_qrt<T, SW>>();
+    ensure_dyn_smem<k_pair_qrt<T, SW>>(Plan<T, SW>::pair_qrt(nb));
     {
       ProfScope ps_(tri ? "k_ttqrt" : "k_tsqrt", s);
       k_pair_qrt<T, SW><<<tl.count, NT, Plan<T, SW>::pair_qrt(nb), s>>>(F, k, nb, tl, tri, Tk, dec);
@@ -540,7 +704,7 @@ void launch_pair_apply(Mat<const T> F, int k, int nb, TileList tl, bool tri, con
   (void)n;
   pick_sw<T>(PLAN_PAIR_APPLY, nb, [&](auto tag) {
     constexpr int SW = decltype(tag)::value;
-    set_smem<k_pair_apply<T, SW>>();
+    ensure_dyn_smem<k_pair_apply<T, SW>>(Plan<T, SW>::pair_apply(nb));
     dim3 grid((unsigned)((c1 - c0 + SW - 1) / SW), (unsigned)tl.count);
     {
       ProfScope ps_(tri ? "k_ttmqr" : "k_tsmqr", s);

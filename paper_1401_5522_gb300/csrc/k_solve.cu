@@ -6,44 +6,62 @@
 namespace luqr {
 
 // ---------------------------------------------------------------- back substitution
-// One warp per right-hand side: x_k <- U_kk^-1 x_k for diagonal tile k (in place).
+// One block per right-hand side: x_k <- U_kk^-1 x_k for diagonal tile k (in place).
+// The tile is processed in 32-row blocks from the bottom: warp 0 solves the 32 x 32
+// triangle with shuffles, then all threads update the rows above.
 template <typename T>
-__global__ void k_trsv_diag(Mat<const T> U, int k, int nb, Mat<T> X, int nrhs, int* status) {
+__global__ void __launch_bounds__(256) k_trsv_diag(Mat<const T> U, int k, int nb, Mat<T> X, int nrhs,
+                                                   int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* xs_all = reinterpret_cast<T*>(smem_raw);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (j >= nrhs) return;
-  T* xs = xs_all + warp * nb;
+  T* xs = reinterpret_cast<T*>(smem_raw);
+  __shared__ int s_bad;
+  const int j = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t r0 = (int64_t)k * nb;
-  for (int r = lane; r < nb; r += 32) xs[r] = X(r0 + r, j);
-  __syncwarp();
-  for (int r = nb - 1; r >= 0; --r) {
-    const T d = U(r0 + r, r0 + r);
-    if (d == (T)0) {
-      if (lane == 0 && atomicCAS(&status[ST_CODE], 0, -4) == 0) {
-        status[ST_STEP] = k;
-        status[ST_ROW] = (int)(r0 + r);
+  for (int r = tid; r < nb; r += blockDim.x) xs[r] = X(r0 + r, j);
+  if (tid == 0) s_bad = -1;
+  __syncthreads();
+  for (int bb = nb / 32 - 1; bb >= 0; --bb) {
+    const int b0 = bb * 32;
+    if (warp == 0) {
+      T x = xs[b0 + lane];
+      int bad = -1;
+      for (int r = 31; r >= 0; --r) {
+        const T d = U(r0 + b0 + r, r0 + b0 + r);
+        if (d == (T)0) { bad = b0 + r; break; }
+        if (lane == r) x = x / d;
+        const T xr = __shfl_sync(0xffffffffu, x, r);
+        if (lane < r) x -= U(r0 + b0 + lane, r0 + b0 + r) * xr;
       }
-      return;
+      xs[b0 + lane] = x;
+      if (lane == 0 && bad >= 0) s_bad = bad;
     }
-    if (lane == 0) xs[r] = xs[r] / d;
-    __syncwarp();
-    const T xr = xs[r];
-    for (int row = lane; row < r; row += 32) xs[row] -= U(r0 + row, r0 + r) * xr;
-    __syncwarp();
+    __syncthreads();
+    if (s_bad >= 0) break;
+    for (int i = tid; i < b0; i += blockDim.x) {
+      T acc = (T)0;
+#pragma unroll 8
+      for (int q = 0; q < 32; ++q) acc += U(r0 + i, r0 + b0 + q) * xs[b0 + q];
+      xs[i] -= acc;
+    }
+    __syncthreads();
   }
-  for (int r = lane; r < nb; r += 32) X(r0 + r, j) = xs[r];
+  if (s_bad >= 0) {
+    if (tid == 0 && atomicCAS(&status[ST_CODE], 0, -4) == 0) {
+      status[ST_STEP] = k;
+      status[ST_ROW] = (int)(r0 + s_bad);
+    }
+    return;
+  }
+  for (int r = tid; r < nb; r += blockDim.x) X(r0 + r, j) = xs[r];
 }
 
 template <typename T>
 void launch_trsv_diag(Mat<const T> U, int k, int nb, Mat<T> X, int nrhs, int* status,
                       cudaStream_t s) {
-  const int wpb = 4;
   {
     ProfScope ps_("k_trsv_diag", s);
-    k_trsv_diag<T><<<(nrhs + wpb - 1) / wpb, 32 * wpb, wpb * nb * sizeof(T), s>>>(U, k, nb, X, nrhs,
-                                                                                status);
+    k_trsv_diag<T><<<nrhs, 256, nb * sizeof(T), s>>>(U, k, nb, X, nrhs, status);
   }
 }
 
@@ -252,6 +270,80 @@ void launch_axpy_update(double* x, const T* d, int64_t N, const double* scale, c
   {
     ProfScope ps_("k_axpy_update", s);
     k_axpy_update<T><<<bx, 256, 0, s>>>(x, d, N, scale);
+  }
+}
+
+// ---------------------------------------------------------------- GMRES helpers (FP64)
+// out = A v (column-major A); same chunked two-pass scheme as the residual.
+__global__ void k_matvec_reduce(const double* __restrict__ partial, int nchunk, int64_t N,
+                                double* __restrict__ out) {
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < N;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += partial[c * N + row];
+    out[row] = s;
+  }
+}
+
+void launch_matvec(const double* A, int64_t lda, int64_t N, const double* v, double* out,
+                   double* partial, int nchunk, cudaStream_t s) {
+  dim3 grid((unsigned)((N + RES_ROWS - 1) / RES_ROWS), (unsigned)nchunk);
+  {
+    ProfScope ps_("k_residual_partial", s);
+    k_residual_partial<<<grid, RES_ROWS, 0, s>>>(A, lda, N, v, partial);
+  }
+  int bx = (int)((N + 255) / 256);
+  if (bx > 2048) bx = 2048;
+  {
+    ProfScope ps_("k_matvec_reduce", s);
+    k_matvec_reduce<<<bx, 256, 0, s>>>(partial, nchunk, N, out);
+  }
+}
+
+// dots[i] = V[:, i] . w for i < cnt (V column-major, ldv); one block per i.
+__global__ void k_multidot(const double* __restrict__ V, int64_t ldv, int64_t N,
+                           const double* __restrict__ w, double* __restrict__ dots) {
+  __shared__ double red[32];
+  const double* v = V + (int64_t)blockIdx.x * ldv;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) s += v[i] * w[i];
+  s = warp_sum_d(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    dots[blockIdx.x] = t;
+  }
+}
+
+void launch_multidot(const double* V, int64_t ldv, int64_t N, int cnt, const double* w,
+                     double* dots, cudaStream_t s) {
+  if (cnt <= 0) return;
+  {
+    ProfScope ps_("k_multidot", s);
+    k_multidot<<<cnt, 512, 0, s>>>(V, ldv, N, w, dots);
+  }
+}
+
+// w <- alpha * (w - sum_{i<cnt} coef[i] V[:, i])  (coef on the device)
+__global__ void k_multiaxpy(const double* __restrict__ V, int64_t ldv, int64_t N, int cnt,
+                            const double* __restrict__ coef, double* __restrict__ w, double alpha) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    double acc = w[r];
+    for (int i = 0; i < cnt; ++i) acc -= coef[i] * V[r + (int64_t)i * ldv];
+    w[r] = alpha * acc;
+  }
+}
+
+void launch_multiaxpy(const double* V, int64_t ldv, int64_t N, int cnt, const double* coef,
+                      double* w, double alpha, cudaStream_t s) {
+  int bx = (int)((N + 255) / 256);
+  if (bx > 4096) bx = 4096;
+  {
+    ProfScope ps_("k_multiaxpy", s);
+    k_multiaxpy<<<bx, 256, 0, s>>>(V, ldv, N, cnt, coef, w, alpha);
   }
 }
 

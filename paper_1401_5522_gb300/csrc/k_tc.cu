@@ -1,0 +1,398 @@
+// Blackwell (sm_103a) tensor-core GEMM update C <- C - A B for FP32 matrices, the dense
+// contraction of the trailing updates (Alg. 2 GEMM; QR updates expressed as GEMMs).
+//
+// FP32 operands are split 3xTF32 (x = hi + lo, hi = tf32(x), lo = tf32(x - hi)) while
+// they are staged into shared memory, and each K=8 slice issues three tcgen05.mma
+// kind::tf32 instructions (lo*hi, hi*lo, hi*hi) accumulating in FP32 in tensor memory
+// (TMEM).  One CTA computes a 128 x 128 tile of C; K is consumed in 32-wide chunks,
+// double-buffered: while the MMAs of chunk c run, the CTA stages chunk c+1.
+//
+// Shared-memory operand layout: K-major, no swizzle.  A "core matrix" is 8 rows x 16
+// bytes (4 FP32 along K, 128 contiguous bytes); element (r, k) of a 128 x 32 chunk lives
+// at (r/8)*SBO + (k/4)*LBO + (r%8)*16 + (k%4)*4 with LBO = 128 B (next core matrix along
+// K) and SBO = 1024 B (next 8-row group).  MMA k-step s starts 2*LBO*s bytes in.
+//
+// Every wait on an mbarrier is bounded; on expiry the kernel records LUQR_ERR_TIMEOUT in
+// the status word, waits (bounded) for its own MMAs, frees its TMEM and returns.
+#include "internal.cuh"
+
+namespace luqr {
+
+constexpr int TC_BM = 128;      // rows of a C tile (MMA M)
+constexpr int TC_BN = 128;      // columns of a C tile (MMA N)
+constexpr int TC_BK = 32;       // K chunk
+constexpr int TC_THREADS = 256;
+constexpr uint32_t TC_LBO = 128;
+constexpr uint32_t TC_SBO = 1024;
+constexpr int TC_CHUNK_BYTES = TC_BM * TC_BK * 4;           // 16 KB per operand copy
+constexpr int TC_STAGE_BYTES = 4 * TC_CHUNK_BYTES;          // A hi/lo + B hi/lo
+constexpr int TC_SMEM = 2 * TC_STAGE_BYTES + 128;           // two stages + barriers/TMEM addr
+constexpr long long TC_SPIN_LIMIT = 20000000;               // bounded mbarrier polling
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((TC_LBO >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((TC_SBO >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version for tcgen05
+  return d;                 // base offset 0, no swizzle
+}
+
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t make_idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Returns true once the phase with the given parity has completed; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < TC_SPIN_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t kmajor_off(int r, int k) {
+  return (uint32_t)((r >> 3) * TC_SBO + (k >> 2) * TC_LBO + (r & 7) * 16 + (k & 3) * 4);
+}
+
+// Element of a (possibly transposed, possibly masked) operand.  The mask refers to the
+// source matrix P's own row/column (pr, pc): unit-lower keeps pr > pc, puts 1 on the
+// diagonal and 0 above (Householder V of GEQRT); upper keeps pr <= pc (V of TTQRT).
+__device__ __forceinline__ float tc_fetch(const float* P, int64_t ld, int64_t pr, int64_t pc,
+                                          int mask) {
+  if (mask == TC_MASK_UNIT_LOWER) {
+    if (pr == pc) return 1.f;
+    if (pr < pc) return 0.f;
+  } else if (mask == TC_MASK_UPPER) {
+    if (pr > pc) return 0.f;
+  }
+  return P[pr + pc * ld];
+}
+
+__device__ __forceinline__ void tc_put(unsigned char* hi, unsigned char* lo, uint32_t off, float x) {
+  const uint32_t h = tf32_bits(x);
+  const uint32_t l = tf32_bits(x - __uint_as_float(h));
+  *reinterpret_cast<uint32_t*>(hi + off) = h;
+  *reinterpret_cast<uint32_t*>(lo + off) = l;
+}
+
+// Stages chunk [k0, k0 + 32) of the logical operands A (M x K) and B (K x N) into one
+// stage of shared memory as hi/lo TF32 copies (zero outside the matrices).
+__device__ __forceinline__ void tc_stage(unsigned char* st, const TcArgs& a, const float* A,
+                                         const float* B, int64_t m0, int64_t n0, int k0) {
+  unsigned char* ahi = st;
+  unsigned char* alo = st + TC_CHUNK_BYTES;
+  unsigned char* bhi = st + 2 * TC_CHUNK_BYTES;
+  unsigned char* blo = st + 3 * TC_CHUNK_BYTES;
+  if (!a.a_trans) {   // A(m, k) = P[m][k]: consecutive threads walk m (contiguous)
+    for (int idx = threadIdx.x; idx < TC_BM * TC_BK; idx += TC_THREADS) {
+      const int r = idx % TC_BM, k = idx / TC_BM;
+      const int64_t gr = m0 + r;
+      const int gk = k0 + k;
+      const float x = (gr < a.M && gk < a.K) ? tc_fetch(A, a.lda, gr, gk, a.a_mask) : 0.f;
+      tc_put(ahi, alo, kmajor_off(r, k), x);
+    }
+  } else {            // A(m, k) = P[k][m]: consecutive threads walk k (contiguous)
+    for (int idx = threadIdx.x; idx < TC_BM * TC_BK; idx += TC_THREADS) {
+      const int k = idx % TC_BK, r = idx / TC_BK;
+      const int64_t gr = m0 + r;
+      const int gk = k0 + k;
+      const float x = (gr < a.M && gk < a.K) ? tc_fetch(A, a.lda, gk, gr, a.a_mask) : 0.f;
+      tc_put(ahi, alo, kmajor_off(r, k), x);
+    }
+  }
+  if (!a.b_trans) {   // B(k, n) = P[k][n]: consecutive threads walk k
+    for (int idx = threadIdx.x; idx < TC_BN * TC_BK; idx += TC_THREADS) {
+      const int k = idx % TC_BK, c = idx / TC_BK;
+      const int64_t gc = n0 + c;
+      const int gk = k0 + k;
+      const float x = (gc < a.N && gk < a.K) ? tc_fetch(B, a.ldb, gk, gc, a.b_mask) : 0.f;
+      tc_put(bhi, blo, kmajor_off(c, k), x);
+    }
+  } else {            // B(k, n) = P[n][k]: consecutive threads walk n
+    for (int idx = threadIdx.x; idx < TC_BN * TC_BK; idx += TC_THREADS) {
+      const int c = idx % TC_BN, k = idx / TC_BN;
+      const int64_t gc = n0 + c;
+      const int gk = k0 + k;
+      const float x = (gc < a.N && gk < a.K) ? tc_fetch(B, a.ldb, gc, gk, a.b_mask) : 0.f;
+      tc_put(bhi, blo, kmajor_off(c, k), x);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
+  if (a.dec != nullptr && a.dec[a.k_step] != a.want) return;
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  unsigned char* stages = smem_tc;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_tc + 2 * TC_STAGE_BYTES);   // 2 barriers
+  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(smem_tc + 2 * TC_STAGE_BYTES + 64);
+  int* last_commit = reinterpret_cast<int*>(smem_tc + 2 * TC_STAGE_BYTES + 96);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t m0 = (int64_t)blockIdx.y * TC_BM, n0 = (int64_t)blockIdx.x * TC_BN;
+  const int64_t t = blockIdx.z;
+  const float* A = a.A + t * a.sA;
+  const float* B = a.B + t * a.sB;
+  float* C = a.C + t * a.sC;
+  const float* C1 = a.C1 ? a.C1 + t * a.sC1 : nullptr;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(taddr_slot)),
+                 "r"(TC_BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    *last_commit = -1;
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *taddr_slot;
+  const uint32_t idesc = make_idesc_tf32(TC_BM, TC_BN);
+  const int nchunks = (a.K + TC_BK - 1) / TC_BK;
+  bool ok = true;
+  for (int c = 0; c < nchunks; ++c) {
+    const int buf = c & 1;
+    unsigned char* st = stages + buf * TC_STAGE_BYTES;
+    if (c >= 2) {   // the MMAs that read this stage two chunks ago must be done
+      if (!mbar_wait(&bars[buf], (uint32_t)(((c - 2) >> 1) & 1))) ok = false;
+    }
+    if (!__syncthreads_and(ok ? 1 : 0)) { ok = false; break; }
+    tc_stage(st, a, A, B, m0, n0, c * TC_BK);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      const uint32_t base = smem_u32(st);
+#pragma unroll
+      for (int s = 0; s < TC_BK / 8; ++s) {
+        const uint32_t koff = (uint32_t)s * 2 * TC_LBO;
+        const uint64_t ahi = make_desc(base + koff);
+        const uint64_t alo = make_desc(base + TC_CHUNK_BYTES + koff);
+        const uint64_t bhi = make_desc(base + 2 * TC_CHUNK_BYTES + koff);
+        const uint64_t blo = make_desc(base + 3 * TC_CHUNK_BYTES + koff);
+        const uint32_t acc0 = (c > 0 || s > 0) ? 1u : 0u;
+        tc_mma(tmem, alo, bhi, idesc, acc0);
+        tc_mma(tmem, ahi, blo, idesc, 1u);
+        tc_mma(tmem, ahi, bhi, idesc, 1u);
+      }
+      tc_commit(&bars[buf]);
+      *last_commit = c;
+    }
+  }
+  // Wait for the last committed chunk's MMAs (a commit covers every earlier MMA of the
+  // thread), also on the error path, so TMEM is released only when no MMA is in flight.
+  __syncthreads();
+  const int last = *last_commit;
+  if (last >= 0) {
+    if (!mbar_wait(&bars[last & 1], (uint32_t)((last >> 1) & 1))) ok = false;
+  }
+  tc_fence_after();
+  const bool all_ok = __syncthreads_and(ok ? 1 : 0);
+  if (all_ok) {
+    // Epilogue: warp w reads TMEM lanes 32*(w%4).. (rows), columns half (w/4) of the tile.
+    const int lane_base = (warp & 3) * 32;
+    const int col_half = warp >> 2;
+    const int64_t row = m0 + lane_base + lane;
+    for (int cc = 0; cc < TC_BN / 2; cc += 32) {
+      const int col0 = col_half * (TC_BN / 2) + cc;
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)col0, v);
+      if (row < a.M) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int64_t gc = n0 + col0 + i;
+          if (gc < a.N) {
+            if (a.epi == TC_EPI_SUB)
+              C[row + gc * a.ldc] -= v[i];
+            else if (a.epi == TC_EPI_OUT)
+              C[row + gc * a.ldc] = v[i];
+            else
+              C[row + gc * a.ldc] = v[i] + C1[row + gc * a.ldc1];
+          }
+        }
+      }
+    }
+  } else if (tid == 0 && a.status != nullptr) {
+    atomicCAS(&a.status[ST_CODE], 0, -6);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN));
+  }
+}
+
+void launch_tc(const TcArgs& a, int batch, const char* name, cudaStream_t s) {
+  if (a.M <= 0 || a.N <= 0 || a.K <= 0 || batch <= 0) return;
+  ensure_dyn_smem<k_gemm_tc>(TC_SMEM);
+  dim3 grid((unsigned)((a.N + TC_BN - 1) / TC_BN), (unsigned)((a.M + TC_BM - 1) / TC_BM),
+            (unsigned)batch);
+  {
+    ProfScope ps_(name, s);
+    k_gemm_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(a);
+  }
+}
+
+void launch_gemm_tc(const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
+                    int64_t ldc, int64_t M, int64_t N, int K, const uint8_t* dec, int k,
+                    uint8_t want, int* status, cudaStream_t s) {
+  TcArgs a{};
+  a.A = A; a.lda = lda; a.B = B; a.ldb = ldb; a.C = C; a.ldc = ldc;
+  a.M = M; a.N = N; a.K = K; a.epi = TC_EPI_SUB;
+  a.dec = dec; a.k_step = k; a.want = want; a.status = status;
+  launch_tc(a, 1, "k_gemm_tc", s);
+}
+
+// ---------------------------------------------------------------- full compact-WY T
+// Tf (nb x nb, upper triangular, column-major, ld nb) such that Q = I - V Tf V^T for all
+// nb reflectors of a tile, from the Gram matrix G = V^T V (upper part used) and the stored
+// IB x IB diagonal blocks (T slot: block b at columns b*IB.., IB rows):
+//   Tf[blk b, blk b] = T_b;  Tf[0:jb, blk b] = -Tf[0:jb, 0:jb] G[0:jb, blk b] T_b.
+// One CTA per tile of the batch; thread r owns row r of the current block column.
+__global__ void __launch_bounds__(256) k_tfull(const float* __restrict__ G, int64_t sG,
+                                               const float* __restrict__ Tslots, int64_t sT,
+                                               float* __restrict__ Tf, int64_t sTf, int nb,
+                                               const uint8_t* __restrict__ dec, int k) {
+  if (dec[k] != DEC_QR) return;
+  extern __shared__ __align__(16) float tf_smem[];
+  float(*X)[IB + 1] = reinterpret_cast<float(*)[IB + 1]>(tf_smem);                  // nb rows
+  float(*Tb)[IB + 1] = reinterpret_cast<float(*)[IB + 1]>(tf_smem + (size_t)nb * (IB + 1));
+  const int64_t t = blockIdx.x;
+  const float* g = G + t * sG;
+  const float* ts = Tslots + t * sT;
+  float* tf = Tf + t * sTf;
+  const int tid = threadIdx.x;
+  for (int jb = 0; jb < nb; jb += IB) {
+    for (int idx = tid; idx < IB * IB; idx += blockDim.x) {
+      const int a = idx % IB, j = idx / IB;
+      Tb[a][j] = ts[a + (int64_t)(jb + j) * IB];
+    }
+    for (int idx = tid; idx < jb * IB; idx += blockDim.x) {
+      const int r = idx % jb, j = idx / jb;
+      X[r][j] = g[r + (int64_t)(jb + j) * nb];
+    }
+    __syncthreads();
+    for (int r = tid; r < nb; r += blockDim.x) {
+      if (r < jb) {
+        float y[IB];
+#pragma unroll
+        for (int j = 0; j < IB; ++j) y[j] = 0.f;
+        for (int q = r; q < jb; ++q) {
+          const float tq = tf[r + (int64_t)q * nb];
+#pragma unroll
+          for (int j = 0; j < IB; ++j) y[j] += tq * X[q][j];
+        }
+#pragma unroll
+        for (int j = 0; j < IB; ++j) {
+          float z = 0.f;
+#pragma unroll
+          for (int q = 0; q <= j; ++q) z += y[q] * Tb[q][j];
+          tf[r + (int64_t)(jb + j) * nb] = -z;
+        }
+      } else if (r < jb + IB) {
+#pragma unroll
+        for (int j = 0; j < IB; ++j)
+          tf[r + (int64_t)(jb + j) * nb] = (r - jb <= j) ? Tb[r - jb][j] : 0.f;
+      } else {
+#pragma unroll
+        for (int j = 0; j < IB; ++j) tf[r + (int64_t)(jb + j) * nb] = 0.f;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void launch_tfull(const float* G, int64_t sG, const float* Tslots, int64_t sT, float* Tf,
+                  int64_t sTf, int nb, int batch, const uint8_t* dec, int k, cudaStream_t s) {
+  if (batch <= 0) return;
+  const size_t smem = sizeof(float) * ((size_t)nb + IB) * (IB + 1);
+  ensure_dyn_smem<k_tfull>(smem);
+  {
+    ProfScope ps_("k_tfull", s);
+    k_tfull<<<batch, 256, smem, s>>>(G, sG, Tslots, sT, Tf, sTf, nb, dec, k);
+  }
+}
+
+}  // namespace luqr
+
+extern "C" int luqr_gemm_sub_f32(float* C, int64_t ldc, const float* A, int64_t lda,
+                                 const float* B, int64_t ldb, int64_t M, int64_t N, int64_t K,
+                                 int* dstatus, void* stream) {
+  if (!C || !A || !B || M < 0 || N < 0 || K < 0 || K > (1 << 30) || ldc < M || lda < M ||
+      ldb < K)
+    return -1;
+  luqr::launch_gemm_tc(A, lda, B, ldb, C, ldc, M, N, (int)K, nullptr, 0, 0, dstatus,
+                       static_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}

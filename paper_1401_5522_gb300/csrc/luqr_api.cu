@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/luqr.h"
@@ -40,11 +41,26 @@ struct luqr_handle {
   int* status = nullptr;
   uint8_t* forced = nullptr;
   std::vector<char> injected;
+  // look-ahead: the bulk trailing update of step k runs on upd_stream while the caller's
+  // stream factors panel k+1 (events ev_fact / ev_rest order the two streams)
+  cudaStream_t upd_stream = nullptr;
+  std::vector<cudaEvent_t> ev_fact, ev_rest;
+  cudaEvent_t ev_start = nullptr;
+  // FP32 tensor-core trailing updates: W workspace (Npad x Wc, same layout as the trailing
+  // matrix), Gram matrices, full compact-WY T and V T^T per tile (double-buffered by step)
+  bool use_tc = false;      // tcgen05 GEMM for LU trailing updates
+  bool use_tc_qr = false;   // tcgen05 GEMMs for QR trailing updates
+  float* Wbuf = nullptr;
+  float* Gbuf = nullptr;
+  float* Tfull[2] = {nullptr, nullptr};
+  float* Vt[2] = {nullptr, nullptr};
   // second pass / refinement scratch
   void* rhs_ws = nullptr;
   int rhs_cap = 0;
   double* ref = nullptr;    // x, r, scalars, partial sums
   int ref_chunks = 0;
+  double* gm = nullptr;     // GMRES: basis (N x (restart+1)), work vector, dot buffers
+  int gm_restart = 0;
   size_t elt = 8;
 };
 
@@ -62,21 +78,124 @@ size_t t_step_elems(const luqr_handle* h) { return (size_t)h->n * 2 * t_block_el
 // Enqueues the QR step of panel k along the handle's tree.  factor = true factors the
 // panel tiles in F and applies to columns [c0, c1) of C; factor = false only applies
 // the stored transformations to C (second pass).
+// Tensor-core (FP32) helpers of the QR step: per tile of a tile list, G = V^T V, the full
+// compact-WY T (k_tfull) and Vt = V T^T at factor time; at apply time
+//   single (UNMQR):  W = V^T C;            C -= Vt W
+//   pair (TS/TT):    W = C1 + V2^T C2;     C1 -= T^T W;   C2 -= Vt W
+void tc_factor_extra(luqr_handle* h, int k, TileList tl, int kind, int mask, cudaStream_t s) {
+  const int nb = h->nb;
+  const int64_t ld = h->Npad, nb2 = (int64_t)nb * nb;
+  float* W = static_cast<float*>(h->W);
+  const float* V0 = W + (int64_t)tl.i0 * nb + (int64_t)k * nb * ld;
+  const int64_t slot0 = ((int64_t)tl.i0 * 2 + kind) * nb2, sslot = (int64_t)tl.istride * 2 * nb2;
+  float* Tf = h->Tfull[k & 1];
+  float* Vt = h->Vt[k & 1];
+  TcArgs a{};
+  a.dec = h->dec; a.k_step = k; a.want = DEC_QR; a.status = h->status;
+  a.M = nb; a.N = nb; a.K = nb; a.epi = TC_EPI_OUT;
+  // G = V^T V
+  a.A = V0; a.lda = ld; a.sA = (int64_t)tl.istride * nb; a.a_trans = 1; a.a_mask = mask;
+  a.B = V0; a.ldb = ld; a.sB = (int64_t)tl.istride * nb; a.b_trans = 0; a.b_mask = mask;
+  a.C = h->Gbuf + slot0; a.ldc = nb; a.sC = sslot;
+  launch_tc(a, tl.count, "k_tc_gram", s);
+  const float* Tsl = static_cast<const float*>(h->Tbuf) + (size_t)k * t_step_elems(h) +
+                     ((size_t)tl.i0 * 2 + kind) * t_block_elems(h);
+  launch_tfull(h->Gbuf + slot0, sslot, Tsl, (int64_t)tl.istride * 2 * (int64_t)t_block_elems(h),
+               Tf + slot0, sslot, nb, tl.count, h->dec, k, s);
+  // Vt = V T^T
+  a.A = V0; a.lda = ld; a.sA = (int64_t)tl.istride * nb; a.a_trans = 0; a.a_mask = mask;
+  a.B = Tf + slot0; a.ldb = nb; a.sB = sslot; a.b_trans = 1; a.b_mask = TC_MASK_NONE;
+  a.C = Vt + slot0; a.ldc = nb; a.sC = sslot;
+  launch_tc(a, tl.count, "k_tc_vt", s);
+}
+
+void tc_apply_single(luqr_handle* h, int k, TileList tl, Mat<float> C, int64_t c0, int64_t c1,
+                     cudaStream_t s) {
+  const int nb = h->nb;
+  const int64_t ld = h->Npad, nb2 = (int64_t)nb * nb;
+  float* W = static_cast<float*>(h->W);
+  const int64_t slot0 = ((int64_t)tl.i0 * 2 + 0) * nb2, sslot = (int64_t)tl.istride * 2 * nb2;
+  const int64_t rstride = (int64_t)tl.istride * nb;
+  TcArgs a{};
+  a.dec = h->dec; a.k_step = k; a.want = DEC_QR; a.status = h->status;
+  a.M = nb; a.N = c1 - c0; a.K = nb;
+  // W = V^T C
+  a.A = W + (int64_t)tl.i0 * nb + (int64_t)k * nb * ld; a.lda = ld; a.sA = rstride;
+  a.a_trans = 1; a.a_mask = TC_MASK_UNIT_LOWER;
+  a.B = C.p + (int64_t)tl.i0 * nb + c0 * C.ld; a.ldb = C.ld; a.sB = rstride;
+  a.C = h->Wbuf + (int64_t)tl.i0 * nb + c0 * ld; a.ldc = ld; a.sC = rstride; a.epi = TC_EPI_OUT;
+  launch_tc(a, tl.count, "k_tc_unmqr_w", s);
+  // C -= Vt W
+  a.A = h->Vt[k & 1] + slot0; a.lda = nb; a.sA = sslot; a.a_trans = 0; a.a_mask = TC_MASK_NONE;
+  a.B = h->Wbuf + (int64_t)tl.i0 * nb + c0 * ld; a.ldb = ld; a.sB = rstride;
+  a.C = C.p + (int64_t)tl.i0 * nb + c0 * C.ld; a.ldc = C.ld; a.sC = rstride; a.epi = TC_EPI_SUB;
+  launch_tc(a, tl.count, "k_tc_unmqr_c", s);
+}
+
+void tc_apply_pair(luqr_handle* h, int k, TileList tl, bool tri, Mat<float> C, int64_t c0,
+                   int64_t c1, cudaStream_t s) {
+  const int nb = h->nb;
+  const int64_t ld = h->Npad, nb2 = (int64_t)nb * nb;
+  float* W = static_cast<float*>(h->W);
+  const int64_t slot0 = ((int64_t)tl.i0 * 2 + 1) * nb2, sslot = (int64_t)tl.istride * 2 * nb2;
+  const int64_t rstride = (int64_t)tl.istride * nb;
+  const int64_t i0r = (int64_t)tl.i0 * nb, e0r = (int64_t)(tl.i0 - tl.eoff) * nb;
+  float* Wp = h->Wbuf + i0r + c0 * ld;
+  TcArgs a{};
+  a.dec = h->dec; a.k_step = k; a.want = DEC_QR; a.status = h->status;
+  a.M = nb; a.N = c1 - c0; a.K = nb;
+  // W = C1 + V2^T C2
+  a.A = W + i0r + (int64_t)k * nb * ld; a.lda = ld; a.sA = rstride; a.a_trans = 1;
+  a.a_mask = tri ? TC_MASK_UPPER : TC_MASK_NONE;
+  a.B = C.p + i0r + c0 * C.ld; a.ldb = C.ld; a.sB = rstride;
+  a.C1 = C.p + e0r + c0 * C.ld; a.ldc1 = C.ld; a.sC1 = rstride;
+  a.C = Wp; a.ldc = ld; a.sC = rstride; a.epi = TC_EPI_ADD_OUT;
+  launch_tc(a, tl.count, tri ? "k_tc_ttmqr_w" : "k_tc_tsmqr_w", s);
+  a.C1 = nullptr;
+  // C1 -= T^T W
+  a.A = h->Tfull[k & 1] + slot0; a.lda = nb; a.sA = sslot; a.a_trans = 1; a.a_mask = TC_MASK_NONE;
+  a.B = Wp; a.ldb = ld; a.sB = rstride;
+  a.C = C.p + e0r + c0 * C.ld; a.ldc = C.ld; a.sC = rstride; a.epi = TC_EPI_SUB;
+  launch_tc(a, tl.count, tri ? "k_tc_ttmqr_c1" : "k_tc_tsmqr_c1", s);
+  // C2 -= Vt W
+  a.A = h->Vt[k & 1] + slot0; a.lda = nb; a.sA = sslot; a.a_trans = 0;
+  a.C = C.p + i0r + c0 * C.ld;
+  launch_tc(a, tl.count, tri ? "k_tc_ttmqr_c2" : "k_tc_tsmqr_c2", s);
+}
+
 template <typename T>
-void enqueue_qr(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, bool factor) {
-  cudaStream_t s = h->stream;
+void enqueue_qr(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, bool do_factor,
+                bool do_apply, cudaStream_t s, bool tc = false) {
   const int n = h->n, nb = h->nb, m = n - 1 - k;
   Mat<T> F{wsT<T>(h), h->Npad};
   Mat<const T> Fc{wsT<T>(h), h->Npad};
   T* Tk = static_cast<T*>(h->Tbuf) + (size_t)k * t_step_elems(h);
   const uint8_t* dec = h->dec;
+  constexpr bool is_f32 = std::is_same<T, float>::value;
+  tc = tc && is_f32 && h->use_tc_qr;
   auto single = [&](TileList tl) {
-    if (factor) launch_geqrt<T>(F, k, nb, tl, Tk, n, dec, s);
-    launch_unmqr<T>(Fc, k, nb, tl, Tk, n, C, c0, c1, dec, s);
+    if (do_factor) {
+      launch_geqrt<T>(F, k, nb, tl, Tk, n, dec, s);
+      if (tc) tc_factor_extra(h, k, tl, 0, TC_MASK_UNIT_LOWER, s);
+    }
+    if (do_apply) {
+      if constexpr (is_f32) {
+        if (tc) { tc_apply_single(h, k, tl, C, c0, c1, s); return; }
+      }
+      launch_unmqr<T>(Fc, k, nb, tl, Tk, n, C, c0, c1, dec, s);
+    }
   };
   auto pair = [&](TileList tl, bool tri) {
-    if (factor) launch_pair_qrt<T>(F, k, nb, tl, tri, Tk, n, dec, s);
-    launch_pair_apply<T>(Fc, k, nb, tl, tri, Tk, n, C, c0, c1, dec, s);
+    if (do_factor) {
+      launch_pair_qrt<T>(F, k, nb, tl, tri, Tk, n, dec, s);
+      if (tc) tc_factor_extra(h, k, tl, 1, tri ? TC_MASK_UPPER : TC_MASK_NONE, s);
+    }
+    if (do_apply) {
+      if constexpr (is_f32) {
+        if (tc) { tc_apply_pair(h, k, tl, tri, C, c0, c1, s); return; }
+      }
+      launch_pair_apply<T>(Fc, k, nb, tl, tri, Tk, n, C, c0, c1, dec, s);
+    }
   };
   if (h->tree == LUQR_TREE_FLAT_TS) {
     single(TileList{k, 1, 1, 0});
@@ -105,8 +224,8 @@ void enqueue_qr(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, bool fa
 
 // ---------------------------------------------------------------- LU step on a target
 template <typename T>
-void enqueue_lu_apply(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1) {
-  cudaStream_t s = h->stream;
+void enqueue_lu_apply(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, cudaStream_t s,
+                      bool tc = false) {
   const int nb = h->nb;
   const int64_t r0 = (int64_t)k * nb, r1 = r0 + nb, ld = h->Npad;
   T* W = wsT<T>(h);
@@ -115,12 +234,19 @@ void enqueue_lu_apply(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1) {
   Mat<const T> Ablk{W + r1 + r0 * ld, ld};
   Mat<const T> Brow{C.p + r0 + c0 * C.ld, C.ld};
   Mat<T> Cblk{C.p + r1 + c0 * C.ld, C.ld};
+  if constexpr (std::is_same<T, float>::value) {
+    if (tc && h->use_tc) {
+      launch_gemm_tc(Ablk.p, ld, Brow.p, C.ld, Cblk.p, C.ld, h->Npad - r1, c1 - c0, nb, h->dec, k,
+                     DEC_LU, h->status, s);
+      return;
+    }
+  }
   launch_gemm_update<T>(Ablk, Brow, Cblk, h->Npad - r1, c1 - c0, nb, h->dec, k, DEC_LU, s);
 }
 
 template <typename T>
 void enqueue_factor(luqr_handle* h) {
-  cudaStream_t s = h->stream;
+  cudaStream_t s = h->stream, su = h->upd_stream;
   const int n = h->n, nb = h->nb;
   const int64_t ld = h->Npad;
   T* W = wsT<T>(h);
@@ -128,9 +254,17 @@ void enqueue_factor(luqr_handle* h) {
   Mat<T> F{W, ld};
   const bool need_inv = (h->forced == nullptr) &&
                         (h->criterion == LUQR_MAX || h->criterion == LUQR_SUM) && h->alpha != 0.0;
+  cudaEventRecord(h->ev_start, s);
+  cudaStreamWaitEvent(su, h->ev_start, 0);
   for (int k = 0; k < n; ++k) {
     const int64_t r0 = (int64_t)k * nb, r1 = r0 + nb;
-    if (h->injected[k]) launch_scale_rows<T>(W, ld, r0, nb, r0, h->Wc, std::ldexp(1.0, -27), s);
+    const int64_t la_end = std::min<int64_t>(r1 + nb, h->Npad);   // look-ahead column k+1
+    // ---- panel k on the caller's stream (column k is complete: see the waits below)
+    if (h->injected[k]) {
+      // the injected row spans every column >= k: wait for the previous bulk update
+      if (k > 0) cudaStreamWaitEvent(s, h->ev_rest[k - 1], 0);
+      launch_scale_rows<T>(W, ld, r0, nb, r0, h->Wc, std::ldexp(1.0, -27), s);
+    }
     launch_panel_stats<T>(W, ld, k, n, nb, h->norms + (size_t)k * n, h->local, h->away, h->status,
                           s);
     launch_getrf<T>(W, ld, k, nb, S, h->piv_s, h->status, s);
@@ -139,14 +273,27 @@ void enqueue_factor(luqr_handle* h) {
                   h->norms + (size_t)k * n, h->colsum, h->local, h->away,     h->forced,
                   h->dec,   h->margin, h->lhs,   h->rhs,       h->status};
     launch_decide<T>(da, S, s);
-    // ---- LU branch (Alg. 2)
+    // ---- factor the panel: LU (Alg. 2: commit + TRSM) or QR (GEQRT + TS/TT chain)
     launch_lu_commit<T>(W, ld, k, nb, S, h->piv_s, h->piv_all + (size_t)k * nb, h->dec, s);
     Mat<const T> LU{W + r0 + r0 * ld, ld};
     launch_trsm<T>(LU, nb, F, r1, h->Npad, r0, h->dec, k, s);
-    enqueue_lu_apply<T>(h, k, F, r1, h->Wc);
-    // ---- QR branch (Alg. 3 + Alg. 4)
-    enqueue_qr<T>(h, k, F, r1, h->Wc, true);
+    enqueue_qr<T>(h, k, F, 0, 0, true, false, s, true);
+    cudaEventRecord(h->ev_fact[k], s);
+    // ---- bulk update of columns >= k+2 (and b) on the update stream
+    if (la_end < h->Wc) {
+      cudaStreamWaitEvent(su, h->ev_fact[k], 0);
+      enqueue_lu_apply<T>(h, k, F, la_end, h->Wc, su, true);
+      enqueue_qr<T>(h, k, F, la_end, h->Wc, false, true, su, true);
+    }
+    cudaEventRecord(h->ev_rest[k], su);
+    // ---- look-ahead: column k+1 needs step k-1's bulk update, then step k's transform
+    if (r1 < la_end) {
+      if (k > 0) cudaStreamWaitEvent(s, h->ev_rest[k - 1], 0);
+      enqueue_lu_apply<T>(h, k, F, r1, la_end, s, true);
+      enqueue_qr<T>(h, k, F, r1, la_end, false, true, s, true);
+    }
   }
+  cudaStreamWaitEvent(s, h->ev_rest[n - 1], 0);
 }
 
 template <typename T>
@@ -164,8 +311,8 @@ void enqueue_replay(luqr_handle* h, Mat<T> X, int nrhs) {
   for (int k = 0; k < h->n; ++k) {
     const int64_t r0 = (int64_t)k * h->nb;
     if (h->injected[k]) launch_scale_rows<T>(X.p, X.ld, r0, h->nb, 0, nrhs, std::ldexp(1.0, -27), h->stream);
-    enqueue_lu_apply<T>(h, k, X, 0, nrhs);
-    enqueue_qr<T>(h, k, X, 0, nrhs, false);
+    enqueue_lu_apply<T>(h, k, X, 0, nrhs, h->stream);
+    enqueue_qr<T>(h, k, X, 0, nrhs, false, true, h->stream);
   }
   enqueue_backsolve<T>(h, X, nrhs);
 }
@@ -193,9 +340,14 @@ int solve_impl(luqr_handle* h, double* db, int nrhs, int64_t ldb, const double* 
 
 void free_handle(luqr_handle* h) {
   if (!h) return;
-  void* ptrs[] = {h->W,     h->Tbuf,   h->S,    h->piv_s, h->piv_all, h->norms, h->local,
-                  h->away,  h->colsum, h->dec,  h->margin, h->lhs,    h->rhs,   h->status,
-                  h->forced, h->rhs_ws, h->ref};
+  for (cudaEvent_t e : h->ev_fact) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_rest) if (e) cudaEventDestroy(e);
+  if (h->ev_start) cudaEventDestroy(h->ev_start);
+  if (h->upd_stream) cudaStreamDestroy(h->upd_stream);
+  void* ptrs[] = {h->W,      h->Tbuf,     h->S,        h->piv_s, h->piv_all, h->norms,
+                  h->local,  h->away,     h->colsum,   h->dec,   h->margin,  h->lhs,
+                  h->rhs,    h->status,   h->forced,   h->rhs_ws, h->ref,    h->Wbuf,
+                  h->Gbuf,   h->Tfull[0], h->Tfull[1], h->Vt[0], h->Vt[1], h->gm};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -213,6 +365,130 @@ int read_status(luqr_handle* h, int* st3) {
 
 }  // namespace
 
+// Preconditioner of GMRES-IR: out = M^-1 in with M the handle's factorization (second
+// pass in the factorization's precision, input scaled by ||in||_inf on the device).
+template <typename T>
+void precond(luqr_handle* h, const double* in, double* out, double* scal) {
+  launch_vec_absmax(in, h->N, scal, h->stream);
+  solve_impl<T>(h, const_cast<double*>(in), 1, h->N, scal);
+  cudaMemsetAsync(out, 0, sizeof(double) * h->N, h->stream);
+  launch_axpy_update<T>(out, static_cast<T*>(h->rhs_ws), h->N, scal, h->stream);
+}
+
+template <typename T>
+int refine_gmres_impl(luqr_handle* h, const double* dA, int64_t lda, const double* db, double* dx,
+                      double tol, int max_iter, int restart, int* iters, double* eta) {
+  cudaStream_t s = h->stream;
+  const int64_t N = h->N;
+  const int nchunk = (int)((N + 511) / 512);
+  if (!h->ref || h->ref_chunks < nchunk) {
+    if (h->ref) cudaFree(h->ref);
+    h->ref = nullptr;
+    cudaError_t e = cudaMalloc(&h->ref, sizeof(double) * ((size_t)N * (nchunk + 1) + 8));
+    if (e != cudaSuccess) return cuda_err(e);
+    h->ref_chunks = nchunk;
+  }
+  if (!h->gm || h->gm_restart < restart) {
+    if (h->gm) cudaFree(h->gm);
+    h->gm = nullptr;
+    cudaError_t e = cudaMalloc(&h->gm, sizeof(double) * ((size_t)N * (restart + 2) + 4 * (restart + 2) + 16));
+    if (e != cudaSuccess) return cuda_err(e);
+    h->gm_restart = restart;
+  }
+  int st = ensure_rhs(h, 1);
+  if (st) return st;
+  double* r = h->ref;
+  double* partial = r + N;
+  double* scal = partial + (size_t)N * nchunk;   // [0] ||A|| [1] ||r|| [2] ||x|| [3] ||b|| [4] pc
+  double* V = h->gm;                             // N x (restart + 1)
+  double* tmp = V + (size_t)N * (restart + 1);   // N
+  double* dots = tmp + N;                        // 2 x (restart + 2)
+  double* dots2 = dots + (restart + 2);
+  double* coef = dots2 + (restart + 2);
+  launch_row_abs_sum_max(dA, lda, N, partial, nchunk, scal + 0, s);
+  launch_vec_absmax(db, N, scal + 3, s);
+  cudaMemsetAsync(dx, 0, sizeof(double) * N, s);
+  cudaMemcpyAsync(r, db, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+  std::vector<double> H((size_t)(restart + 1) * restart), g(restart + 1), cs(restart), sn(restart),
+      hv(restart + 2), hv2(restart + 2), y(restart);
+  int total = 0;
+  double e_it = INFINITY, best = INFINITY;
+  for (int outer = 0; outer <= max_iter; ++outer) {
+    // z0 = M^-1 r, v0 = z0 / beta
+    precond<T>(h, r, V, scal + 4);
+    launch_multidot(V, N, N, 1, V, dots, s);
+    double nrm2;
+    cudaMemcpyAsync(&nrm2, dots, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LUQR_ERR_CUDA;
+    const double beta = std::sqrt(nrm2);
+    int jend = 0;
+    if (beta > 0.0 && std::isfinite(beta)) {
+      launch_multiaxpy(V, N, N, 0, dots, V, 1.0 / beta, s);
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      for (int j = 0; j < restart; ++j) {
+        double* vj = V + (size_t)N * j;
+        double* w = V + (size_t)N * (j + 1);
+        launch_matvec(dA, lda, N, vj, tmp, partial, nchunk, s);
+        precond<T>(h, tmp, w, scal + 4);
+        // classical Gram-Schmidt, twice
+        launch_multidot(V, N, N, j + 1, w, dots, s);
+        launch_multiaxpy(V, N, N, j + 1, dots, w, 1.0, s);
+        launch_multidot(V, N, N, j + 1, w, dots2, s);
+        launch_multiaxpy(V, N, N, j + 1, dots2, w, 1.0, s);
+        launch_multidot(w, N, N, 1, w, dots2 + j + 1, s);
+        cudaMemcpyAsync(hv.data(), dots, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(hv2.data(), dots2, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) return LUQR_ERR_CUDA;
+        ++total;
+        double* Hj = H.data() + (size_t)j * (restart + 1);
+        for (int i = 0; i <= j; ++i) Hj[i] = hv[i] + hv2[i];
+        const double hn = std::sqrt(std::max(hv2[j + 1], 0.0));
+        Hj[j + 1] = hn;
+        if (hn > 0.0) launch_multiaxpy(V, N, N, 0, dots, w, 1.0 / hn, s);
+        for (int i = 0; i < j; ++i) {   // previous rotations
+          const double a = Hj[i], b = Hj[i + 1];
+          Hj[i] = cs[i] * a + sn[i] * b;
+          Hj[i + 1] = -sn[i] * a + cs[i] * b;
+        }
+        const double a = Hj[j], b = Hj[j + 1];
+        const double rr = std::hypot(a, b);
+        cs[j] = rr > 0.0 ? a / rr : 1.0;
+        sn[j] = rr > 0.0 ? b / rr : 0.0;
+        Hj[j] = rr;
+        Hj[j + 1] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        jend = j + 1;
+        if (std::fabs(g[j + 1]) <= 1e-10 * beta || hn == 0.0) break;
+      }
+      for (int i = jend - 1; i >= 0; --i) {   // back substitution on the rotated H
+        double acc = g[i];
+        for (int q = i + 1; q < jend; ++q) acc -= H[(size_t)q * (restart + 1) + i] * y[q];
+        const double d = H[(size_t)i * (restart + 1) + i];
+        y[i] = d != 0.0 ? acc / d : 0.0;
+      }
+      for (int i = 0; i < jend; ++i) y[i] = -y[i];
+      cudaMemcpyAsync(coef, y.data(), sizeof(double) * jend, cudaMemcpyHostToDevice, s);
+      launch_multiaxpy(V, N, N, jend, coef, dx, 1.0, s);   // x <- x + V y
+    }
+    launch_residual(dA, lda, N, dx, db, r, partial, nchunk, s);
+    launch_vec_absmax(r, N, scal + 1, s);
+    launch_vec_absmax(dx, N, scal + 2, s);
+    double host[4];
+    cudaMemcpyAsync(host, scal, sizeof(host), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LUQR_ERR_CUDA;
+    e_it = host[1] / (host[0] * host[2] + host[3]);
+    best = std::min(best, e_it);
+    if (!(e_it > tol) || jend == 0) break;
+  }
+  if (iters) *iters = total;
+  if (eta) *eta = e_it;
+  int code = read_status(h, nullptr);
+  if (code) return code;
+  return (e_it <= tol) ? LUQR_OK : LUQR_ERR_NOT_CONVERGED;
+}
+
 // ======================================================================= C ABI
 extern "C" {
 
@@ -228,6 +504,7 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   if (!(alpha >= 0.0)) return LUQR_ERR_INVALID;   // rejects NaN too
   if (criterion < LUQR_MAX || criterion > LUQR_FORCE_QR) return LUQR_ERR_INVALID;
   if (o.tree < 0 || o.tree > 2 || o.precision < 0 || o.precision > 1) return LUQR_ERR_INVALID;
+  if (o.fp32_kernels < 0 || o.fp32_kernels > 2) return LUQR_ERR_INVALID;
   if (o.mumps_mode < 0 || o.mumps_mode > 1 || o.n_inject < 0) return LUQR_ERR_INVALID;
   luqr_handle* h = new (std::nothrow) luqr_handle();
   if (!h) return LUQR_ERR_NOMEM;
@@ -272,6 +549,25 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   A((void**)&h->rhs, sizeof(double) * n);
   A((void**)&h->status, sizeof(int) * ST_WORDS);
   if (o.forced) A((void**)&h->forced, (size_t)n);
+  h->use_tc = (h->prec == LUQR_PREC_FP32) && (o.fp32_kernels != 1);
+  h->use_tc_qr = (h->prec == LUQR_PREC_FP32) && (o.fp32_kernels == 2);
+  if (h->use_tc_qr) {
+    const size_t slots = (size_t)n * 2 * nb * nb;
+    A((void**)&h->Wbuf, sizeof(float) * (size_t)h->Npad * h->Wc);
+    A((void**)&h->Gbuf, sizeof(float) * slots);
+    for (int q = 0; q < 2; ++q) {
+      A((void**)&h->Tfull[q], sizeof(float) * slots);
+      A((void**)&h->Vt[q], sizeof(float) * slots);
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->upd_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
+  h->ev_fact.assign(n, nullptr);
+  h->ev_rest.assign(n, nullptr);
+  for (int q = 0; q < n && e == cudaSuccess; ++q) {
+    e = cudaEventCreateWithFlags(&h->ev_fact[q], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_rest[q], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     free_handle(h);
     cudaGetLastError();
@@ -379,6 +675,17 @@ int luqr_refine(luqr_handle_t h, const double* dA, int64_t lda, const double* db
   if (eta) *eta = best;
   int code = read_status(h, nullptr);
   return code ? code : LUQR_ERR_NOT_CONVERGED;
+}
+
+int luqr_refine_gmres(luqr_handle_t h, const double* dA, int64_t lda, const double* db, double* dx,
+                      double tol, int max_iter, int restart, int* iters, double* eta, void* stream) {
+  if (!h || !dA || !db || !dx || lda < h->N || max_iter < 0 || restart < 1 || restart > 200 ||
+      !(tol >= 0.0))
+    return LUQR_ERR_INVALID;
+  h->stream = static_cast<cudaStream_t>(stream);
+  if (h->prec == LUQR_PREC_FP64)
+    return refine_gmres_impl<double>(h, dA, lda, db, dx, tol, max_iter, restart, iters, eta);
+  return refine_gmres_impl<float>(h, dA, lda, db, dx, tol, max_iter, restart, iters, eta);
 }
 
 int luqr_decisions(luqr_handle_t h, uint8_t* dec, double* margin, int* n_out) {

@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
     _fields_ = [("tree", ctypes.c_int), ("group", ctypes.c_int), ("precision", ctypes.c_int),
                 ("mumps_mode", ctypes.c_int), ("forced", ctypes.POINTER(ctypes.c_uint8)),
                 ("inject", ctypes.POINTER(ctypes.c_int)), ("n_inject", ctypes.c_int),
-                ("reserved", ctypes.c_int * 9)]
+                ("fp32_kernels", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
 
 
 _lib = None
@@ -52,6 +52,9 @@ _SIGS = {
     "luqr_solve": (ctypes.c_int, [_P, _P, ctypes.c_int, _I64, _P]),
     "luqr_refine": (ctypes.c_int, [_P, _P, _I64, _P, _P, ctypes.c_double, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _P]),
+    "luqr_refine_gmres": (ctypes.c_int, [_P, _P, _I64, _P, _P, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_double), _P]),
     "luqr_decisions": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
     "luqr_step_stats": (ctypes.c_int, [_P, _P, _P]),
     "luqr_factor_data": (ctypes.c_int, [_P, _P, _I64]),
@@ -64,6 +67,7 @@ _SIGS = {
     "luqr_profile": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "luqr_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    "luqr_gemm_sub_f32": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _I64, _I64, _I64, _I64, _P, _P]),
     "luqr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "luqr_version": (ctypes.c_char_p, []),
 }
@@ -195,6 +199,17 @@ class Handle:
                                _stream_ptr(stream))
         return st, it.value, eta.value
 
+    def refine_gmres(self, A, b, x, tol=1e-13, max_iter=10, restart=30, stream=None):
+        """GMRES-IR; returns (status, total GMRES iterations, eta)."""
+        lda = _check_matrix(A)
+        it = ctypes.c_int()
+        eta = ctypes.c_double()
+        st = lib().luqr_refine_gmres(self._ptr(), ctypes.c_void_p(A.data_ptr()), lda,
+                                     ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                     float(tol), int(max_iter), int(restart), ctypes.byref(it),
+                                     ctypes.byref(eta), _stream_ptr(stream))
+        return st, it.value, eta.value
+
     def close(self):
         if self._h:
             lib().luqr_destroy(self._h)
@@ -214,7 +229,8 @@ class Handle:
 
 
 def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
-           precision="fp64", mumps_mode=0, forced=None, inject=None, stream=None):
+           precision="fp64", mumps_mode=0, forced=None, inject=None, stream=None,
+           fp32_kernels="default"):
     """luqr_factor on a column-major float64 CUDA matrix; b (if given) is overwritten by x."""
     N = A.shape[0]
     lda = _check_matrix(A)
@@ -224,6 +240,7 @@ def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
     opt.group = int(group)
     opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     opt.mumps_mode = int(mumps_mode)
+    opt.fp32_kernels = {"default": 0, "cuda": 1, "tensor": 2}[fp32_kernels]
     keep = []
     if forced is not None:
         fa = np.ascontiguousarray(np.asarray(forced, dtype=np.uint8))
@@ -265,3 +282,21 @@ def profile_read(cap=64):
     ms = (ctypes.c_double * cap)()
     n = L.luqr_profile_read(names, launches, ms, cap)
     return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(n)}
+
+
+def gemm_sub_f32(C, A, B, status=None, stream=None):
+    """C <- C - A B on the tensor cores (FP32, column-major CUDA tensors)."""
+    import torch
+    for t in (C, A, B):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.dim() == 2 and t.stride(0) == 1):
+            raise TypeError("C, A, B must be column-major float32 CUDA matrices")
+    M, N = C.shape
+    K = A.shape[1]
+    ld = lambda t: max(t.stride(1), t.shape[0])
+    st = lib().luqr_gemm_sub_f32(ctypes.c_void_p(C.data_ptr()), ld(C), ctypes.c_void_p(A.data_ptr()),
+                                 ld(A), ctypes.c_void_p(B.data_ptr()), ld(B), M, N, K,
+                                 None if status is None else ctypes.c_void_p(status.data_ptr()),
+                                 _stream_ptr(stream))
+    if st != OK:
+        raise LuqrError(st, "luqr_gemm_sub_f32")
+    return C

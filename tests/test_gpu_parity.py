@@ -210,3 +210,37 @@ def test_fp32_refinement_reaches_fp64_accuracy(tree):
     assert st == 0, (st, iters, eta)
     assert eta <= 1e-14
     assert O.backward_error(A, x.cpu().numpy(), b.cpu().numpy()) <= 1e-13
+
+
+@pytest.mark.parametrize("tree,crit,alpha,dd", [("binary_tt", "max", 100.0, False),
+                                                ("grouped", "force_qr", 0.0, False),
+                                                ("flat_ts", "force_lu", 0.0, True),
+                                                ("flat_ts", "max", 3000.0, False),
+                                                ("grouped", "sum", 8000.0, False)])
+def test_fp32_tensor_core_updates_match_cuda_core_updates(tree, crit, alpha, dd):
+    """The tcgen05 (3xTF32) trailing updates and the CUDA-core ones compute the same FP32
+    factorization up to rounding: identical decisions and refinement to 1e-14 everywhere;
+    U compared element-wise where no pivot choice can flip (QR-only runs, and all-LU on a
+    diagonally dominant matrix).  In mixed runs a near-tie in a later GETRF's pivot search
+    can pick the other row under a 1e-6 perturbation: a different, equally valid U."""
+    luqr = L()
+    N, nb = 768, 64
+    A = gauss(N, 12) + (4.0 * np.sqrt(N) * np.eye(N) if dd else 0.0)
+    dA = cuda_colmajor(A)
+    h1 = luqr.factor(dA, nb, crit, alpha, precision="fp32", tree=tree, group=3,
+                     fp32_kernels="tensor")
+    h2 = luqr.factor(dA, nb, crit, alpha, precision="fp32", tree=tree, group=3,
+                     fp32_kernels="cuda")
+    d1, _ = h1.decisions()
+    d2, _ = h2.decisions()
+    assert np.array_equal(d1, d2)
+    if crit in ("force_qr", "force_lu") or np.all(d1[:-1] == 0):
+        U1 = np.triu(h1.factor_data()[:N, :N])
+        U2 = np.triu(h2.factor_data()[:N, :N])
+        rho = max(1.0, np.max(np.abs(U2)) / np.max(np.abs(A)))
+        assert np.max(np.abs(U1 - U2)) <= 2e-4 * rho * np.max(np.abs(U2))
+    b = torch.from_numpy(A @ np.ones(N)).cuda()
+    for h in (h1, h2):
+        x = torch.zeros(N, dtype=torch.float64, device="cuda")
+        st, iters, eta = h.refine(dA, b, x, tol=1e-14, max_iter=20)
+        assert st == 0 and eta <= 1e-14, (st, iters, eta)
