@@ -174,8 +174,15 @@ struct TcArgs {
   int64_t M, N; int K; int epi;
   const uint8_t* dec; int k_step; uint8_t want;
   int* status;
+  const unsigned char* Apk; int64_t sApk;   // packed A (launch_tc2)
 };
 void launch_tc(const TcArgs& a, int batch, const char* name, cudaStream_t s);
+// Packed-A form: pack A once (launch_tc_pack), then launch_tc2 with a.Apk/a.sApk set.
+size_t tc_packed_bytes(int64_t M, int K);
+void launch_tc_pack(const float* A, int64_t lda, int64_t sA, int a_trans, int a_mask, int64_t M,
+                    int K, unsigned char* Apk, int64_t sApk, int batch, const uint8_t* dec, int k,
+                    uint8_t want, cudaStream_t s);
+void launch_tc2(const TcArgs& a, int batch, const char* name, cudaStream_t s);
 void launch_tfull(const float* G, int64_t sG, const float* Tslots, int64_t sT, float* Tf,
                   int64_t sTf, int nb, int batch, const uint8_t* dec, int k, cudaStream_t s);
 // C[M x N] -= A[M x K] B[K x N], FP32 column-major (single matrix).

@@ -314,6 +314,271 @@ void launch_gemm_tc(const float* A, int64_t lda, const float* B, int64_t ldb, fl
   launch_tc(a, 1, "k_gemm_tc", s);
 }
 
+// ---------------------------------------------------------------- packed-A pipeline
+// Second form of the contraction for operands shared by many output tiles (the V^T,
+// V T^T and T^T tiles of a QR step): A is packed once into K-major no-swizzle core-matrix
+// blocks (128 rows x 16 K, hi and lo TF32, 16 KB per block) and every CTA brings its
+// blocks in with TMA bulk copies (cp.async.bulk, completion tracked by the mbarrier's
+// transaction count).  The CTA tile is 256 x 256 (two M=128 accumulators, all 512 TMEM
+// columns); K advances in 16-wide chunks through a 3-stage ring.
+constexpr int P_BK = 16;
+constexpr int P_BN = 256;
+constexpr int P_STAGES = 3;
+constexpr int P_ABLK = 128 * P_BK * 4;                 // 8 KB per hi or lo copy
+constexpr int P_ASTAGE = 2 * 2 * P_ABLK;               // two M-halves x (hi, lo) = 32 KB
+constexpr int P_BSTAGE = 2 * P_BN * P_BK * 4;          // hi + lo = 32 KB
+constexpr int P_STAGE = P_ASTAGE + P_BSTAGE;           // 64 KB
+constexpr int P_SMEM = P_STAGES * P_STAGE + 256;
+constexpr uint32_t P_SBO = (P_BK / 4) * 128;           // 512 B between 8-row groups
+
+__device__ __forceinline__ uint64_t make_desc_sbo(uint32_t saddr, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((TC_LBO >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+__device__ __forceinline__ uint32_t kmajor_off16(int r, int k) {
+  return (uint32_t)((r >> 3) * P_SBO + (k >> 2) * TC_LBO + (r & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Packs the logical operand A (M x K; transposed / masked like tc_fetch) of every batch item
+// into blocks: block (mb, kc) of item t starts at Apk + t*sApk + (mb*nK + kc)*2*P_ABLK bytes,
+// hi copy first, then lo.  One CTA per block.
+__global__ void __launch_bounds__(256) k_tc_pack(const float* __restrict__ A, int64_t lda,
+                                                 int64_t sA, int a_trans, int a_mask, int64_t M,
+                                                 int K, unsigned char* __restrict__ Apk,
+                                                 int64_t sApk, const uint8_t* __restrict__ dec,
+                                                 int k_step, uint8_t want) {
+  if (dec != nullptr && dec[k_step] != want) return;
+  const int kc = blockIdx.x, mb = blockIdx.y;
+  const int64_t t = blockIdx.z;
+  const int nK = (K + P_BK - 1) / P_BK;
+  const float* P = A + t * sA;
+  unsigned char* hi = Apk + t * sApk + ((int64_t)mb * nK + kc) * 2 * P_ABLK;
+  unsigned char* lo = hi + P_ABLK;
+  for (int idx = threadIdx.x; idx < 128 * P_BK; idx += 256) {
+    int r, k;
+    if (a_trans) { k = idx % P_BK; r = idx / P_BK; } else { r = idx % 128; k = idx / 128; }
+    const int64_t gr = (int64_t)mb * 128 + r;
+    const int gk = kc * P_BK + k;
+    float x = 0.f;
+    if (gr < M && gk < K) x = a_trans ? tc_fetch(P, lda, gk, gr, a_mask) : tc_fetch(P, lda, gr, gk, a_mask);
+    tc_put(hi, lo, kmajor_off16(r, k), x);
+  }
+}
+
+// Stages a B chunk (K rows [k0, k0+16) x P_BN columns) with hi/lo splitting.
+__device__ __forceinline__ void p_stage_b(unsigned char* bst, const TcArgs& a, const float* B,
+                                          int64_t n0, int k0) {
+  unsigned char* bhi = bst;
+  unsigned char* blo = bst + P_BN * P_BK * 4;
+  if (!a.b_trans && a.b_mask == TC_MASK_NONE) {
+    // 4 consecutive K of one column per thread step: one 16-byte core-matrix row
+    for (int idx = threadIdx.x; idx < P_BN * (P_BK / 4); idx += TC_THREADS) {
+      const int q = idx % (P_BK / 4), c = idx / (P_BK / 4);
+      const int64_t gc = n0 + c;
+      const int gk = k0 + 4 * q;
+      float x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        x[u] = (gc < a.N && gk + u < a.K) ? B[gk + u + gc * a.ldb] : 0.f;
+      uint4 h, l;
+      uint32_t* hp = reinterpret_cast<uint32_t*>(&h);
+      uint32_t* lp = reinterpret_cast<uint32_t*>(&l);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        hp[u] = tf32_bits(x[u]);
+        lp[u] = tf32_bits(x[u] - __uint_as_float(hp[u]));
+      }
+      const uint32_t off = kmajor_off16(c, 4 * q);
+      *reinterpret_cast<uint4*>(bhi + off) = h;
+      *reinterpret_cast<uint4*>(blo + off) = l;
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < P_BN * P_BK; idx += TC_THREADS) {
+      int c, k;
+      if (a.b_trans) { c = idx % P_BN; k = idx / P_BN; } else { k = idx % P_BK; c = idx / P_BK; }
+      const int64_t gc = n0 + c;
+      const int gk = k0 + k;
+      float x = 0.f;
+      if (gc < a.N && gk < a.K)
+        x = a.b_trans ? tc_fetch(B, a.ldb, gc, gk, a.b_mask) : tc_fetch(B, a.ldb, gk, gc, a.b_mask);
+      tc_put(bhi, blo, kmajor_off16(c, k), x);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc2(TcArgs a) {
+  if (a.dec != nullptr && a.dec[a.k_step] != a.want) return;
+  extern __shared__ __align__(1024) unsigned char smem_p[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_p + P_STAGES * P_STAGE);
+  uint64_t* empty = full + P_STAGES;
+  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(empty + P_STAGES);
+  int* last_commit = reinterpret_cast<int*>(taddr_slot + 1);
+  int* pending_copy = last_commit + 1;   // chunk whose bulk copy was not seen complete
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t m0 = (int64_t)blockIdx.y * 256, n0 = (int64_t)blockIdx.x * P_BN;
+  const int64_t t = blockIdx.z;
+  const int nK = (a.K + P_BK - 1) / P_BK;
+  const int mh = (a.M - m0) > 128 ? 2 : 1;     // M halves present in this tile
+  const unsigned char* Apk = a.Apk + t * a.sApk;
+  const float* B = a.B + t * a.sB;
+  float* C = a.C + t * a.sC;
+  const float* C1 = a.C1 ? a.C1 + t * a.sC1 : nullptr;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(taddr_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    *last_commit = -1;
+    *pending_copy = -1;
+    for (int q = 0; q < P_STAGES; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *taddr_slot;
+  const uint32_t idesc = make_idesc_tf32(128, P_BN);
+  bool ok = true;
+  for (int c = 0; c < nK; ++c) {
+    const int st = c % P_STAGES;
+    const uint32_t use = (uint32_t)(c / P_STAGES);
+    unsigned char* sa = smem_p + st * P_STAGE;
+    unsigned char* sb = sa + P_ASTAGE;
+    if (c >= P_STAGES && !mbar_wait(&empty[st], (use - 1) & 1)) ok = false;
+    if (!__syncthreads_and(ok ? 1 : 0)) { ok = false; break; }
+    if (tid == 0) {
+      const uint32_t bytes = (uint32_t)mh * 2 * P_ABLK;
+      mbar_expect_tx(&full[st], bytes);
+      for (int h = 0; h < mh; ++h) {
+        const unsigned char* src = Apk + (((int64_t)(m0 / 128 + h) * nK + c) * 2 * P_ABLK);
+        bulk_g2s(sa + h * 2 * P_ABLK, src, 2 * P_ABLK, &full[st]);
+      }
+    }
+    p_stage_b(sb, a, B, n0, c * P_BK);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      if (!mbar_wait(&full[st], use & 1)) {
+        ok = false;
+        *pending_copy = c;
+      } else {
+        const uint32_t sbase = smem_u32(sb);
+#pragma unroll
+        for (int s8 = 0; s8 < P_BK / 8; ++s8) {
+          const uint32_t koff = (uint32_t)s8 * 2 * TC_LBO;
+          const uint64_t bhi = make_desc_sbo(sbase + koff, P_SBO);
+          const uint64_t blo = make_desc_sbo(sbase + P_BN * P_BK * 4 + koff, P_SBO);
+          for (int h = 0; h < mh; ++h) {
+            const uint32_t abase = smem_u32(sa + h * 2 * P_ABLK);
+            const uint64_t ahi = make_desc_sbo(abase + koff, P_SBO);
+            const uint64_t alo = make_desc_sbo(abase + P_ABLK + koff, P_SBO);
+            const uint32_t d = tmem + (uint32_t)(h * P_BN);
+            const uint32_t acc0 = (c > 0 || s8 > 0) ? 1u : 0u;
+            tc_mma(d, alo, bhi, idesc, acc0);
+            tc_mma(d, ahi, blo, idesc, 1u);
+            tc_mma(d, ahi, bhi, idesc, 1u);
+          }
+        }
+        tc_commit(&empty[st]);
+        *last_commit = c;
+      }
+    }
+  }
+  __syncthreads();
+  const int last = *last_commit;
+  if (last >= 0 && !mbar_wait(&empty[last % P_STAGES], (uint32_t)(last / P_STAGES) & 1)) ok = false;
+  // a bulk copy that was not seen complete must land before shared memory is released
+  if (tid == 0 && *pending_copy >= 0) {
+    const int pc = *pending_copy;
+    (void)mbar_wait(&full[pc % P_STAGES], (uint32_t)(pc / P_STAGES) & 1);
+  }
+  tc_fence_after();
+  const bool all_ok = __syncthreads_and(ok ? 1 : 0);
+  if (all_ok) {
+    const int h = warp >> 2;                       // M half handled by this warp
+    const int lane_base = (warp & 3) * 32;
+    const int64_t row = m0 + h * 128 + lane_base + lane;
+    if (h < mh) {
+      for (int cc = 0; cc < P_BN; cc += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(h * P_BN + cc), v);
+        if (row < a.M) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int64_t gc = n0 + cc + i;
+            if (gc < a.N) {
+              if (a.epi == TC_EPI_SUB)
+                C[row + gc * a.ldc] -= v[i];
+              else if (a.epi == TC_EPI_OUT)
+                C[row + gc * a.ldc] = v[i];
+              else
+                C[row + gc * a.ldc] = v[i] + C1[row + gc * a.ldc1];
+            }
+          }
+        }
+      }
+    }
+  } else if (tid == 0 && a.status != nullptr) {
+    atomicCAS(&a.status[ST_CODE], 0, -6);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+size_t tc_packed_bytes(int64_t M, int K) {
+  const int64_t mb = (M + 127) / 128, nK = (K + P_BK - 1) / P_BK;
+  return (size_t)(mb * nK) * 2 * P_ABLK;
+}
+
+void launch_tc_pack(const float* A, int64_t lda, int64_t sA, int a_trans, int a_mask, int64_t M,
+                    int K, unsigned char* Apk, int64_t sApk, int batch, const uint8_t* dec, int k,
+                    uint8_t want, cudaStream_t s) {
+  if (M <= 0 || K <= 0 || batch <= 0) return;
+  dim3 grid((unsigned)((K + P_BK - 1) / P_BK), (unsigned)((M + 127) / 128), (unsigned)batch);
+  {
+    ProfScope ps_("k_tc_pack", s);
+    k_tc_pack<<<grid, 256, 0, s>>>(A, lda, sA, a_trans, a_mask, M, K, Apk, sApk, dec, k, want);
+  }
+}
+
+void launch_tc2(const TcArgs& a, int batch, const char* name, cudaStream_t s) {
+  if (a.M <= 0 || a.N <= 0 || a.K <= 0 || batch <= 0) return;
+  ensure_dyn_smem<k_gemm_tc2>(P_SMEM);
+  dim3 grid((unsigned)((a.N + P_BN - 1) / P_BN), (unsigned)((a.M + 255) / 256), (unsigned)batch);
+  {
+    ProfScope ps_(name, s);
+    k_gemm_tc2<<<grid, TC_THREADS, P_SMEM, s>>>(a);
+  }
+}
+
 // ---------------------------------------------------------------- full compact-WY T
 // Tf (nb x nb, upper triangular, column-major, ld nb) such that Q = I - V Tf V^T for all
 // nb reflectors of a tile, from the Gram matrix G = V^T V (upper part used) and the stored

@@ -54,6 +54,9 @@ struct luqr_handle {
   float* Gbuf = nullptr;
   float* Tfull[2] = {nullptr, nullptr};
   float* Vt[2] = {nullptr, nullptr};
+  unsigned char* Apk[2] = {nullptr, nullptr};   // packed QR operands (V^T, V T^T, T^T) per tile
+  unsigned char* Lpk[2] = {nullptr, nullptr};   // packed LU panel (rows below the diagonal)
+  size_t pk_tile = 0;                           // bytes of one packed nb x nb operand
   // second pass / refinement scratch
   void* rhs_ws = nullptr;
   int rhs_cap = 0;
@@ -107,60 +110,68 @@ void tc_factor_extra(luqr_handle* h, int k, TileList tl, int kind, int mask, cud
   a.B = Tf + slot0; a.ldb = nb; a.sB = sslot; a.b_trans = 1; a.b_mask = TC_MASK_NONE;
   a.C = Vt + slot0; a.ldc = nb; a.sC = sslot;
   launch_tc(a, tl.count, "k_tc_vt", s);
+  // pack the A operands of the apply phase: V^T (0), V T^T (1), T^T (2, pairs only)
+  unsigned char* pk = h->Apk[k & 1] + (((size_t)tl.i0 * 2 + kind) * 3) * h->pk_tile;
+  const int64_t spk = (int64_t)tl.istride * 2 * 3 * (int64_t)h->pk_tile;
+  launch_tc_pack(V0, ld, (int64_t)tl.istride * nb, 1, mask, nb, nb, pk, spk, tl.count, h->dec, k,
+                 DEC_QR, s);
+  launch_tc_pack(Vt + slot0, nb, sslot, 0, TC_MASK_NONE, nb, nb, pk + h->pk_tile, spk, tl.count,
+                 h->dec, k, DEC_QR, s);
+  if (kind == 1)
+    launch_tc_pack(Tf + slot0, nb, sslot, 1, TC_MASK_NONE, nb, nb, pk + 2 * h->pk_tile, spk,
+                   tl.count, h->dec, k, DEC_QR, s);
 }
 
 void tc_apply_single(luqr_handle* h, int k, TileList tl, Mat<float> C, int64_t c0, int64_t c1,
                      cudaStream_t s) {
   const int nb = h->nb;
-  const int64_t ld = h->Npad, nb2 = (int64_t)nb * nb;
-  float* W = static_cast<float*>(h->W);
-  const int64_t slot0 = ((int64_t)tl.i0 * 2 + 0) * nb2, sslot = (int64_t)tl.istride * 2 * nb2;
+  const int64_t ld = h->Npad;
   const int64_t rstride = (int64_t)tl.istride * nb;
+  const unsigned char* pk = h->Apk[k & 1] + (((size_t)tl.i0 * 2 + 0) * 3) * h->pk_tile;
+  const int64_t spk = (int64_t)tl.istride * 2 * 3 * (int64_t)h->pk_tile;
   TcArgs a{};
   a.dec = h->dec; a.k_step = k; a.want = DEC_QR; a.status = h->status;
-  a.M = nb; a.N = c1 - c0; a.K = nb;
+  a.M = nb; a.N = c1 - c0; a.K = nb; a.sApk = spk;
   // W = V^T C
-  a.A = W + (int64_t)tl.i0 * nb + (int64_t)k * nb * ld; a.lda = ld; a.sA = rstride;
-  a.a_trans = 1; a.a_mask = TC_MASK_UNIT_LOWER;
+  a.Apk = pk;
   a.B = C.p + (int64_t)tl.i0 * nb + c0 * C.ld; a.ldb = C.ld; a.sB = rstride;
   a.C = h->Wbuf + (int64_t)tl.i0 * nb + c0 * ld; a.ldc = ld; a.sC = rstride; a.epi = TC_EPI_OUT;
-  launch_tc(a, tl.count, "k_tc_unmqr_w", s);
-  // C -= Vt W
-  a.A = h->Vt[k & 1] + slot0; a.lda = nb; a.sA = sslot; a.a_trans = 0; a.a_mask = TC_MASK_NONE;
+  launch_tc2(a, tl.count, "k_tc_unmqr_w", s);
+  // C -= (V T^T) W
+  a.Apk = pk + h->pk_tile;
   a.B = h->Wbuf + (int64_t)tl.i0 * nb + c0 * ld; a.ldb = ld; a.sB = rstride;
   a.C = C.p + (int64_t)tl.i0 * nb + c0 * C.ld; a.ldc = C.ld; a.sC = rstride; a.epi = TC_EPI_SUB;
-  launch_tc(a, tl.count, "k_tc_unmqr_c", s);
+  launch_tc2(a, tl.count, "k_tc_unmqr_c", s);
 }
 
 void tc_apply_pair(luqr_handle* h, int k, TileList tl, bool tri, Mat<float> C, int64_t c0,
                    int64_t c1, cudaStream_t s) {
   const int nb = h->nb;
-  const int64_t ld = h->Npad, nb2 = (int64_t)nb * nb;
-  float* W = static_cast<float*>(h->W);
-  const int64_t slot0 = ((int64_t)tl.i0 * 2 + 1) * nb2, sslot = (int64_t)tl.istride * 2 * nb2;
+  const int64_t ld = h->Npad;
   const int64_t rstride = (int64_t)tl.istride * nb;
   const int64_t i0r = (int64_t)tl.i0 * nb, e0r = (int64_t)(tl.i0 - tl.eoff) * nb;
   float* Wp = h->Wbuf + i0r + c0 * ld;
+  const unsigned char* pk = h->Apk[k & 1] + (((size_t)tl.i0 * 2 + 1) * 3) * h->pk_tile;
+  const int64_t spk = (int64_t)tl.istride * 2 * 3 * (int64_t)h->pk_tile;
   TcArgs a{};
   a.dec = h->dec; a.k_step = k; a.want = DEC_QR; a.status = h->status;
-  a.M = nb; a.N = c1 - c0; a.K = nb;
+  a.M = nb; a.N = c1 - c0; a.K = nb; a.sApk = spk;
   // W = C1 + V2^T C2
-  a.A = W + i0r + (int64_t)k * nb * ld; a.lda = ld; a.sA = rstride; a.a_trans = 1;
-  a.a_mask = tri ? TC_MASK_UPPER : TC_MASK_NONE;
+  a.Apk = pk;
   a.B = C.p + i0r + c0 * C.ld; a.ldb = C.ld; a.sB = rstride;
   a.C1 = C.p + e0r + c0 * C.ld; a.ldc1 = C.ld; a.sC1 = rstride;
   a.C = Wp; a.ldc = ld; a.sC = rstride; a.epi = TC_EPI_ADD_OUT;
-  launch_tc(a, tl.count, tri ? "k_tc_ttmqr_w" : "k_tc_tsmqr_w", s);
+  launch_tc2(a, tl.count, tri ? "k_tc_ttmqr_w" : "k_tc_tsmqr_w", s);
   a.C1 = nullptr;
   // C1 -= T^T W
-  a.A = h->Tfull[k & 1] + slot0; a.lda = nb; a.sA = sslot; a.a_trans = 1; a.a_mask = TC_MASK_NONE;
+  a.Apk = pk + 2 * h->pk_tile;
   a.B = Wp; a.ldb = ld; a.sB = rstride;
   a.C = C.p + e0r + c0 * C.ld; a.ldc = C.ld; a.sC = rstride; a.epi = TC_EPI_SUB;
-  launch_tc(a, tl.count, tri ? "k_tc_ttmqr_c1" : "k_tc_tsmqr_c1", s);
-  // C2 -= Vt W
-  a.A = h->Vt[k & 1] + slot0; a.lda = nb; a.sA = sslot; a.a_trans = 0;
+  launch_tc2(a, tl.count, tri ? "k_tc_ttmqr_c1" : "k_tc_tsmqr_c1", s);
+  // C2 -= (V2 T^T) W
+  a.Apk = pk + h->pk_tile;
   a.C = C.p + i0r + c0 * C.ld;
-  launch_tc(a, tl.count, tri ? "k_tc_ttmqr_c2" : "k_tc_tsmqr_c2", s);
+  launch_tc2(a, tl.count, tri ? "k_tc_ttmqr_c2" : "k_tc_tsmqr_c2", s);
 }
 
 template <typename T>
@@ -236,8 +247,13 @@ void enqueue_lu_apply(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, c
   Mat<T> Cblk{C.p + r1 + c0 * C.ld, C.ld};
   if constexpr (std::is_same<T, float>::value) {
     if (tc && h->use_tc) {
-      launch_gemm_tc(Ablk.p, ld, Brow.p, C.ld, Cblk.p, C.ld, h->Npad - r1, c1 - c0, nb, h->dec, k,
-                     DEC_LU, h->status, s);
+      TcArgs a{};
+      a.dec = h->dec; a.k_step = k; a.want = DEC_LU; a.status = h->status;
+      a.M = h->Npad - r1; a.N = c1 - c0; a.K = nb;
+      a.Apk = h->Lpk[k & 1];   // packed by the factor phase (pack_lu_panel)
+      a.B = Brow.p; a.ldb = C.ld;
+      a.C = Cblk.p; a.ldc = C.ld; a.epi = TC_EPI_SUB;
+      launch_tc2(a, 1, "k_tc_lu_gemm", s);
       return;
     }
   }
@@ -277,6 +293,11 @@ void enqueue_factor(luqr_handle* h) {
     launch_lu_commit<T>(W, ld, k, nb, S, h->piv_s, h->piv_all + (size_t)k * nb, h->dec, s);
     Mat<const T> LU{W + r0 + r0 * ld, ld};
     launch_trsm<T>(LU, nb, F, r1, h->Npad, r0, h->dec, k, s);
+    if constexpr (std::is_same<T, float>::value) {
+      if (h->use_tc && r1 < h->Npad)   // pack A_ik U^-1 for the tensor-core trailing GEMM
+        launch_tc_pack(reinterpret_cast<float*>(W) + r1 + r0 * ld, ld, 0, 0, TC_MASK_NONE,
+                       h->Npad - r1, nb, h->Lpk[k & 1], 0, 1, h->dec, k, DEC_LU, s);
+    }
     enqueue_qr<T>(h, k, F, 0, 0, true, false, s, true);
     cudaEventRecord(h->ev_fact[k], s);
     // ---- bulk update of columns >= k+2 (and b) on the update stream
@@ -347,7 +368,8 @@ void free_handle(luqr_handle* h) {
   void* ptrs[] = {h->W,      h->Tbuf,     h->S,        h->piv_s, h->piv_all, h->norms,
                   h->local,  h->away,     h->colsum,   h->dec,   h->margin,  h->lhs,
                   h->rhs,    h->status,   h->forced,   h->rhs_ws, h->ref,    h->Wbuf,
-                  h->Gbuf,   h->Tfull[0], h->Tfull[1], h->Vt[0], h->Vt[1], h->gm};
+                  h->Gbuf,   h->Tfull[0], h->Tfull[1], h->Vt[0], h->Vt[1], h->gm,
+                  h->Apk[0], h->Apk[1],   h->Lpk[0],   h->Lpk[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -551,7 +573,12 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   if (o.forced) A((void**)&h->forced, (size_t)n);
   h->use_tc = (h->prec == LUQR_PREC_FP32) && (o.fp32_kernels != 1);
   h->use_tc_qr = (h->prec == LUQR_PREC_FP32) && (o.fp32_kernels == 2);
+  h->pk_tile = tc_packed_bytes(nb, nb);
+  if (h->use_tc) {
+    for (int q = 0; q < 2; ++q) A((void**)&h->Lpk[q], tc_packed_bytes(h->Npad, nb));
+  }
   if (h->use_tc_qr) {
+    for (int q = 0; q < 2; ++q) A((void**)&h->Apk[q], (size_t)n * 2 * 3 * h->pk_tile);
     const size_t slots = (size_t)n * 2 * nb * nb;
     A((void**)&h->Wbuf, sizeof(float) * (size_t)h->Npad * h->Wc);
     A((void**)&h->Gbuf, sizeof(float) * slots);

@@ -300,3 +300,4 @@ def gemm_sub_f32(C, A, B, status=None, stream=None):
     if st != OK:
         raise LuqrError(st, "luqr_gemm_sub_f32")
     return C
+
