@@ -209,6 +209,39 @@ int luqr_profile_read(const char** names, int64_t* launches, double* total_ms, i
 int luqr_gemm_sub_f32(float* C, int64_t ldc, const float* A, int64_t lda, const float* B,
                       int64_t ldb, int64_t M, int64_t N, int64_t K, int* dstatus, void* stream);
 
+/* Maximum sizes accepted by luqr_panel_test_noalloc (its scratch is a fixed array). */
+#define LUQR_NOALLOC_MAX_NB 256
+#define LUQR_NOALLOC_MAX_TILES 1024
+
+/*
+ * luqr_panel_test_noalloc - the per-step robustness test of one panel (panel statistics,
+ * LU with partial pivoting of a scratch copy of the diagonal tile, exact ||A_kk^-1||_1 and
+ * the Max / Sum / MUMPS comparison) without allocating any device memory.  The paper has
+ * no counterpart: this entry exists for callers that cannot call cudaMalloc, e.g. code
+ * that records a CUDA graph under stream capture (allocation is not allowed there), code
+ * confined to a pre-reserved memory budget, or latency-critical paths that must not wait
+ * on the allocator.
+ *   dpanel    device, column-major FP64 panel of `rows` x nb: the diagonal tile on top,
+ *             then the (rows/nb - 1) sub-diagonal tiles; leading dimension ld >= rows.
+ *   rows      a multiple of nb, at most LUQR_NOALLOC_MAX_TILES * nb (pad with zero tiles).
+ *   nb        multiple of 32 with 32 <= nb <= LUQR_NOALLOC_MAX_NB.
+ *   criterion, alpha, mumps_mode  as luqr_factor / luqr_options.
+ *   ddec      device uint8: receives LUQR_DEC_LU, LUQR_DEC_QR, or LUQR_DEC_ABORTED when the
+ *             panel holds a NaN/Inf or FORCE_LU meets an exact zero pivot.
+ *   dmargin   device double: log2(lhs/rhs) of the test (as luqr_decisions).
+ * Work is enqueued on `stream`; nothing is synchronised and no device memory is allocated
+ * or freed.  Scratch: one file-scope device array of about 0.53 MB per GPU, shared by every
+ * call and kept until the process exits.  Calls that overlap on the GPU (different streams
+ * or devices sharing the array's contents on one GPU) race on it and must be serialised by
+ * the caller.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture begins.  Returns LUQR_ERR_INVALID for sizes beyond the limits above or bad
+ * arguments, LUQR_ERR_CUDA if the set-up or a launch fails.
+ */
+int luqr_panel_test_noalloc(const double* dpanel, int64_t ld, int64_t rows, int nb, int criterion,
+                            double alpha, int mumps_mode, uint8_t* ddec, double* dmargin,
+                            void* stream);
+
 /* luqr_status_string - static text for a status code. */
 const char* luqr_status_string(int status);
 

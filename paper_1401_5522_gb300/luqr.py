@@ -68,6 +68,8 @@ _SIGS = {
     "luqr_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "luqr_gemm_sub_f32": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _I64, _I64, _I64, _I64, _P, _P]),
+    "luqr_panel_test_noalloc": (ctypes.c_int, [_P, _I64, _I64, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_double, ctypes.c_int, _P, _P, _P]),
     "luqr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "luqr_version": (ctypes.c_char_p, []),
 }
@@ -301,3 +303,22 @@ def gemm_sub_f32(C, A, B, status=None, stream=None):
         raise LuqrError(st, "luqr_gemm_sub_f32")
     return C
 
+
+def panel_test_noalloc(panel, nb, criterion="max", alpha=100.0, mumps_mode=0, dec=None,
+                       margin=None, stream=None):
+    """Allocation-free robustness test of one panel (rows x nb, column-major float64 CUDA).
+
+    ``dec`` (uint8[1]) and ``margin`` (float64[1]) are caller-provided CUDA tensors that
+    receive the result; the call itself allocates no device memory."""
+    import torch
+    if not (panel.is_cuda and panel.dtype == torch.float64 and panel.stride(0) == 1):
+        raise TypeError("panel must be a column-major float64 CUDA matrix")
+    rows = panel.shape[0]
+    ld = max(panel.stride(1), rows) if panel.dim() == 2 and panel.shape[1] > 1 else rows
+    crit = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
+    st = lib().luqr_panel_test_noalloc(ctypes.c_void_p(panel.data_ptr()), ld, rows, int(nb), crit,
+                                       float(alpha), int(mumps_mode), ctypes.c_void_p(dec.data_ptr()),
+                                       ctypes.c_void_p(margin.data_ptr()), _stream_ptr(stream))
+    if st != OK:
+        raise LuqrError(st, "luqr_panel_test_noalloc")
+    return dec, margin
