@@ -44,6 +44,7 @@ def parse(argv=None):
     p.add_argument("--tree", default="binary_tt")
     p.add_argument("--precision", default="fp32")
     p.add_argument("--tol", type=float, default=1e-13)
+    p.add_argument("--fp32-kernels", default="default", choices=["default", "cuda", "tensor"])
     p.add_argument("--fp64-baseline", type=int, default=1, help="also time one plain FP64 solve")
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--cpu-N", type=int, default=2048, help="oracle sample size")
@@ -216,7 +217,8 @@ def main():
                            f"eta<={args.tol:g}"),
               "N": args.N, "nb": args.nb, "kappa": args.kappa, "criterion": args.criterion,
               "alpha": args.alpha, "tree": args.tree, "factor_precision": args.precision,
-              "refinement": "fp64", "parallelism": f"replicas x{args.gpus}",
+              "refinement": "fp64", "fp32_kernels": args.fp32_kernels,
+              "parallelism": f"replicas x{args.gpus}",
               "l2": "inputs larger than L2 (A is N^2 float64)"}
 
     if args.impl == "reference":
@@ -252,7 +254,8 @@ def main():
     info = {}
 
     def one_solve():
-        h = luqr.factor(A, nb, args.criterion, args.alpha, tree=args.tree, precision=args.precision)
+        h = luqr.factor(A, nb, args.criterion, args.alpha, tree=args.tree, precision=args.precision,
+                        fp32_kernels=args.fp32_kernels)
         st, its, eta = h.refine(A, b, x, tol=args.tol, max_iter=30)
         dec, _ = h.decisions()
         h.close()
@@ -342,7 +345,7 @@ def main():
             dA2.copy_(hA, non_blocking=True)
             db2.copy_(hb, non_blocking=True)
             h = luqr.factor(dA2, nb, args.criterion, args.alpha, tree=args.tree,
-                            precision=args.precision)
+                            precision=args.precision, fp32_kernels=args.fp32_kernels)
             h.refine(dA2, db2, dx2, tol=args.tol, max_iter=30)
             h.close()
             hx.copy_(dx2, non_blocking=True)

@@ -80,9 +80,9 @@ typedef struct luqr_options {
   const int* inject;       /* optional HOST list of steps whose tile row of [A^(k)|b^(k)] is
                               scaled by 2^-27 before the criterion (run-time injection) */
   int n_inject;
-  int fp32_kernels;        /* FP32 only: 0 = default (tcgen05 GEMM for LU updates, fused
-                              shared-memory QR updates), 1 = no tcgen05 kernels,
-                              2 = tcgen05 for the LU and the QR trailing updates */
+  int fp32_kernels;        /* FP32 only: 0 = default = 2; 1 = CUDA-core trailing updates
+                              (fused shared-memory QR kernels, register-tiled GEMM);
+                              2 = tcgen05 tensor-core trailing updates (3xTF32) */
   int reserved[8];
 } luqr_options;
 
@@ -208,6 +208,37 @@ int luqr_profile_read(const char** names, int64_t* launches, double* total_ms, i
  */
 int luqr_gemm_sub_f32(float* C, int64_t ldc, const float* A, int64_t lda, const float* B,
                       int64_t ldb, int64_t M, int64_t N, int64_t K, int* dstatus, void* stream);
+
+/*
+ * Batched solves: many independent systems of uneven order in ONE persistent kernel
+ * launch.  Each CTA claims systems largest-first from a device queue and runs the whole
+ * hybrid method for one system at a time (Alg. 1-4 with the flat TS tree, in-kernel
+ * decisions), back-substitutes the augmented right-hand side and, with precision
+ * LUQR_PREC_FP32, refines x with FP64 residuals until eta <= tol (at most max_iter
+ * corrections).
+ *
+ * luqr_batched_create - uploads the description of the batch and allocates scratch.
+ *   dA, db   HOST arrays of `count` DEVICE pointers: A_i column-major N_i x N_i (lda = N_i,
+ *            read only), b_i of length N_i (overwritten with x_i by luqr_batched_run).
+ *   N, nb    HOST arrays: orders (1..8192) and tile sizes (32 or 64) per system (pick nb
+ *            with the autotuner of the Python package or pass a fixed value).
+ *   criterion, alpha, opt (precision, mumps_mode), tol, max_iter as for luqr_factor/refine.
+ * luqr_batched_run - enqueues one persistent launch on `stream`; it allocates nothing and
+ *   synchronises nothing, so it can be captured in a CUDA graph and replayed (the batch's
+ *   b_i must be reset by the caller between replays).
+ * luqr_batched_results - synchronises the device and copies to HOST arrays (any may be
+ *   NULL): per-system decisions (count x nmax, LUQR_DEC_*, 255 past the system's last
+ *   step), status, refinement iterations and final eta; *nmax_out = nmax.
+ * luqr_batched_destroy - frees the batch (synchronises the device first).
+ */
+typedef struct luqr_batched* luqr_batched_t;
+int luqr_batched_create(const double* const* dA, double* const* db, const int* N, const int* nb,
+                        int count, int criterion, double alpha, const luqr_options* opt,
+                        double tol, int max_iter, luqr_batched_t* out);
+int luqr_batched_run(luqr_batched_t b, void* stream);
+int luqr_batched_results(luqr_batched_t b, uint8_t* dec, int* status, int* iters, double* eta,
+                         int* nmax_out);
+void luqr_batched_destroy(luqr_batched_t b);
 
 /* Maximum sizes accepted by luqr_panel_test_noalloc (its scratch is a fixed array). */
 #define LUQR_NOALLOC_MAX_NB 256

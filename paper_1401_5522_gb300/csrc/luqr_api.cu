@@ -572,7 +572,7 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   A((void**)&h->status, sizeof(int) * ST_WORDS);
   if (o.forced) A((void**)&h->forced, (size_t)n);
   h->use_tc = (h->prec == LUQR_PREC_FP32) && (o.fp32_kernels != 1);
-  h->use_tc_qr = (h->prec == LUQR_PREC_FP32) && (o.fp32_kernels == 2);
+  h->use_tc_qr = (h->prec == LUQR_PREC_FP32) && (o.fp32_kernels != 1);
   h->pk_tile = tc_packed_bytes(nb, nb);
   if (h->use_tc) {
     for (int q = 0; q < 2; ++q) A((void**)&h->Lpk[q], tc_packed_bytes(h->Npad, nb));

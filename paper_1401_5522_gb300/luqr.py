@@ -70,6 +70,12 @@ _SIGS = {
     "luqr_gemm_sub_f32": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _I64, _I64, _I64, _I64, _P, _P]),
     "luqr_panel_test_noalloc": (ctypes.c_int, [_P, _I64, _I64, ctypes.c_int, ctypes.c_int,
                                                ctypes.c_double, ctypes.c_int, _P, _P, _P]),
+    "luqr_batched_create": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           ctypes.POINTER(Options), ctypes.c_double, ctypes.c_int,
+                                           ctypes.POINTER(_P)]),
+    "luqr_batched_run": (ctypes.c_int, [_P, _P]),
+    "luqr_batched_results": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
+    "luqr_batched_destroy": (None, [_P]),
     "luqr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "luqr_version": (ctypes.c_char_p, []),
 }
