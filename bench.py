@@ -45,6 +45,10 @@ def parse(argv=None):
     p.add_argument("--precision", default="fp32")
     p.add_argument("--tol", type=float, default=1e-13)
     p.add_argument("--fp32-kernels", default="default", choices=["default", "cuda", "tensor"])
+    p.add_argument("--speculate", default="off", choices=["off", "repeat", "mlp"],
+                   help="predicted-branch speculation of the factorization")
+    p.add_argument("--mlp-params", default=None,
+                   help="float32 .npy parameter vector of the decision MLP (speculate=mlp)")
     p.add_argument("--fp64-baseline", type=int, default=1, help="also time one plain FP64 solve")
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--cpu-N", type=int, default=2048, help="oracle sample size")
@@ -89,6 +93,48 @@ def step_kernel_flops(dec, n, nb, tree, ncols_extra, replay=False):
         if not replay:
             add("k_getrf", 2.0 / 3.0 * nb3)
     return out
+
+
+def step_tc_bytes(dec, n, nb, tree, ncols_extra):
+    """Algorithmic HBM bytes per tensor-core update kernel for one FP32 factorization:
+    every launch reads its B operand and C (when accumulated), writes C, and reads its
+    nb x nb FP32 A operand once.  W = V^T C (UNMQR) / W = C1 + V2^T C2 (TT pair);
+    C -= (V T^T) W; C1 -= T^T W; C2 -= (V2 T^T) W; LU: C -= L U."""
+    out = {}
+
+    def add(k, v):
+        out[k] = out.get(k, 0.0) + v
+
+    a_op = 4.0 * nb * nb
+    for k in range(n):
+        m = n - 1 - k
+        cols = m * nb + ncols_extra
+        if cols <= 0:
+            continue
+        if dec[k] == 1:
+            rows = m * nb
+            add("k_tc_lu_gemm", 4.0 * (rows * nb + nb * cols + 2.0 * rows * cols))
+            continue
+        if tree == "binary_tt":
+            singles, pairs, kind = m + 1, m, "tt"
+        else:
+            singles, pairs, kind = 1, m, "ts"
+        add("k_tc_unmqr_w", singles * (8.0 * nb * cols + a_op))
+        add("k_tc_unmqr_c", singles * (12.0 * nb * cols + a_op))
+        add(f"k_tc_{kind}mqr_w", pairs * (12.0 * nb * cols + a_op))
+        add(f"k_tc_{kind}mqr_c1", pairs * (12.0 * nb * cols + a_op))
+        add(f"k_tc_{kind}mqr_c2", pairs * (12.0 * nb * cols + a_op))
+    return out
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
 # ------------------------------------------------------------------ clocks
@@ -218,6 +264,7 @@ def main():
               "N": args.N, "nb": args.nb, "kappa": args.kappa, "criterion": args.criterion,
               "alpha": args.alpha, "tree": args.tree, "factor_precision": args.precision,
               "refinement": "fp64", "fp32_kernels": args.fp32_kernels,
+              "speculate": args.speculate,
               "parallelism": f"replicas x{args.gpus}",
               "l2": "inputs larger than L2 (A is N^2 float64)"}
 
@@ -252,10 +299,14 @@ def main():
     x = torch.zeros(N, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     info = {}
+    spec = {"speculate": args.speculate}
+    if args.speculate == "mlp":
+        spec["mlp_params"] = torch.from_numpy(
+            np.load(args.mlp_params).astype(np.float32)).cuda()
 
     def one_solve():
         h = luqr.factor(A, nb, args.criterion, args.alpha, tree=args.tree, precision=args.precision,
-                        fp32_kernels=args.fp32_kernels)
+                        fp32_kernels=args.fp32_kernels, **spec)
         st, its, eta = h.refine(A, b, x, tol=args.tol, max_iter=30)
         dec, _ = h.decisions()
         h.close()
@@ -306,21 +357,34 @@ def main():
     rep = step_kernel_flops(dec, n, nb, args.tree, 0, replay=True)
     total_alg = {k: args.steps * fac.get(k, 0.0) + sum(iters) * rep.get(k, 0.0)
                  for k in set(fac) | set(rep)}
+    tc_bytes = step_tc_bytes(dec, n, nb, args.tree, 0) if args.precision == "fp32" else {}
     dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
     roofline = None
     if dom is not None:
         name, (launches, tot_ms) = dom
-        alg = total_alg.get(name)
-        peak = FP32_FFMA_PEAK_TFLOPS if args.precision == "fp32" else FP64_DFMA_PEAK_TFLOPS
-        if alg:
-            achieved = alg / (tot_ms / 1e3) / 1e12
-            roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
-                        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                        "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
-                                        if args.precision == "fp32" else
-                                        "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"),
+        if name in tc_bytes:
+            peaks = load_peaks()
+            alg_bytes = args.steps * tc_bytes[name]
+            achieved = alg_bytes / (tot_ms / 1e3) / 1e9
+            roofline = {"bound": "hbm", "kernel": name, "achieved": achieved,
+                        "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                        "peak_source": f"{peaks['source']} HBM copy bandwidth",
+                        "bytes_per_launch": alg_bytes / launches,
                         "launches": launches, "avg_launch_ms": tot_ms / launches,
-                        "share_of_step": tot_ms / (ms * args.steps)}
+                        "share_of_kernel_time": tot_ms / sum(v[1] for v in prof.values())}
+        else:
+            alg = total_alg.get(name)
+            peak = FP32_FFMA_PEAK_TFLOPS if args.precision == "fp32" else FP64_DFMA_PEAK_TFLOPS
+            if alg:
+                achieved = alg / (tot_ms / 1e3) / 1e12
+                roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
+                            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                            "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+                                            if args.precision == "fp32" else
+                                            "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"),
+                            "launches": launches, "avg_launch_ms": tot_ms / launches,
+                            "share_of_kernel_time": tot_ms / sum(v[1] for v in prof.values())}
     gpu_launches = int(sum(v[0] for v in prof.values())) if prof else 0
     kernel_table = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in
                     sorted(prof.items(), key=lambda kv: -kv[1][1])}
@@ -345,7 +409,7 @@ def main():
             dA2.copy_(hA, non_blocking=True)
             db2.copy_(hb, non_blocking=True)
             h = luqr.factor(dA2, nb, args.criterion, args.alpha, tree=args.tree,
-                            precision=args.precision, fp32_kernels=args.fp32_kernels)
+                            precision=args.precision, fp32_kernels=args.fp32_kernels, **spec)
             h.refine(dA2, db2, dx2, tol=args.tol, max_iter=30)
             h.close()
             hx.copy_(dx2, non_blocking=True)

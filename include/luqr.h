@@ -83,6 +83,17 @@ typedef struct luqr_options {
   int fp32_kernels;        /* FP32 only: 0 = default = 2; 1 = CUDA-core trailing updates
                               (fused shared-memory QR kernels, register-tiled GEMM);
                               2 = tcgen05 tensor-core trailing updates (3xTF32) */
+  int speculate;           /* predicted-branch speculation (not in the paper; decisions and
+                              results are those of the plain method in every mode):
+                              0 off; 1 decision-MLP predictor (mlp_params required);
+                              2 repeat-the-previous-decision predictor.  A step predicted QR
+                              factors its panel on a copy while the diagonal GETRF and the
+                              criterion run; the copy is committed when the criterion
+                              selects QR and discarded otherwise. */
+  int log_features;        /* != 0: store the LUQR_MLP_FEATURES features of every step
+                              (read with luqr_features); implied by speculate != 0 */
+  const float* mlp_params; /* DEVICE, LUQR_MLP_PARAMS floats (layout at luqr_mlp_forward);
+                              read during the factorization, caller-owned */
   int reserved[8];
 } luqr_options;
 
@@ -231,6 +242,45 @@ int luqr_gemm_sub_f32(float* C, int64_t ldc, const float* A, int64_t lda, const 
  *   step), status, refinement iterations and final eta; *nmax_out = nmax.
  * luqr_batched_destroy - frees the batch (synchronises the device first).
  */
+/*
+ * Decision predictor (not in the paper).  Per step k the factorization can compute
+ * LUQR_MLP_FEATURES FP32 features from the panel statistics that precede the criterion
+ * (all log2-scaled where they are magnitudes):
+ *   0 ||A_kk||_1   1 max_{i>k} ||A_ik||_1   2 sum_{i>k} ||A_ik||_1
+ *   3 min_j max_i |A_kk(i,j)|   4 max_j |A_kk(j,j)| / max|A_kk|   5 min_j |A_kk(j,j)| / max|A_kk|
+ *   6 max_j log2(away(j)/local(j))   7 mean_j log2(away(j)/local(j))  (away: column max
+ *     over the sub-diagonal tiles, local: over A_kk; 64 when local(j) = 0)
+ *   8 previous decision (1 LU, 0 QR, 0.5 at k = 0)   9, 10 margins of steps k-1, k-2
+ *     (log2(lhs/rhs) of the criterion, clamped to [-64, 64])
+ *   11 k/n   12 log2 alpha (64 for infinity)   13 log2 (n - k)   14 criterion / 4
+ *   15 fraction of QR steps before k.
+ * The network maps 16 -> 64 -> 64 -> 1 with ReLU hidden layers; logit > 0 predicts LU.
+ * Parameter vector (FP32, LUQR_MLP_PARAMS): W1[64][16] row-major, b1[64], W2[64][64],
+ * b2[64], W3[64], b3.  All pointers are DEVICE pointers; work is enqueued on `stream`.
+ *
+ * luqr_mlp_forward - dlogits[s] = network(dX[s*16 .. s*16+15]) for s < B (B = 0: no-op,
+ *                    pointers may then be NULL).
+ * luqr_mlp_grad    - ADDS to dgrad the gradient of the mean binary cross-entropy with
+ *                    logits over the batch (labels 1 = LU, 0 = QR) and, if dloss is not
+ *                    NULL, adds the mean loss to *dloss.  Zero dgrad/dloss first.
+ * luqr_mlp_adam    - one Adam step (Kingma and Ba) at iteration t >= 1 on all parameters
+ *                    with first/second moment buffers dm, dv (zero before t = 1).
+ * Errors: LUQR_ERR_INVALID for NULL pointers, B < 0 (B < 1 for grad) or t < 1;
+ * LUQR_ERR_CUDA if the launch fails.
+ *
+ * luqr_features - copies the logged features (n x 16, row k = step k) and the
+ *   predictions made during the factorization (n bytes, LUQR_DEC_*; NULL to skip)
+ *   to HOST arrays.  LUQR_ERR_INVALID when the handle logged no features.
+ */
+#define LUQR_MLP_FEATURES 16
+#define LUQR_MLP_PARAMS 5313
+int luqr_mlp_forward(const float* dparams, const float* dX, float* dlogits, int B, void* stream);
+int luqr_mlp_grad(const float* dparams, const float* dX, const float* dlabels, int B,
+                  float* dgrad, float* dloss, void* stream);
+int luqr_mlp_adam(float* dparams, const float* dgrad, float* dm, float* dv, int t, float lr,
+                  float beta1, float beta2, float eps, void* stream);
+int luqr_features(luqr_handle_t h, float* feat, uint8_t* predicted, int* n_out);
+
 typedef struct luqr_batched* luqr_batched_t;
 int luqr_batched_create(const double* const* dA, double* const* db, const int* N, const int* nb,
                         int count, int criterion, double alpha, const luqr_options* opt,

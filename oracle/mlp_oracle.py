@@ -81,3 +81,55 @@ def loss_and_grad(p, X, y):
     gb1 = dz1.sum(axis=0)
     g = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3, gb3])
     return L, g
+
+
+def adam_step(p, g, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma and Ba, Algorithm 1) at iteration t >= 1; returns (p, m, v)."""
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    return np.asarray(p, dtype=np.float64) - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def _log2(v):
+    return float(np.log2(max(float(v), 1e-300)))
+
+
+def step_features(k, n, alpha, criterion, tile_norms, Akk, away_max, dec, margin):
+    """The 16 predictor features of step k, from the state the criterion sees.
+
+    tile_norms: ||A_ik||_1 for i = k..n-1 (Sec. III-D inputs); Akk: the diagonal tile;
+    away_max[j]: max |A_ij| over the sub-diagonal tiles; dec, margin: the decisions and
+    log2(lhs/rhs) margins of steps 0..k-1.  Definitions as in the C header.
+    """
+    Akk = np.abs(np.asarray(Akk, dtype=np.float64))
+    local = Akk.max(axis=0)
+    away = np.asarray(away_max, dtype=np.float64)
+    diag = np.diag(Akk)
+    lmax = local.max()
+    ratio = np.where(local > 0, np.log2(np.maximum(away, 1e-300) / np.where(local > 0, local, 1.0)),
+                     64.0)
+    rest = np.asarray(tile_norms[1:], dtype=np.float64)
+
+    def clamp(m):
+        return 0.0 if np.isnan(m) else float(min(64.0, max(-64.0, m)))
+
+    f = np.zeros(F)
+    f[0] = _log2(tile_norms[0])
+    f[1] = _log2(rest.max() if rest.size else 0.0)
+    f[2] = _log2(rest.sum())
+    f[3] = _log2(local.min())
+    f[4] = _log2(diag.max() / max(lmax, 1e-300))
+    f[5] = _log2(diag.min() / max(lmax, 1e-300))
+    f[6] = clamp(ratio.max())
+    f[7] = clamp(ratio.mean())
+    f[8] = (1.0 if dec[k - 1] == 1 else 0.0) if k > 0 else 0.5
+    f[9] = clamp(margin[k - 1]) if k > 0 else 0.0
+    f[10] = clamp(margin[k - 2]) if k > 1 else 0.0
+    f[11] = k / n
+    f[12] = 64.0 if np.isinf(alpha) else _log2(alpha)
+    f[13] = _log2(n - k)
+    f[14] = criterion / 4.0
+    f[15] = (np.sum(np.asarray(dec[:k]) == 0) / k) if k > 0 else 0.0
+    return f

@@ -216,4 +216,17 @@ void launch_multidot(const double* V, int64_t ldv, int64_t N, int cnt, const dou
 void launch_multiaxpy(const double* V, int64_t ldv, int64_t N, int cnt, const double* coef,
                       double* w, double alpha, cudaStream_t s);
 
+// Decision predictor and speculation helpers (k_mlp.cu).
+template <typename T>
+void launch_features_spec(const T* W, int64_t ldw, int k, int n, int nb, double alpha,
+                          int criterion, const double* norms_k, const unsigned long long* local,
+                          const unsigned long long* away, const uint8_t* dec, const double* margin,
+                          float* feat, int mode, const float* params, uint8_t* spec,
+                          cudaStream_t s);
+void launch_spec_resolve(int k, const uint8_t* dec, const uint8_t* spec, uint8_t* qrfac,
+                         uint8_t* commit, cudaStream_t s);
+template <typename T>
+void launch_gated_copy(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t rows, int cols,
+                       const uint8_t* gate, int k, uint8_t want, const char* name, cudaStream_t s);
+
 }  // namespace luqr

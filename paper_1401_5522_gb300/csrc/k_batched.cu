@@ -531,7 +531,6 @@ __global__ void __launch_bounds__(BT, 1) k_batched(BatchArgs a) {
       sl.W[r + (int64_t)c * ldw] = (T)v;
     }
     __syncthreads();
-    const int Wc = Np + 1;
     for (int k = 0; k < n && st == 0; ++k) {
       const int64_t r0 = (int64_t)k * nb;
       const int m = n - 1 - k;

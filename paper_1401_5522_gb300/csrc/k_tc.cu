@@ -110,6 +110,36 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Epilogue of 32 consecutive columns gc0.. of one row: all loads of the row segment are
+// issued before any store, so a thread keeps 32 independent loads in flight.
+__device__ __forceinline__ void tc_epi32(const TcArgs& a, float* C, const float* C1, int64_t row,
+                                         int64_t gc0, const float* v) {
+  if (row >= a.M || gc0 >= a.N) return;
+  const int64_t lim = a.N - gc0;
+  float* Cr = C + row + gc0 * a.ldc;
+  if (a.epi == TC_EPI_OUT) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < lim) Cr[(int64_t)i * a.ldc] = v[i];
+    return;
+  }
+  float old[32];
+  if (a.epi == TC_EPI_SUB) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) old[i] = (i < lim) ? Cr[(int64_t)i * a.ldc] : 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < lim) Cr[(int64_t)i * a.ldc] = old[i] - v[i];
+  } else {
+    const float* C1r = C1 + row + gc0 * a.ldc1;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) old[i] = (i < lim) ? C1r[(int64_t)i * a.ldc1] : 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < lim) Cr[(int64_t)i * a.ldc] = v[i] + old[i];
+  }
+}
+
 __device__ __forceinline__ uint32_t tf32_bits(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -267,20 +297,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
       const int col0 = col_half * (TC_BN / 2) + cc;
       float v[32];
       tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)col0, v);
-      if (row < a.M) {
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int64_t gc = n0 + col0 + i;
-          if (gc < a.N) {
-            if (a.epi == TC_EPI_SUB)
-              C[row + gc * a.ldc] -= v[i];
-            else if (a.epi == TC_EPI_OUT)
-              C[row + gc * a.ldc] = v[i];
-            else
-              C[row + gc * a.ldc] = v[i] + C1[row + gc * a.ldc1];
-          }
-        }
-      }
+      tc_epi32(a, C, C1, row, n0 + col0, v);
     }
   } else if (tid == 0 && a.status != nullptr) {
     atomicCAS(&a.status[ST_CODE], 0, -6);
@@ -526,20 +543,199 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc2(TcArgs a) {
       for (int cc = 0; cc < P_BN; cc += 32) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(h * P_BN + cc), v);
-        if (row < a.M) {
+        tc_epi32(a, C, C1, row, n0 + cc, v);
+      }
+    }
+  } else if (tid == 0 && a.status != nullptr) {
+    atomicCAS(&a.status[ST_CODE], 0, -6);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// Same contraction with the B operand streamed by cp.async (16-byte copies, zero fill
+// past N) into a 4-slot raw ring that runs three K chunks ahead of the tensor cores, so
+// that every SM keeps ~48 KB of B loads in flight; the raw chunk is split into TF32 hi/lo
+// in shared memory right before its MMAs.  Requires a column-major B with ldb % 4 == 0,
+// a 16-byte aligned base, sB % 4 == 0 and K % 16 == 0 (checked by the launcher).
+constexpr int V_STAGES = 2;                              // MMA operand stages (A + B hi/lo)
+constexpr int V_RAW = 4;                                 // raw B ring slots
+constexpr int V_RAWB = P_BN * P_BK * 4;                  // 16 KB raw chunk
+constexpr int V_SMEM = V_STAGES * P_STAGE + V_RAW * V_RAWB + 256;
+
+__device__ __forceinline__ void cp_async16_zfill(void* sdst, const void* gsrc, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(sdst)), "l"(gsrc),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Raw chunk layout: column c of the tile at c * 64 bytes (16 consecutive K values).
+__device__ __forceinline__ void v_issue_b(unsigned char* raw, const float* B, int64_t ldb,
+                                          int64_t N, int64_t n0, int k0) {
+  for (int idx = threadIdx.x; idx < P_BN * (P_BK / 4); idx += TC_THREADS) {
+    const int q = idx & 3, c = idx >> 2;
+    const int64_t gc = n0 + c;
+    const bool in = gc < N;
+    const float* src = in ? B + (k0 + 4 * q) + gc * ldb : B;
+    cp_async16_zfill(raw + idx * 16, src, in ? 16u : 0u);
+  }
+}
+
+__device__ __forceinline__ void v_convert_b(unsigned char* bst, const unsigned char* raw) {
+  unsigned char* bhi = bst;
+  unsigned char* blo = bst + P_BN * P_BK * 4;
+  for (int idx = threadIdx.x; idx < P_BN * (P_BK / 4); idx += TC_THREADS) {
+    const int q = idx & 3, c = idx >> 2;
+    const float4 x = *reinterpret_cast<const float4*>(raw + idx * 16);
+    uint4 h, l;
+    h.x = tf32_bits(x.x); l.x = tf32_bits(x.x - __uint_as_float(h.x));
+    h.y = tf32_bits(x.y); l.y = tf32_bits(x.y - __uint_as_float(h.y));
+    h.z = tf32_bits(x.z); l.z = tf32_bits(x.z - __uint_as_float(h.z));
+    h.w = tf32_bits(x.w); l.w = tf32_bits(x.w - __uint_as_float(h.w));
+    const uint32_t off = kmajor_off16(c, 4 * q);
+    *reinterpret_cast<uint4*>(bhi + off) = h;
+    *reinterpret_cast<uint4*>(blo + off) = l;
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc2v(TcArgs a) {
+  if (a.dec != nullptr && a.dec[a.k_step] != a.want) return;
+  extern __shared__ __align__(1024) unsigned char smem_v[];
+  unsigned char* rawbase = smem_v + V_STAGES * P_STAGE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(rawbase + V_RAW * V_RAWB);
+  uint64_t* empty = full + V_STAGES;
+  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(empty + V_STAGES);
+  int* s_fail = reinterpret_cast<int*>(taddr_slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t m0 = (int64_t)blockIdx.y * 256, n0 = (int64_t)blockIdx.x * P_BN;
+  const int64_t t = blockIdx.z;
+  const int nK = a.K / P_BK;
+  const int mh = (a.M - m0) > 128 ? 2 : 1;
+  const unsigned char* Apk = a.Apk + t * a.sApk;
+  const float* B = a.B + t * a.sB;
+  float* C = a.C + t * a.sC;
+  const float* C1 = a.C1 ? a.C1 + t * a.sC1 : nullptr;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(taddr_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // tid 0 bookkeeping: last chunk whose A copy was issued / seen landed, last MMA commit
+  int a_issued = -1, a_landed = -1, last_commit = -1;
+  auto issue_a = [&](int c) {
+    const int st = c % V_STAGES;
+    unsigned char* sa = smem_v + st * P_STAGE;
+    mbar_expect_tx(&full[st], (uint32_t)mh * 2 * P_ABLK);
+    for (int h = 0; h < mh; ++h) {
+      const unsigned char* src = Apk + (((int64_t)(m0 / 128 + h) * nK + c) * 2 * P_ABLK);
+      bulk_g2s(sa + h * 2 * P_ABLK, src, 2 * P_ABLK, &full[st]);
+    }
+    a_issued = c;
+  };
+  if (tid == 0) {
+    *s_fail = 0;
+    for (int q = 0; q < V_STAGES; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *taddr_slot;
+  const uint32_t idesc = make_idesc_tf32(128, P_BN);
+  if (tid == 0)
+    for (int c = 0; c < V_STAGES && c < nK; ++c) issue_a(c);
+  for (int p = 0; p < V_RAW - 1; ++p) {
+    if (p < nK) v_issue_b(rawbase + p * V_RAWB, B, a.ldb, a.N, n0, p * P_BK);
+    cp_async_commit();
+  }
+  for (int c = 0; c < nK; ++c) {
+    const int st = c % V_STAGES;
+    unsigned char* sb = smem_v + st * P_STAGE + P_ASTAGE;
+    const int pf = c + V_RAW - 1;
+    if (pf < nK) v_issue_b(rawbase + (pf % V_RAW) * V_RAWB, B, a.ldb, a.N, n0, pf * P_BK);
+    cp_async_commit();
+    cp_async_wait_group<V_RAW - 1>();
+    __syncthreads();                 // raw chunk c complete in every thread; stage st free
+    if (*s_fail) break;
+    v_convert_b(sb, rawbase + (c % V_RAW) * V_RAWB);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      if (!mbar_wait(&full[st], (uint32_t)(c / V_STAGES) & 1)) {
+        *s_fail = 1;
+      } else {
+        a_landed = c;
+        const uint32_t sbase = smem_u32(sb);
+        const unsigned char* sa = smem_v + st * P_STAGE;
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const int64_t gc = n0 + cc + i;
-            if (gc < a.N) {
-              if (a.epi == TC_EPI_SUB)
-                C[row + gc * a.ldc] -= v[i];
-              else if (a.epi == TC_EPI_OUT)
-                C[row + gc * a.ldc] = v[i];
-              else
-                C[row + gc * a.ldc] = v[i] + C1[row + gc * a.ldc1];
-            }
+        for (int s8 = 0; s8 < P_BK / 8; ++s8) {
+          const uint32_t koff = (uint32_t)s8 * 2 * TC_LBO;
+          const uint64_t bhi = make_desc_sbo(sbase + koff, P_SBO);
+          const uint64_t blo = make_desc_sbo(sbase + P_BN * P_BK * 4 + koff, P_SBO);
+          for (int h = 0; h < mh; ++h) {
+            const uint32_t abase = smem_u32(sa + h * 2 * P_ABLK);
+            const uint64_t ahi = make_desc_sbo(abase + koff, P_SBO);
+            const uint64_t alo = make_desc_sbo(abase + P_ABLK + koff, P_SBO);
+            const uint32_t d = tmem + (uint32_t)(h * P_BN);
+            const uint32_t acc0 = (c > 0 || s8 > 0) ? 1u : 0u;
+            tc_mma(d, alo, bhi, idesc, acc0);
+            tc_mma(d, ahi, blo, idesc, 1u);
+            tc_mma(d, ahi, bhi, idesc, 1u);
           }
         }
+        tc_commit(&empty[st]);
+        last_commit = c;
+        // the next chunk's A goes into the stage of chunk c+1-V_STAGES once its MMAs are done
+        const int nx = c + 1;
+        if (nx < nK && nx >= V_STAGES) {
+          const int pst = nx % V_STAGES;
+          if (!mbar_wait(&empty[pst], (uint32_t)(nx / V_STAGES - 1) & 1)) *s_fail = 1;
+          else issue_a(nx);
+        }
+      }
+    }
+  }
+  cp_async_wait_group<0>();
+  __syncthreads();
+  bool ok = *s_fail == 0;
+  if (tid == 0) {
+    // every issued MMA and every issued copy must be complete before TMEM and shared
+    // memory are released (bounded waits; a timeout leaves the error flag set)
+    if (last_commit >= 0 &&
+        !mbar_wait(&empty[last_commit % V_STAGES], (uint32_t)(last_commit / V_STAGES) & 1))
+      ok = false;
+    for (int q = a_landed + 1; q <= a_issued; ++q)
+      if (!mbar_wait(&full[q % V_STAGES], (uint32_t)(q / V_STAGES) & 1)) ok = false;
+    if (!ok) *s_fail = 1;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const bool all_ok = *s_fail == 0;
+  if (all_ok) {
+    const int h = warp >> 2;
+    const int lane_base = (warp & 3) * 32;
+    const int64_t row = m0 + h * 128 + lane_base + lane;
+    if (h < mh) {
+      for (int cc = 0; cc < P_BN; cc += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(h * P_BN + cc), v);
+        tc_epi32(a, C, C1, row, n0 + cc, v);
       }
     }
   } else if (tid == 0 && a.status != nullptr) {
@@ -571,10 +767,16 @@ void launch_tc_pack(const float* A, int64_t lda, int64_t sA, int a_trans, int a_
 
 void launch_tc2(const TcArgs& a, int batch, const char* name, cudaStream_t s) {
   if (a.M <= 0 || a.N <= 0 || a.K <= 0 || batch <= 0) return;
-  ensure_dyn_smem<k_gemm_tc2>(P_SMEM);
   dim3 grid((unsigned)((a.N + P_BN - 1) / P_BN), (unsigned)((a.M + 255) / 256), (unsigned)batch);
-  {
-    ProfScope ps_(name, s);
+  const bool vec = !a.b_trans && a.b_mask == TC_MASK_NONE && (a.K % P_BK) == 0 &&
+                   (a.ldb % 4) == 0 && (a.sB % 4) == 0 &&
+                   (reinterpret_cast<uintptr_t>(a.B) % 16) == 0;
+  ProfScope ps_(name, s);
+  if (vec) {
+    ensure_dyn_smem<k_gemm_tc2v>(V_SMEM);
+    k_gemm_tc2v<<<grid, TC_THREADS, V_SMEM, s>>>(a);
+  } else {
+    ensure_dyn_smem<k_gemm_tc2>(P_SMEM);
     k_gemm_tc2<<<grid, TC_THREADS, P_SMEM, s>>>(a);
   }
 }

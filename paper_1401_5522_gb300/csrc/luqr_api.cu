@@ -57,6 +57,19 @@ struct luqr_handle {
   unsigned char* Apk[2] = {nullptr, nullptr};   // packed QR operands (V^T, V T^T, T^T) per tile
   unsigned char* Lpk[2] = {nullptr, nullptr};   // packed LU panel (rows below the diagonal)
   size_t pk_tile = 0;                           // bytes of one packed nb x nb operand
+  // decision predictor and speculation (spec_stream factors predicted-QR panels on the
+  // shadow copy while the criterion runs on the panel stream)
+  int speculate = 0;
+  const float* mlp = nullptr;
+  float* feat = nullptr;        // n x 16 features (when logged)
+  uint8_t* spec = nullptr;      // predicted decision per step
+  uint8_t* qrfac = nullptr;     // QR chosen and not speculated: factor in place
+  uint8_t* cmt = nullptr;       // QR chosen and speculated: commit the shadow copy
+  void* shadow = nullptr;       // Npad x nb copy of the panel column (same leading dimension)
+  cudaStream_t spec_stream = nullptr;
+  cudaStream_t panel_stream = nullptr;   // high priority; the caller's stream waits on it
+  std::vector<cudaEvent_t> ev_stats, ev_spec;
+  cudaEvent_t ev_end = nullptr;
   // second pass / refinement scratch
   void* rhs_ws = nullptr;
   int rhs_cap = 0;
@@ -174,40 +187,11 @@ void tc_apply_pair(luqr_handle* h, int k, TileList tl, bool tri, Mat<float> C, i
   launch_tc2(a, tl.count, tri ? "k_tc_ttmqr_c2" : "k_tc_tsmqr_c2", s);
 }
 
-template <typename T>
-void enqueue_qr(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, bool do_factor,
-                bool do_apply, cudaStream_t s, bool tc = false) {
-  const int n = h->n, nb = h->nb, m = n - 1 - k;
-  Mat<T> F{wsT<T>(h), h->Npad};
-  Mat<const T> Fc{wsT<T>(h), h->Npad};
-  T* Tk = static_cast<T*>(h->Tbuf) + (size_t)k * t_step_elems(h);
-  const uint8_t* dec = h->dec;
-  constexpr bool is_f32 = std::is_same<T, float>::value;
-  tc = tc && is_f32 && h->use_tc_qr;
-  auto single = [&](TileList tl) {
-    if (do_factor) {
-      launch_geqrt<T>(F, k, nb, tl, Tk, n, dec, s);
-      if (tc) tc_factor_extra(h, k, tl, 0, TC_MASK_UNIT_LOWER, s);
-    }
-    if (do_apply) {
-      if constexpr (is_f32) {
-        if (tc) { tc_apply_single(h, k, tl, C, c0, c1, s); return; }
-      }
-      launch_unmqr<T>(Fc, k, nb, tl, Tk, n, C, c0, c1, dec, s);
-    }
-  };
-  auto pair = [&](TileList tl, bool tri) {
-    if (do_factor) {
-      launch_pair_qrt<T>(F, k, nb, tl, tri, Tk, n, dec, s);
-      if (tc) tc_factor_extra(h, k, tl, 1, tri ? TC_MASK_UPPER : TC_MASK_NONE, s);
-    }
-    if (do_apply) {
-      if constexpr (is_f32) {
-        if (tc) { tc_apply_pair(h, k, tl, tri, C, c0, c1, s); return; }
-      }
-      launch_pair_apply<T>(Fc, k, nb, tl, tri, Tk, n, C, c0, c1, dec, s);
-    }
-  };
+// Visits the tile lists of step k's elimination tree in execution order:
+// single(tl) for the tiles factored by GEQRT, pair(tl, tri) for the TS / TT levels.
+template <typename FS, typename FP>
+void for_each_tile_list(const luqr_handle* h, int k, FS&& single, FP&& pair) {
+  const int n = h->n, m = n - 1 - k;
   if (h->tree == LUQR_TREE_FLAT_TS) {
     single(TileList{k, 1, 1, 0});
     for (int i = k + 1; i < n; ++i) pair(TileList{i, 1, 1, i - k}, false);
@@ -231,6 +215,63 @@ void enqueue_qr(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, bool do
       pair(TileList{k + step * g, 2 * step * g, count, step * g}, true);
     }
   }
+}
+
+// Enqueues the QR step of panel k along the handle's tree.  do_factor factors the panel
+// tiles, do_apply applies the step's transformations to columns [c0, c1) of C.
+// The factorization works on column k of fbase (default: the workspace; the shadow copy
+// is passed with its base shifted by k*nb columns) and runs when fdec[k] == QR (default:
+// the decision).  extras = false leaves the tensor-core operand preparation to
+// enqueue_qr_extras.
+template <typename T>
+void enqueue_qr(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, bool do_factor,
+                bool do_apply, cudaStream_t s, bool tc = false, T* fbase = nullptr,
+                const uint8_t* fdec = nullptr, bool extras = true) {
+  const int n = h->n, nb = h->nb;
+  Mat<T> F{fbase ? fbase : wsT<T>(h), h->Npad};
+  Mat<const T> Fc{wsT<T>(h), h->Npad};
+  T* Tk = static_cast<T*>(h->Tbuf) + (size_t)k * t_step_elems(h);
+  const uint8_t* dec = h->dec;
+  const uint8_t* fd = fdec ? fdec : h->dec;
+  constexpr bool is_f32 = std::is_same<T, float>::value;
+  tc = tc && is_f32 && h->use_tc_qr;
+  auto single = [&](TileList tl) {
+    if (do_factor) {
+      launch_geqrt<T>(F, k, nb, tl, Tk, n, fd, s);
+      if (tc && extras) tc_factor_extra(h, k, tl, 0, TC_MASK_UNIT_LOWER, s);
+    }
+    if (do_apply) {
+      if constexpr (is_f32) {
+        if (tc) { tc_apply_single(h, k, tl, C, c0, c1, s); return; }
+      }
+      launch_unmqr<T>(Fc, k, nb, tl, Tk, n, C, c0, c1, dec, s);
+    }
+  };
+  auto pair = [&](TileList tl, bool tri) {
+    if (do_factor) {
+      launch_pair_qrt<T>(F, k, nb, tl, tri, Tk, n, fd, s);
+      if (tc && extras) tc_factor_extra(h, k, tl, 1, tri ? TC_MASK_UPPER : TC_MASK_NONE, s);
+    }
+    if (do_apply) {
+      if constexpr (is_f32) {
+        if (tc) { tc_apply_pair(h, k, tl, tri, C, c0, c1, s); return; }
+      }
+      launch_pair_apply<T>(Fc, k, nb, tl, tri, Tk, n, C, c0, c1, dec, s);
+    }
+  };
+  for_each_tile_list(h, k, single, pair);
+}
+
+// Tensor-core operand preparation of QR step k (Gram, full T, V T^T, packed operands) for
+// a panel already factored in the workspace.  Every reflector block V stays untouched by
+// the later levels of the tree (they only update R parts), so it can run after the chain.
+void enqueue_qr_extras(luqr_handle* h, int k, cudaStream_t s) {
+  if (!h->use_tc_qr) return;
+  for_each_tile_list(
+      h, k, [&](TileList tl) { tc_factor_extra(h, k, tl, 0, TC_MASK_UNIT_LOWER, s); },
+      [&](TileList tl, bool tri) {
+        tc_factor_extra(h, k, tl, 1, tri ? TC_MASK_UPPER : TC_MASK_NONE, s);
+      });
 }
 
 // ---------------------------------------------------------------- LU step on a target
@@ -262,20 +303,26 @@ void enqueue_lu_apply(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, c
 
 template <typename T>
 void enqueue_factor(luqr_handle* h) {
-  cudaStream_t s = h->stream, su = h->upd_stream;
+  // The panel chain runs on a high-priority internal stream so that its small kernels are
+  // scheduled ahead of the bulk update's blocks; the caller's stream waits for both.
+  cudaStream_t s = h->panel_stream, su = h->upd_stream, sp = h->spec_stream;
   const int n = h->n, nb = h->nb;
   const int64_t ld = h->Npad;
   T* W = wsT<T>(h);
   T* S = static_cast<T*>(h->S);
+  T* shadow = static_cast<T*>(h->shadow);
   Mat<T> F{W, ld};
   const bool need_inv = (h->forced == nullptr) &&
                         (h->criterion == LUQR_MAX || h->criterion == LUQR_SUM) && h->alpha != 0.0;
-  cudaEventRecord(h->ev_start, s);
+  const bool spec = h->speculate != 0;
+  cudaEventRecord(h->ev_start, h->stream);
+  cudaStreamWaitEvent(s, h->ev_start, 0);
   cudaStreamWaitEvent(su, h->ev_start, 0);
+  if (spec) cudaStreamWaitEvent(sp, h->ev_start, 0);
   for (int k = 0; k < n; ++k) {
     const int64_t r0 = (int64_t)k * nb, r1 = r0 + nb;
     const int64_t la_end = std::min<int64_t>(r1 + nb, h->Npad);   // look-ahead column k+1
-    // ---- panel k on the caller's stream (column k is complete: see the waits below)
+    // ---- panel k on the panel stream (column k is complete: see the waits below)
     if (h->injected[k]) {
       // the injected row spans every column >= k: wait for the previous bulk update
       if (k > 0) cudaStreamWaitEvent(s, h->ev_rest[k - 1], 0);
@@ -283,12 +330,26 @@ void enqueue_factor(luqr_handle* h) {
     }
     launch_panel_stats<T>(W, ld, k, n, nb, h->norms + (size_t)k * n, h->local, h->away, h->status,
                           s);
+    if (h->feat || spec)
+      launch_features_spec<T>(W, ld, k, n, nb, h->alpha, h->criterion, h->norms + (size_t)k * n,
+                              h->local, h->away, h->dec, h->margin, h->feat, h->speculate, h->mlp,
+                              h->spec, s);
+    if (spec) {
+      // predicted QR: factor a copy of column k while GETRF and the criterion run
+      cudaEventRecord(h->ev_stats[k], s);
+      cudaStreamWaitEvent(sp, h->ev_stats[k], 0);
+      launch_gated_copy<T>(W + r0 + r0 * ld, ld, shadow + r0, ld, h->Npad - r0, nb, h->spec, k,
+                           DEC_QR, "k_spec_copy", sp);
+      enqueue_qr<T>(h, k, F, 0, 0, true, false, sp, true, shadow - r0 * ld, h->spec, false);
+      cudaEventRecord(h->ev_spec[k], sp);
+    }
     launch_getrf<T>(W, ld, k, nb, S, h->piv_s, h->status, s);
     if (need_inv) launch_invnorm<T>(S, nb, h->piv_s, h->colsum, h->status, s);
     DecideArgs da{k,        n,         nb,       h->criterion, h->mumps_mode, h->alpha,
                   h->norms + (size_t)k * n, h->colsum, h->local, h->away,     h->forced,
                   h->dec,   h->margin, h->lhs,   h->rhs,       h->status};
     launch_decide<T>(da, S, s);
+    if (spec) launch_spec_resolve(k, h->dec, h->spec, h->qrfac, h->cmt, s);
     // ---- factor the panel: LU (Alg. 2: commit + TRSM) or QR (GEQRT + TS/TT chain)
     launch_lu_commit<T>(W, ld, k, nb, S, h->piv_s, h->piv_all + (size_t)k * nb, h->dec, s);
     Mat<const T> LU{W + r0 + r0 * ld, ld};
@@ -298,7 +359,15 @@ void enqueue_factor(luqr_handle* h) {
         launch_tc_pack(reinterpret_cast<float*>(W) + r1 + r0 * ld, ld, 0, 0, TC_MASK_NONE,
                        h->Npad - r1, nb, h->Lpk[k & 1], 0, 1, h->dec, k, DEC_LU, s);
     }
-    enqueue_qr<T>(h, k, F, 0, 0, true, false, s, true);
+    if (spec) {
+      enqueue_qr<T>(h, k, F, 0, 0, true, false, s, true, nullptr, h->qrfac, false);
+      cudaStreamWaitEvent(s, h->ev_spec[k], 0);
+      launch_gated_copy<T>(shadow + r0, ld, W + r0 + r0 * ld, ld, h->Npad - r0, nb, h->cmt, k,
+                           DEC_QR, "k_spec_commit", s);
+      if constexpr (std::is_same<T, float>::value) enqueue_qr_extras(h, k, s);
+    } else {
+      enqueue_qr<T>(h, k, F, 0, 0, true, false, s, true);
+    }
     cudaEventRecord(h->ev_fact[k], s);
     // ---- bulk update of columns >= k+2 (and b) on the update stream
     if (la_end < h->Wc) {
@@ -315,6 +384,8 @@ void enqueue_factor(luqr_handle* h) {
     }
   }
   cudaStreamWaitEvent(s, h->ev_rest[n - 1], 0);
+  cudaEventRecord(h->ev_end, s);
+  cudaStreamWaitEvent(h->stream, h->ev_end, 0);
 }
 
 template <typename T>
@@ -364,12 +435,18 @@ void free_handle(luqr_handle* h) {
   for (cudaEvent_t e : h->ev_fact) if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : h->ev_rest) if (e) cudaEventDestroy(e);
   if (h->ev_start) cudaEventDestroy(h->ev_start);
+  for (cudaEvent_t e : h->ev_stats) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_spec) if (e) cudaEventDestroy(e);
+  if (h->ev_end) cudaEventDestroy(h->ev_end);
   if (h->upd_stream) cudaStreamDestroy(h->upd_stream);
+  if (h->spec_stream) cudaStreamDestroy(h->spec_stream);
+  if (h->panel_stream) cudaStreamDestroy(h->panel_stream);
   void* ptrs[] = {h->W,      h->Tbuf,     h->S,        h->piv_s, h->piv_all, h->norms,
                   h->local,  h->away,     h->colsum,   h->dec,   h->margin,  h->lhs,
                   h->rhs,    h->status,   h->forced,   h->rhs_ws, h->ref,    h->Wbuf,
                   h->Gbuf,   h->Tfull[0], h->Tfull[1], h->Vt[0], h->Vt[1], h->gm,
-                  h->Apk[0], h->Apk[1],   h->Lpk[0],   h->Lpk[1]};
+                  h->Apk[0], h->Apk[1],   h->Lpk[0],   h->Lpk[1], h->feat, h->spec,
+                  h->qrfac,  h->cmt,      h->shadow};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -528,6 +605,8 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   if (o.tree < 0 || o.tree > 2 || o.precision < 0 || o.precision > 1) return LUQR_ERR_INVALID;
   if (o.fp32_kernels < 0 || o.fp32_kernels > 2) return LUQR_ERR_INVALID;
   if (o.mumps_mode < 0 || o.mumps_mode > 1 || o.n_inject < 0) return LUQR_ERR_INVALID;
+  if (o.speculate < 0 || o.speculate > 2 || (o.speculate == 1 && !o.mlp_params))
+    return LUQR_ERR_INVALID;
   luqr_handle* h = new (std::nothrow) luqr_handle();
   if (!h) return LUQR_ERR_NOMEM;
   h->N = N;
@@ -587,13 +666,38 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
       A((void**)&h->Vt[q], sizeof(float) * slots);
     }
   }
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->upd_stream, cudaStreamNonBlocking);
+  h->speculate = o.speculate;
+  h->mlp = o.mlp_params;
+  if (o.log_features || o.speculate) A((void**)&h->feat, sizeof(float) * 16 * (size_t)n);
+  if (o.speculate) {
+    A((void**)&h->spec, (size_t)n);
+    A((void**)&h->qrfac, (size_t)n);
+    A((void**)&h->cmt, (size_t)n);
+    A(&h->shadow, (size_t)h->Npad * nb * h->elt);
+  }
+  int prio_low = 0, prio_high = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+  if (e == cudaSuccess)
+    e = cudaStreamCreateWithPriority(&h->upd_stream, cudaStreamNonBlocking, prio_low);
+  if (e == cudaSuccess)
+    e = cudaStreamCreateWithPriority(&h->panel_stream, cudaStreamNonBlocking, prio_high);
+  if (e == cudaSuccess && o.speculate)
+    e = cudaStreamCreateWithPriority(&h->spec_stream, cudaStreamNonBlocking, prio_high);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_end, cudaEventDisableTiming);
   h->ev_fact.assign(n, nullptr);
   h->ev_rest.assign(n, nullptr);
   for (int q = 0; q < n && e == cudaSuccess; ++q) {
     e = cudaEventCreateWithFlags(&h->ev_fact[q], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_rest[q], cudaEventDisableTiming);
+  }
+  if (o.speculate) {
+    h->ev_stats.assign(n, nullptr);
+    h->ev_spec.assign(n, nullptr);
+    for (int q = 0; q < n && e == cudaSuccess; ++q) {
+      e = cudaEventCreateWithFlags(&h->ev_stats[q], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_spec[q], cudaEventDisableTiming);
+    }
   }
   if (e != cudaSuccess) {
     free_handle(h);
@@ -713,6 +817,24 @@ int luqr_refine_gmres(luqr_handle_t h, const double* dA, int64_t lda, const doub
   if (h->prec == LUQR_PREC_FP64)
     return refine_gmres_impl<double>(h, dA, lda, db, dx, tol, max_iter, restart, iters, eta);
   return refine_gmres_impl<float>(h, dA, lda, db, dx, tol, max_iter, restart, iters, eta);
+}
+
+int luqr_features(luqr_handle_t h, float* feat, uint8_t* predicted, int* n_out) {
+  if (!h || !h->feat) return LUQR_ERR_INVALID;
+  int code = read_status(h, nullptr);
+  if (feat && cudaMemcpy(feat, h->feat, sizeof(float) * 16 * (size_t)h->n,
+                         cudaMemcpyDeviceToHost) != cudaSuccess)
+    return LUQR_ERR_CUDA;
+  if (predicted) {
+    if (h->spec) {
+      if (cudaMemcpy(predicted, h->spec, (size_t)h->n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return LUQR_ERR_CUDA;
+    } else {
+      std::memset(predicted, LUQR_DEC_ABORTED, (size_t)h->n);
+    }
+  }
+  if (n_out) *n_out = h->n;
+  return code;
 }
 
 int luqr_decisions(luqr_handle_t h, uint8_t* dec, double* margin, int* n_out) {

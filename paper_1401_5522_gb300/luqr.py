@@ -25,6 +25,8 @@ PREC_FP64, PREC_FP32 = 0, 1
 CRITERIA = {"max": MAX, "sum": SUM, "mumps": MUMPS, "force_lu": FORCE_LU, "force_qr": FORCE_QR}
 TREES = {"flat_ts": TREE_FLAT_TS, "binary_tt": TREE_BINARY_TT, "grouped": TREE_GROUPED}
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32}
+SPECULATE = {"off": 0, "mlp": 1, "repeat": 2}
+MLP_FEATURES, MLP_PARAMS = 16, 5313
 
 
 class LuqrError(RuntimeError):
@@ -38,7 +40,9 @@ class Options(ctypes.Structure):
     _fields_ = [("tree", ctypes.c_int), ("group", ctypes.c_int), ("precision", ctypes.c_int),
                 ("mumps_mode", ctypes.c_int), ("forced", ctypes.POINTER(ctypes.c_uint8)),
                 ("inject", ctypes.POINTER(ctypes.c_int)), ("n_inject", ctypes.c_int),
-                ("fp32_kernels", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("fp32_kernels", ctypes.c_int), ("speculate", ctypes.c_int),
+                ("log_features", ctypes.c_int), ("mlp_params", ctypes.c_void_p),
+                ("reserved", ctypes.c_int * 8)]
 
 
 _lib = None
@@ -76,6 +80,11 @@ _SIGS = {
     "luqr_batched_run": (ctypes.c_int, [_P, _P]),
     "luqr_batched_results": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
     "luqr_batched_destroy": (None, [_P]),
+    "luqr_mlp_forward": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+    "luqr_mlp_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P]),
+    "luqr_mlp_adam": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_float, ctypes.c_float, _P]),
+    "luqr_features": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
     "luqr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "luqr_version": (ctypes.c_char_p, []),
 }
@@ -148,6 +157,17 @@ class Handle:
         if st not in (OK,):
             raise LuqrError(st, "luqr_decisions")
         return dec, mg
+
+    def features(self):
+        """(features float32[n, 16], predicted uint8[n]) logged during the factorization."""
+        feat = np.zeros((self.n, MLP_FEATURES), dtype=np.float32)
+        pred = np.zeros(self.n, dtype=np.uint8)
+        nout = ctypes.c_int()
+        st = lib().luqr_features(self._ptr(), feat.ctypes.data_as(_P), pred.ctypes.data_as(_P),
+                                 ctypes.byref(nout))
+        if st != OK:
+            raise LuqrError(st, "luqr_features")
+        return feat, pred
 
     def step_stats(self):
         lhs = np.zeros(self.n)
@@ -238,8 +258,11 @@ class Handle:
 
 def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
            precision="fp64", mumps_mode=0, forced=None, inject=None, stream=None,
-           fp32_kernels="default"):
-    """luqr_factor on a column-major float64 CUDA matrix; b (if given) is overwritten by x."""
+           fp32_kernels="default", speculate="off", mlp_params=None, log_features=False):
+    """luqr_factor on a column-major float64 CUDA matrix; b (if given) is overwritten by x.
+
+    speculate: "off", "mlp" (mlp_params: float32 CUDA tensor of MLP_PARAMS values, kept
+    alive by the caller until the factorization has run) or "repeat"."""
     N = A.shape[0]
     lda = _check_matrix(A)
     crit = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
@@ -249,6 +272,14 @@ def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
     opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     opt.mumps_mode = int(mumps_mode)
     opt.fp32_kernels = {"default": 0, "cuda": 1, "tensor": 2}[fp32_kernels]
+    opt.speculate = SPECULATE[speculate] if isinstance(speculate, str) else int(speculate)
+    opt.log_features = 1 if log_features else 0
+    if mlp_params is not None:
+        import torch
+        if not (mlp_params.is_cuda and mlp_params.dtype == torch.float32 and
+                mlp_params.is_contiguous() and mlp_params.numel() == MLP_PARAMS):
+            raise TypeError(f"mlp_params must be a contiguous float32 CUDA tensor of {MLP_PARAMS}")
+        opt.mlp_params = mlp_params.data_ptr()
     keep = []
     if forced is not None:
         fa = np.ascontiguousarray(np.asarray(forced, dtype=np.uint8))
@@ -328,3 +359,43 @@ def panel_test_noalloc(panel, nb, criterion="max", alpha=100.0, mumps_mode=0, de
     if st != OK:
         raise LuqrError(st, "luqr_panel_test_noalloc")
     return dec, margin
+
+
+def _f32_cuda(t, what):
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError(f"{what} must be a contiguous float32 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def mlp_forward(params, X, out=None, stream=None):
+    """Logits of the decision MLP for X (B x 16 float32 CUDA)."""
+    import torch
+    B = X.shape[0]
+    if out is None:
+        out = torch.empty(B, dtype=torch.float32, device=X.device)
+    st = lib().luqr_mlp_forward(_f32_cuda(params, "params"), _f32_cuda(X, "X"),
+                                _f32_cuda(out, "out"), B, _stream_ptr(stream))
+    if st != OK:
+        raise LuqrError(st, "luqr_mlp_forward")
+    return out
+
+
+def mlp_grad(params, X, y, grad, loss=None, stream=None):
+    """Adds the mean-BCE gradient over (X, y) to grad (and the loss to loss[0])."""
+    st = lib().luqr_mlp_grad(_f32_cuda(params, "params"), _f32_cuda(X, "X"), _f32_cuda(y, "y"),
+                             X.shape[0], _f32_cuda(grad, "grad"),
+                             None if loss is None else _f32_cuda(loss, "loss"), _stream_ptr(stream))
+    if st != OK:
+        raise LuqrError(st, "luqr_mlp_grad")
+    return grad
+
+
+def mlp_adam(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """One Adam step at iteration t >= 1 (in place on params, m, v)."""
+    st = lib().luqr_mlp_adam(_f32_cuda(params, "params"), _f32_cuda(grad, "grad"), _f32_cuda(m, "m"),
+                             _f32_cuda(v, "v"), int(t), float(lr), float(beta1), float(beta2),
+                             float(eps), _stream_ptr(stream))
+    if st != OK:
+        raise LuqrError(st, "luqr_mlp_adam")
+    return params

@@ -24,3 +24,44 @@ def test_parameter_count_and_layout():
     p = np.arange(M.NPARAMS, dtype=float)
     q = M.unpack(p)
     assert q["W1"][0, 1] == 1 and q["b1"][0] == 1024 and q["b3"][0] == M.NPARAMS - 1
+
+
+def test_zero_network_closed_forms():
+    # all-zero parameters: every logit is 0, the loss is log 2 and only b3 and W3 see a
+    # gradient through the (zero) hidden layers: d/db3 = mean(sigmoid(0) - y)
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((7, M.F))
+    y = np.array([1, 0, 1, 1, 0, 0, 1], dtype=float)
+    L, g = M.loss_and_grad(np.zeros(M.NPARAMS), X, y)
+    assert abs(L - np.log(2.0)) < 1e-15
+    assert abs(g[-1] - np.mean(0.5 - y)) < 1e-15
+    assert np.all(g[:-1] == 0.0)
+
+
+def test_adam_first_step_is_signed_learning_rate():
+    # at t = 1 the bias-corrected moments are g and g^2, so every parameter moves by
+    # lr * g / (|g| + eps), i.e. lr * sign(g) for |g| >> eps (Kingma and Ba, Sec. 2)
+    rng = np.random.default_rng(4)
+    p = rng.standard_normal(50)
+    g = rng.standard_normal(50)
+    p1, m, v = M.adam_step(p, g, np.zeros(50), np.zeros(50), 1, lr=0.01)
+    np.testing.assert_allclose(p - p1, 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+    np.testing.assert_allclose(p - p1, 0.01 * np.sign(g), rtol=1e-5)
+    np.testing.assert_allclose(m, 0.1 * g, rtol=1e-14)
+    np.testing.assert_allclose(v, 0.001 * g * g, rtol=1e-14)
+
+
+def test_step_features_hand_computed():
+    # identity diagonal tile, tile norms 1, 2, 4, sub-diagonal column maxima 2, two prior
+    # steps (LU with margin 3, QR with margin -100), alpha 1024, MUMPS (id 2), k=2 of n=5
+    f = M.step_features(2, 5, 1024.0, 2, [1.0, 2.0, 4.0], np.eye(4), [2.0] * 4,
+                        np.array([1, 0], dtype=np.uint8), np.array([3.0, -100.0]))
+    expect = [0.0, 2.0, np.log2(6.0), 0.0, 0.0, 0.0, 1.0, 1.0, 0.0, -64.0, 3.0, 0.4, 10.0,
+              np.log2(3.0), 0.5, 0.5]
+    np.testing.assert_allclose(f, expect, rtol=0, atol=1e-15)
+    # a zero column in the diagonal tile: its away/local ratio saturates at 64
+    A = np.eye(4)
+    A[:, 1] = 0.0
+    f0 = M.step_features(0, 3, np.inf, 0, [3.0, 1.0], A, [1.0] * 4, [], [])
+    assert f0[6] == 64.0 and f0[8] == 0.5 and f0[12] == 64.0 and f0[15] == 0.0
+    assert abs(f0[7] - 16.0) < 1e-15        # mean of 0, 64, 0, 0
