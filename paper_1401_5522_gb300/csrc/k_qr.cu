@@ -254,125 +254,105 @@ __device__ __forceinline__ void make_reflector(T a0, T ss, T* beta, T* tau, T* d
   }
 }
 
-// Unblocked QR of an IB-column panel P (nrows x IB) in shared memory (GEQRT panel).
-// Warp 0 forms each reflector (norm, beta, tau, scaling by 1/(a0 - beta)); then every
-// warp applies it to its share of the remaining panel columns: two barriers per column.
-template <typename T>
-__device__ void panel_single(T* Ps, int nrows, T* tau_s, T* red, T* bc) {
-  (void)red; (void)bc;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
-  (void)tid;
-  for (int j = 0; j < IB; ++j) {
-    if (warp == 0) {
-      T part = (T)0;
-      for (int r = j + 1 + lane; r < nrows; r += 32) {
-        const T v = Ps[r * VST + j];
-        part += v * v;
-      }
-      const T ss = warp_sum<T>(part);
-      T beta, tau, denom;
-      make_reflector<T>(Ps[j * VST + j], ss, &beta, &tau, &denom);
-      const T inv = (T)1 / denom;
-      for (int r = j + 1 + lane; r < nrows; r += 32)
-        Ps[r * VST + j] = (tau == (T)0) ? (T)0 : Ps[r * VST + j] * inv;
-      __syncwarp();
-      if (lane == 0) {
-        Ps[j * VST + j] = beta;
-        tau_s[j] = tau;
-      }
-    }
-    __syncthreads();
-    const T tau = tau_s[j];
-    if (tau != (T)0) {
-      for (int c = j + 1 + warp; c < IB; c += nw) {
-        T sum = (T)0;
-        for (int r = j + 1 + lane; r < nrows; r += 32) sum += Ps[r * VST + j] * Ps[r * VST + c];
-        sum = warp_sum<T>(sum);
-        const T wc = Ps[j * VST + c] + sum;
-        __syncwarp();
-        if (lane == 0) Ps[j * VST + c] -= tau * wc;
-        for (int r = j + 1 + lane; r < nrows; r += 32) Ps[r * VST + c] -= tau * Ps[r * VST + j] * wc;
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// Unblocked QR of [Rs; Ps] for a TS/TT pair: Rs is the IB x IB upper block of the
-// eliminator rows jb.., Ps (nrows x IB) the eliminated tile's columns.  For TT the
-// reflector of column j only involves rows < jb + j + 1 of Ps.
-template <typename T>
-__device__ void panel_pair(T* Rs, T* Ps, int nrows, bool tri, int jb, T* tau_s, T* red, T* bc) {
-  (void)red; (void)bc;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
-  (void)tid;
-  for (int j = 0; j < IB; ++j) {
-    const int rows = tri ? min(jb + j + 1, nrows) : nrows;
-    if (warp == 0) {
-      T part = (T)0;
-      for (int r = lane; r < rows; r += 32) {
-        const T v = Ps[r * VST + j];
-        part += v * v;
-      }
-      const T ss = warp_sum<T>(part);
-      T beta, tau, denom;
-      make_reflector<T>(Rs[j * VST + j], ss, &beta, &tau, &denom);
-      const T inv = (T)1 / denom;
-      for (int r = lane; r < rows; r += 32)
-        Ps[r * VST + j] = (tau == (T)0) ? (T)0 : Ps[r * VST + j] * inv;
-      __syncwarp();
-      if (lane == 0) {
-        Rs[j * VST + j] = beta;
-        tau_s[j] = tau;
-      }
-    }
-    __syncthreads();
-    const T tau = tau_s[j];
-    if (tau != (T)0) {
-      for (int c = j + 1 + warp; c < IB; c += nw) {
-        T sum = (T)0;
-        for (int r = lane; r < rows; r += 32) sum += Ps[r * VST + j] * Ps[r * VST + c];
-        sum = warp_sum<T>(sum);
-        const T wc = Rs[j * VST + c] + sum;
-        __syncwarp();
-        if (lane == 0) Rs[j * VST + c] -= tau * wc;
-        for (int r = lane; r < rows; r += 32) Ps[r * VST + c] -= tau * Ps[r * VST + j] * wc;
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// T of one inner block: G[b][j] = v_b . v_j (b < j), then the forward recurrence
-// T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j], T[j][j] = tau_j.
-// single: v_j = [0..0, 1 (row j), Ps[j+1:, j]];  pair: v_j = [e_j; Ps[:, j]].
-template <typename T>
-__device__ void build_T(const T* Ps, int nrows, bool single, const T* tau_s, T* Gs, T* Ts) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
-  for (int p = warp; p < IB * IB; p += nw) {
-    const int b = p % IB, j = p / IB;
-    if (b >= j) continue;
-    T s = (T)0;
-    const int r0 = single ? j + 1 : 0;
-    for (int r = r0 + lane; r < nrows; r += 32) s += Ps[r * VST + b] * Ps[r * VST + j];
-    s = warp_sum<T>(s);
-    if (lane == 0) Gs[b * TST + j] = single ? s + Ps[j * VST + b] : s;
+// Panel QR of IB columns with the block's T built alongside (dlarfg reflectors, the
+// Schreiber-Van Loan recurrence T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j], G = V^T V).
+// SINGLE (GEQRT): the panel is Ps (nrows x IB); reflector j has a unit at row j and acts on
+//   rows j.. ; the "top" row of step j is row j of Ps.
+// pair (TS/TT):  the panel is [Rs; Ps]; reflector j is e_j in Rs plus rows [0, hi_j) of Ps
+//   (hi_j = min(jb + j + 1, nrows) for TT, nrows for TS); the top row is row j of Rs.
+// Thread (warp w, lane c) owns column c on rows r = w (mod 8), so the reductions over rows
+// are 8 partials per column; the reflector columns stay unscaled (scale 1/(a0 - beta) kept
+// in sinv) until the end of the panel, which removes one barrier per column.
+// scratch: >= 8*IB + 8 + 2*IB + 2 elements.
+template <typename T, bool SINGLE>
+__device__ void panel_qr(T* Rs, T* Ps, int nrows, bool tri, int jb, T* tau_s, T* Ts, T* scratch) {
+  static_assert(NT == 256 && IB == 32, "thread map assumes 8 warps x 32 columns");
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  T* part = scratch;               // [8][IB] partial dot products
+  T* nrm = part + 8 * IB;          // [8] partial squared norms of the next column
+  T* wv = nrm + 8;                 // [IB] w_c (c > j) or G[c][j] (c < j)
+  T* sinv = wv + IB;               // [IB] scale of each reflector column
+  T* sc = sinv + IB;               // [2] tau, inv of the current column
+  auto lo = [&](int j) { return SINGLE ? j + 1 : 0; };
+  auto hi = [&](int j) { return SINGLE ? nrows : (tri ? min(jb + j + 1, nrows) : nrows); };
+  auto top = [&](int j, int c) -> T& { return SINGLE ? Ps[j * VST + c] : Rs[j * VST + c]; };
+  const int c = lane;
+  // partial norm of column 0
+  if (c == 0) {
+    T sq = (T)0;
+    for (int r = lo(0) + ((w - lo(0)) % 8 + 8) % 8; r < hi(0); r += 8) sq += Ps[r * VST] * Ps[r * VST];
+    nrm[w] = sq;
   }
   __syncthreads();
-  if (warp == 0) {
-    for (int j = 0; j < IB; ++j) {
-      const T tj = tau_s[j];
-      T val = (T)0;
-      if (lane < j) {
-        T s = (T)0;
-        for (int b = lane; b < j; ++b) s += Ts[lane * TST + b] * Gs[b * TST + j];
-        val = -tj * s;
+  for (int j = 0; j < IB; ++j) {
+    const int l0 = lo(j), h0 = hi(j);
+    const int rs = l0 + ((w - l0) % 8 + 8) % 8;     // first row of this warp in [l0, h0)
+    // [A] partial dots of the (unscaled) column j with every column
+    {
+      T d = (T)0;
+      if (c != j)
+        for (int r = rs; r < h0; r += 8) d += Ps[r * VST + j] * Ps[r * VST + c];
+      part[w * IB + c] = d;
+    }
+    __syncthreads();
+    // [B] warp 0: reflector, w_c / G column, T column
+    if (w == 0) {
+      T ss = (T)0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) ss += nrm[q];
+      const T a0 = top(j, j);
+      T beta, tau, denom;
+      make_reflector<T>(a0, ss, &beta, &tau, &denom);
+      const T inv = (tau == (T)0) ? (T)0 : (T)1 / denom;
+      T dsum = (T)0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) dsum += part[q * IB + c];
+      if (c > j) wv[c] = top(j, c) + inv * dsum;
+      else if (c < j) wv[c] = sinv[c] * (inv * dsum + (SINGLE ? Ps[j * VST + c] : (T)0));
+      __syncwarp();
+      T tcol = (T)0;
+      if (c < j) {
+        T acc = (T)0;
+        for (int b = c; b < j; ++b) acc += Ts[c * TST + b] * wv[b];
+        tcol = -tau * acc;
+      } else if (c == j) {
+        tcol = tau;
       }
-      __syncwarp();
-      if (lane < j) Ts[lane * TST + j] = val;
-      else if (lane == j) Ts[j * TST + j] = tj;
-      else Ts[lane * TST + j] = (T)0;
-      __syncwarp();
+      Ts[c * TST + j] = tcol;
+      if (c == 0) {
+        top(j, j) = beta;
+        tau_s[j] = tau;
+        sinv[j] = inv;
+        sc[0] = tau;
+        sc[1] = inv;
+      }
+    }
+    __syncthreads();
+    // [C] update of the columns right of j; partial norm of column j+1
+    {
+      const T tau = sc[0], inv = sc[1];
+      if (c > j && tau != (T)0) {
+        const T f = tau * inv * wv[c];
+        for (int r = rs; r < h0; r += 8) Ps[r * VST + c] -= f * Ps[r * VST + j];
+        if (w == 0) top(j, c) -= tau * wv[c];
+      }
+      if (j + 1 < IB) {
+        __syncwarp();
+        if (c == j + 1) {
+          const int l1 = lo(j + 1), h1 = hi(j + 1);
+          T sq = (T)0;
+          for (int r = l1 + ((w - l1) % 8 + 8) % 8; r < h1; r += 8) sq += Ps[r * VST + c] * Ps[r * VST + c];
+          nrm[w] = sq;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // scale the reflector columns (column c: rows [lo(c), hi(c)); zero when tau = 0)
+  for (int r = w; r < nrows; r += 8) {
+    if (r >= lo(c) && r < hi(c)) {
+      const T f = sinv[c];
+      Ps[r * VST + c] = (f == (T)0) ? (T)0 : Ps[r * VST + c] * f;
     }
   }
   __syncthreads();
@@ -425,8 +405,7 @@ __global__ void __launch_bounds__(NT) k_geqrt(Mat<T> F, int k, int nb, TileList 
     }
     cp_async_wait_all();
     __syncthreads();
-    panel_single<T>(Ps, nrows, tau_s, red, bc);
-    build_T<T>(Ps, nrows, true, tau_s, Gs, Ts);
+    panel_qr<T, true>(nullptr, Ps, nrows, false, jb, tau_s, Ts, Gs);
     for (int idx = tid; idx < nrows * IB; idx += NT) {
       const int r = idx % nrows, j = idx / nrows;
       tile[(jb + r) + (int64_t)(jb + j) * F.ld] = Ps[r * VST + j];
@@ -537,8 +516,7 @@ __global__ void __launch_bounds__(NT) k_pair_qrt(Mat<T> F, int k, int nb, TileLi
     }
     cp_async_wait_all();
     __syncthreads();
-    panel_pair<T>(Rs, Ps, rl, tri, jb, tau_s, red, bc);
-    build_T<T>(Ps, rl, false, tau_s, Gs, Ts);
+    panel_qr<T, false>(Rs, Ps, rl, tri, jb, tau_s, Ts, Gs);
     for (int idx = tid; idx < IB * IB; idx += NT) {
       const int a = idx % IB, j = idx / IB;
       if (a <= j) R[(jb + a) + (int64_t)(jb + j) * F.ld] = Rs[a * VST + j];
@@ -643,9 +621,14 @@ static size_t plan_bytes(PlanKind kind, int nb) {
   }
 }
 
+// ncols: columns the launch updates; a narrow target (the second pass on a few right-hand
+// sides) takes the narrowest slab that covers it instead of a mostly idle wide one.
 template <typename T, typename Fn>
-static void pick_sw(PlanKind kind, int nb, Fn&& fn) {
-  if (plan_bytes<T, 64>(kind, nb) <= (size_t)SMEM_MAX) fn(std::integral_constant<int, 64>{});
+static void pick_sw(PlanKind kind, int nb, Fn&& fn, int64_t ncols = 1 << 30) {
+  if (ncols <= 8) fn(std::integral_constant<int, 8>{});
+  else if (ncols <= 16 && plan_bytes<T, 16>(kind, nb) <= (size_t)SMEM_MAX)
+    fn(std::integral_constant<int, 16>{});
+  else if (plan_bytes<T, 64>(kind, nb) <= (size_t)SMEM_MAX) fn(std::integral_constant<int, 64>{});
   else if (plan_bytes<T, 32>(kind, nb) <= (size_t)SMEM_MAX) fn(std::integral_constant<int, 32>{});
   else if (plan_bytes<T, 16>(kind, nb) <= (size_t)SMEM_MAX) fn(std::integral_constant<int, 16>{});
   else fn(std::integral_constant<int, 8>{});
@@ -671,15 +654,19 @@ void launch_unmqr(Mat<const T> F, int k, int nb, TileList tl, const T* Tk, int n
                   int64_t c0, int64_t c1, const uint8_t* dec, cudaStream_t s) {
   if (tl.count <= 0 || c1 <= c0) return;
   (void)n;
-  pick_sw<T>(PLAN_UNMQR, nb, [&](auto tag) {
-    constexpr int SW = decltype(tag)::value;
-    ensure_dyn_smem<k_unmqr<T, SW>>(Plan<T, SW>::unmqr(nb));
-    dim3 grid((unsigned)((c1 - c0 + SW - 1) / SW), (unsigned)tl.count);
-    {
-      ProfScope ps_("k_unmqr", s);
-      k_unmqr<T, SW><<<grid, NT, Plan<T, SW>::unmqr(nb), s>>>(F, k, nb, tl, Tk, C, c0, c1, dec);
-    }
-  });
+  pick_sw<T>(
+      PLAN_UNMQR, nb,
+      [&](auto tag) {
+        constexpr int SW = decltype(tag)::value;
+        ensure_dyn_smem<k_unmqr<T, SW>>(Plan<T, SW>::unmqr(nb));
+        dim3 grid((unsigned)((c1 - c0 + SW - 1) / SW), (unsigned)tl.count);
+        {
+          ProfScope ps_("k_unmqr", s);
+          k_unmqr<T, SW><<<grid, NT, Plan<T, SW>::unmqr(nb), s>>>(F, k, nb, tl, Tk, C, c0, c1,
+                                                                   dec);
+        }
+      },
+      c1 - c0);
 }
 
 template <typename T>
@@ -702,16 +689,19 @@ void launch_pair_apply(Mat<const T> F, int k, int nb, TileList tl, bool tri, con
                        Mat<T> C, int64_t c0, int64_t c1, const uint8_t* dec, cudaStream_t s) {
   if (tl.count <= 0 || c1 <= c0) return;
   (void)n;
-  pick_sw<T>(PLAN_PAIR_APPLY, nb, [&](auto tag) {
-    constexpr int SW = decltype(tag)::value;
-    ensure_dyn_smem<k_pair_apply<T, SW>>(Plan<T, SW>::pair_apply(nb));
-    dim3 grid((unsigned)((c1 - c0 + SW - 1) / SW), (unsigned)tl.count);
-    {
-      ProfScope ps_(tri ? "k_ttmqr" : "k_tsmqr", s);
-      k_pair_apply<T, SW><<<grid, NT, Plan<T, SW>::pair_apply(nb), s>>>(F, k, nb, tl, tri, Tk, C, c0,
-                                                                       c1, dec);
-    }
-  });
+  pick_sw<T>(
+      PLAN_PAIR_APPLY, nb,
+      [&](auto tag) {
+        constexpr int SW = decltype(tag)::value;
+        ensure_dyn_smem<k_pair_apply<T, SW>>(Plan<T, SW>::pair_apply(nb));
+        dim3 grid((unsigned)((c1 - c0 + SW - 1) / SW), (unsigned)tl.count);
+        {
+          ProfScope ps_(tri ? "k_ttmqr" : "k_tsmqr", s);
+          k_pair_apply<T, SW><<<grid, NT, Plan<T, SW>::pair_apply(nb), s>>>(F, k, nb, tl, tri, Tk,
+                                                                           C, c0, c1, dec);
+        }
+      },
+      c1 - c0);
 }
 
 #define INST(T)                                                                                  \

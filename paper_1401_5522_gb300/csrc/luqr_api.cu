@@ -68,6 +68,10 @@ struct luqr_handle {
   void* shadow = nullptr;       // Npad x nb copy of the panel column (same leading dimension)
   cudaStream_t spec_stream = nullptr;
   cudaStream_t panel_stream = nullptr;   // high priority; the caller's stream waits on it
+  cudaStream_t la_stream = nullptr;      // look-ahead column, one tree level behind the panel
+  cudaStream_t extra_stream = nullptr;   // tensor-core operand preparation of QR steps
+  std::vector<cudaEvent_t> ev_lvl;       // per tile list of the current step (reused)
+  std::vector<cudaEvent_t> ev_extra, ev_la;
   std::vector<cudaEvent_t> ev_stats, ev_spec;
   cudaEvent_t ev_end = nullptr;
   // second pass / refinement scratch
@@ -223,10 +227,13 @@ void for_each_tile_list(const luqr_handle* h, int k, FS&& single, FP&& pair) {
 // is passed with its base shifted by k*nb columns) and runs when fdec[k] == QR (default:
 // the decision).  extras = false leaves the tensor-core operand preparation to
 // enqueue_qr_extras.
+// rec / wait (optional, one event per tile list in tree order): record after each tile
+// list's factorization, or wait before each tile list's application.
 template <typename T>
 void enqueue_qr(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, bool do_factor,
                 bool do_apply, cudaStream_t s, bool tc = false, T* fbase = nullptr,
-                const uint8_t* fdec = nullptr, bool extras = true) {
+                const uint8_t* fdec = nullptr, bool extras = true,
+                const cudaEvent_t* rec = nullptr, const cudaEvent_t* wait = nullptr) {
   const int n = h->n, nb = h->nb;
   Mat<T> F{fbase ? fbase : wsT<T>(h), h->Npad};
   Mat<const T> Fc{wsT<T>(h), h->Npad};
@@ -235,11 +242,15 @@ void enqueue_qr(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, bool do
   const uint8_t* fd = fdec ? fdec : h->dec;
   constexpr bool is_f32 = std::is_same<T, float>::value;
   tc = tc && is_f32 && h->use_tc_qr;
+  int lvl = 0;
   auto single = [&](TileList tl) {
+    if (wait) cudaStreamWaitEvent(s, wait[lvl], 0);
     if (do_factor) {
       launch_geqrt<T>(F, k, nb, tl, Tk, n, fd, s);
       if (tc && extras) tc_factor_extra(h, k, tl, 0, TC_MASK_UNIT_LOWER, s);
     }
+    if (rec) cudaEventRecord(rec[lvl], s);
+    ++lvl;
     if (do_apply) {
       if constexpr (is_f32) {
         if (tc) { tc_apply_single(h, k, tl, C, c0, c1, s); return; }
@@ -248,10 +259,13 @@ void enqueue_qr(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, bool do
     }
   };
   auto pair = [&](TileList tl, bool tri) {
+    if (wait) cudaStreamWaitEvent(s, wait[lvl], 0);
     if (do_factor) {
       launch_pair_qrt<T>(F, k, nb, tl, tri, Tk, n, fd, s);
       if (tc && extras) tc_factor_extra(h, k, tl, 1, tri ? TC_MASK_UPPER : TC_MASK_NONE, s);
     }
+    if (rec) cudaEventRecord(rec[lvl], s);
+    ++lvl;
     if (do_apply) {
       if constexpr (is_f32) {
         if (tc) { tc_apply_pair(h, k, tl, tri, C, c0, c1, s); return; }
@@ -306,6 +320,8 @@ void enqueue_factor(luqr_handle* h) {
   // The panel chain runs on a high-priority internal stream so that its small kernels are
   // scheduled ahead of the bulk update's blocks; the caller's stream waits for both.
   cudaStream_t s = h->panel_stream, su = h->upd_stream, sp = h->spec_stream;
+  cudaStream_t sl = h->la_stream, sx = h->extra_stream;
+  const bool tcqr = std::is_same<T, float>::value && h->use_tc_qr;
   const int n = h->n, nb = h->nb;
   const int64_t ld = h->Npad;
   T* W = wsT<T>(h);
@@ -318,6 +334,8 @@ void enqueue_factor(luqr_handle* h) {
   cudaEventRecord(h->ev_start, h->stream);
   cudaStreamWaitEvent(s, h->ev_start, 0);
   cudaStreamWaitEvent(su, h->ev_start, 0);
+  cudaStreamWaitEvent(sl, h->ev_start, 0);
+  cudaStreamWaitEvent(sx, h->ev_start, 0);
   if (spec) cudaStreamWaitEvent(sp, h->ev_start, 0);
   for (int k = 0; k < n; ++k) {
     const int64_t r0 = (int64_t)k * nb, r1 = r0 + nb;
@@ -359,31 +377,51 @@ void enqueue_factor(luqr_handle* h) {
         launch_tc_pack(reinterpret_cast<float*>(W) + r1 + r0 * ld, ld, 0, 0, TC_MASK_NONE,
                        h->Npad - r1, nb, h->Lpk[k & 1], 0, 1, h->dec, k, DEC_LU, s);
     }
+    // The QR chain of column k records one event per tree level (non-speculative runs), so
+    // that the look-ahead stream applies level l to column k+1 while level l+1 factors.
+    const bool piped = !spec && r1 < la_end;
     if (spec) {
       enqueue_qr<T>(h, k, F, 0, 0, true, false, s, true, nullptr, h->qrfac, false);
       cudaStreamWaitEvent(s, h->ev_spec[k], 0);
       launch_gated_copy<T>(shadow + r0, ld, W + r0 + r0 * ld, ld, h->Npad - r0, nb, h->cmt, k,
                            DEC_QR, "k_spec_commit", s);
-      if constexpr (std::is_same<T, float>::value) enqueue_qr_extras(h, k, s);
     } else {
-      enqueue_qr<T>(h, k, F, 0, 0, true, false, s, true);
+      enqueue_qr<T>(h, k, F, 0, 0, true, false, s, true, nullptr, nullptr, !tcqr,
+                    piped ? h->ev_lvl.data() : nullptr);
     }
     cudaEventRecord(h->ev_fact[k], s);
+    // ---- tensor-core operands of the QR step (Gram, full T, V T^T, packing) off the
+    //      panel's critical path; only the bulk update consumes them
+    if (tcqr) {
+      cudaStreamWaitEvent(sx, h->ev_fact[k], 0);
+      if constexpr (std::is_same<T, float>::value) enqueue_qr_extras(h, k, sx);
+      cudaEventRecord(h->ev_extra[k], sx);
+    }
     // ---- bulk update of columns >= k+2 (and b) on the update stream
     if (la_end < h->Wc) {
       cudaStreamWaitEvent(su, h->ev_fact[k], 0);
+      if (tcqr) cudaStreamWaitEvent(su, h->ev_extra[k], 0);
       enqueue_lu_apply<T>(h, k, F, la_end, h->Wc, su, true);
       enqueue_qr<T>(h, k, F, la_end, h->Wc, false, true, su, true);
     }
     cudaEventRecord(h->ev_rest[k], su);
     // ---- look-ahead: column k+1 needs step k-1's bulk update, then step k's transform
+    //      (CUDA-core QR kernels: they need only the stored V and the IB x IB T blocks)
     if (r1 < la_end) {
-      if (k > 0) cudaStreamWaitEvent(s, h->ev_rest[k - 1], 0);
-      enqueue_lu_apply<T>(h, k, F, r1, la_end, s, true);
-      enqueue_qr<T>(h, k, F, r1, la_end, false, true, s, true);
+      cudaStreamWaitEvent(sl, spec ? h->ev_fact[k] : h->ev_lvl[0], 0);
+      if (k > 0) cudaStreamWaitEvent(sl, h->ev_rest[k - 1], 0);
+      enqueue_lu_apply<T>(h, k, F, r1, la_end, sl, true);
+      enqueue_qr<T>(h, k, F, r1, la_end, false, true, sl, false, nullptr, nullptr, true, nullptr,
+                    piped ? h->ev_lvl.data() : nullptr);
+      cudaEventRecord(h->ev_la[k], sl);
+      cudaStreamWaitEvent(s, h->ev_la[k], 0);
     }
   }
   cudaStreamWaitEvent(s, h->ev_rest[n - 1], 0);
+  cudaEventRecord(h->ev_end, sx);
+  cudaStreamWaitEvent(s, h->ev_end, 0);
+  cudaEventRecord(h->ev_end, sl);
+  cudaStreamWaitEvent(s, h->ev_end, 0);
   cudaEventRecord(h->ev_end, s);
   cudaStreamWaitEvent(h->stream, h->ev_end, 0);
 }
@@ -441,6 +479,11 @@ void free_handle(luqr_handle* h) {
   if (h->upd_stream) cudaStreamDestroy(h->upd_stream);
   if (h->spec_stream) cudaStreamDestroy(h->spec_stream);
   if (h->panel_stream) cudaStreamDestroy(h->panel_stream);
+  if (h->la_stream) cudaStreamDestroy(h->la_stream);
+  if (h->extra_stream) cudaStreamDestroy(h->extra_stream);
+  for (cudaEvent_t e : h->ev_lvl) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_extra) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_la) if (e) cudaEventDestroy(e);
   void* ptrs[] = {h->W,      h->Tbuf,     h->S,        h->piv_s, h->piv_all, h->norms,
                   h->local,  h->away,     h->colsum,   h->dec,   h->margin,  h->lhs,
                   h->rhs,    h->status,   h->forced,   h->rhs_ws, h->ref,    h->Wbuf,
@@ -683,6 +726,10 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
     e = cudaStreamCreateWithPriority(&h->panel_stream, cudaStreamNonBlocking, prio_high);
   if (e == cudaSuccess && o.speculate)
     e = cudaStreamCreateWithPriority(&h->spec_stream, cudaStreamNonBlocking, prio_high);
+  if (e == cudaSuccess)
+    e = cudaStreamCreateWithPriority(&h->la_stream, cudaStreamNonBlocking, prio_high);
+  if (e == cudaSuccess)
+    e = cudaStreamCreateWithPriority(&h->extra_stream, cudaStreamNonBlocking, prio_high);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_end, cudaEventDisableTiming);
   h->ev_fact.assign(n, nullptr);
@@ -690,6 +737,15 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   for (int q = 0; q < n && e == cudaSuccess; ++q) {
     e = cudaEventCreateWithFlags(&h->ev_fact[q], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_rest[q], cudaEventDisableTiming);
+  }
+  h->ev_lvl.assign(n + 2, nullptr);
+  h->ev_extra.assign(n, nullptr);
+  h->ev_la.assign(n, nullptr);
+  for (size_t q = 0; q < h->ev_lvl.size() && e == cudaSuccess; ++q)
+    e = cudaEventCreateWithFlags(&h->ev_lvl[q], cudaEventDisableTiming);
+  for (int q = 0; q < n && e == cudaSuccess; ++q) {
+    e = cudaEventCreateWithFlags(&h->ev_extra[q], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_la[q], cudaEventDisableTiming);
   }
   if (o.speculate) {
     h->ev_stats.assign(n, nullptr);
