@@ -52,6 +52,9 @@ def parse(argv=None):
     p.add_argument("--fp64-baseline", type=int, default=1, help="also time one plain FP64 solve")
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--cpu-N", type=int, default=2048, help="oracle sample size")
+    p.add_argument("--forms", type=int, default=1,
+                   help="also measure the batched and the MLP-speculative forms")
+    p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--seed", type=int, default=0)
     return p.parse_args(argv)
@@ -125,6 +128,26 @@ def step_tc_bytes(dec, n, nb, tree, ncols_extra):
         add(f"k_tc_{kind}mqr_c1", pairs * (12.0 * nb * cols + a_op))
         add(f"k_tc_{kind}mqr_c2", pairs * (12.0 * nb * cols + a_op))
     return out
+
+
+# CUDA function behind each launch label of the library's profiler
+KERNEL_OF_LABEL = {
+    **{f"k_tc_{r}": "k_gemm_tc2v" for r in ("ttmqr_w", "ttmqr_c1", "ttmqr_c2", "tsmqr_w",
+                                            "tsmqr_c1", "tsmqr_c2", "unmqr_w", "unmqr_c",
+                                            "lu_gemm")},
+    "k_tc_gram": "k_gemm_tc", "k_tc_vt": "k_gemm_tc",
+    "k_ttqrt": "k_pair_qrt", "k_tsqrt": "k_pair_qrt",
+    "k_ttmqr": "k_pair_apply", "k_tsmqr": "k_pair_apply",
+}
+
+# DRAM bytes per algorithmic byte of the tensor-core update kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of a bulk launch at N=8192, see profiles/)
+TRAFFIC_RATIO = {}
+
+
+def traffic_per_launch(kernel, alg_bytes_per_launch):
+    r = TRAFFIC_RATIO.get(kernel)
+    return None if r is None else r * alg_bytes_per_launch
 
 
 def load_peaks():
@@ -248,6 +271,110 @@ def cpu_baseline_dict(res, args):
             }
 
 
+# ------------------------------------------------------------------ other forms
+def batched_form(args, plain_ms_per_normflop=None):
+    """4096 independent systems, N uniform in [64, 1024], iid N(0,1), 10% with a 1e-6-scaled
+    leading tile; Max alpha=100; one persistent launch replayed as a CUDA graph; tile size
+    per size bucket from the autotuner; FP64 and FP32 + FP64 refinement."""
+    import numpy as np
+    import torch
+    from paper_1401_5522_gb300 import batched, inputs
+    sizes = inputs.batch_sizes(args.batch_count, 64, 1024, args.seed + 4)
+    scaled = set(inputs.choose_panels(args.batch_count, 0.1, args.seed + 4))
+    As, bs = [], []
+    for i, N in enumerate(sizes):
+        A = inputs.gaussian(N, 10_000 + i, device="cuda")
+        if i in scaled:
+            A[:32, :32] *= 1e-6
+        As.append(A)
+        bs.append((A @ torch.ones(N, 1, dtype=torch.float64, device="cuda")).reshape(-1).contiguous())
+
+    def make_system(N, seed):
+        A = inputs.gaussian(N, seed, device="cuda").contiguous().t().contiguous().t()
+        return A, (A @ torch.ones(N, 1, dtype=torch.float64, device="cuda")).reshape(-1).contiguous()
+
+    table = batched.autotune(sizes, make_system, "max", 100.0, "fp64", samples=12, reps=1)
+    nbs = batched.nb_for(sizes, table)
+    flops = sum((2.0 / 3.0) * float(N) ** 3 for N in sizes)
+    out = {"workload": f"{args.batch_count} systems, N~U[64,1024], iid N(0,1), 10% with a "
+                       "1e-6-scaled leading tile, Max alpha=100, one persistent launch as a "
+                       "CUDA graph", "nb_per_bucket": {str(k): v for k, v in table.items()}}
+    for prec in ("fp64", "fp32"):
+        xs = [b.clone() for b in bs]
+        bt = batched.Batch(As, xs, nbs, "max", 100.0, prec, tol=1e-13, max_iter=10)
+        bt.run_graph()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record()
+        for _ in range(reps):
+            bt.run_graph()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        dec, status, iters, eta = bt.results()
+        bt.close()
+        out[prec] = {"ms": ms, "gflops_normalized": flops / (ms / 1e3) / 1e9,
+                     "max_eta": float(np.max(eta)), "failed": int(np.sum(status != 0)),
+                     "mean_ir_iters": float(np.mean(iters)) if prec == "fp32" else 0.0,
+                     "lu_fraction": float(np.mean(dec[dec != 255] == 1))}
+    out["speedup_fp32_ir_over_fp64"] = out["fp64"]["ms"] / out["fp32"]["ms"]
+    out["alu_peak_tflops"] = {"fp64": FP64_DFMA_PEAK_TFLOPS, "fp32": FP32_FFMA_PEAK_TFLOPS}
+    del As, bs
+    torch.cuda.empty_cache()
+    return out
+
+
+def speculation_form(args, A, b, x, base_ms):
+    """Trains the decision MLP with the library's kernels on logged (features, decision)
+    pairs from N=4096, nb=256 iid N(0,1) matrices with 20% of the diagonal tiles scaled
+    by 1e-8 (Max alpha in {1e4, 3e4, 1e5}), then times the headline solve with MLP and with
+    repeat-previous speculation (same decisions and results as the plain run)."""
+    import numpy as np
+    import torch
+    from paper_1401_5522_gb300 import inputs, luqr
+    from paper_1401_5522_gb300 import speculation as S
+    N0, nb0 = 4096, 256
+    runs = []
+    for seed in range(12):
+        A0 = inputs.gaussian(N0, 500 + seed, device="cuda")
+        A0 = inputs.scale_diag_tiles(A0, nb0, inputs.choose_panels(N0 // nb0, 0.2, seed), 1e-8)
+        runs.append(dict(A=A0, nb=nb0, criterion="max", alpha=(1e4, 3e4, 1e5)[seed % 3],
+                         precision="fp32", tree=args.tree))
+    t0 = time.time()
+    X, y = S.collect(runs)
+    params, losses = S.train(X, y, epochs=200, batch=128, lr=3e-3)
+    train_s = time.time() - t0
+    out = {"training": {"samples": int(len(y)), "lu_fraction": float(np.mean(y)),
+                        "loss_first": losses[0], "loss_last": losses[-1], "seconds": train_s}}
+    stream = torch.cuda.current_stream()
+    for mode, extra in (("mlp", {"mlp_params": params}), ("repeat", {})):
+        def solve():
+            h = luqr.factor(A, args.nb, args.criterion, args.alpha, tree=args.tree,
+                            precision=args.precision, fp32_kernels=args.fp32_kernels,
+                            speculate=mode, **extra)
+            st, its, eta = h.refine(A, b, x, tol=args.tol, max_iter=30)
+            dec, _ = h.decisions()
+            pred = h.features()[1]
+            h.close()
+            return st, eta, dec, pred
+        solve()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            st, eta, dec, pred = solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out[mode] = {"ms_per_solve": ms, "speedup_vs_speculation_off": base_ms / ms,
+                     "eta": eta, "status": st,
+                     "prediction_accuracy": float(np.mean(pred == dec))}
+    return out
+
+
 # ------------------------------------------------------------------ main GPU leg
 def main():
     args = parse()
@@ -358,33 +485,46 @@ def main():
     total_alg = {k: args.steps * fac.get(k, 0.0) + sum(iters) * rep.get(k, 0.0)
                  for k in set(fac) | set(rep)}
     tc_bytes = step_tc_bytes(dec, n, nb, args.tree, 0) if args.precision == "fp32" else {}
-    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    # the profiler labels launches by role; the dominant kernel is the CUDA function with the
+    # most device time, summed over the roles it serves
+    funcs = {}
+    for label, (launches, tot_ms) in prof.items():
+        f = KERNEL_OF_LABEL.get(label, label)
+        e = funcs.setdefault(f, [0, 0.0, []])
+        e[0] += launches
+        e[1] += tot_ms
+        e[2].append(label)
+    dom = max(funcs.items(), key=lambda kv: kv[1][1]) if funcs else None
     roofline = None
+    all_ms = sum(v[1] for v in prof.values()) if prof else 0.0
     if dom is not None:
-        name, (launches, tot_ms) = dom
-        if name in tc_bytes:
+        name, (launches, tot_ms, labels) = dom
+        if any(l in tc_bytes for l in labels):
+            # roles without work in this run (kernels launched gated off) count 0 bytes
             peaks = load_peaks()
-            alg_bytes = args.steps * tc_bytes[name]
+            alg_bytes = args.steps * sum(tc_bytes.get(l, 0.0) for l in labels)
             achieved = alg_bytes / (tot_ms / 1e3) / 1e9
-            roofline = {"bound": "hbm", "kernel": name, "achieved": achieved,
+            roofline = {"bound": "hbm", "kernel": name, "roles": labels, "achieved": achieved,
                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                        "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                        "frac": achieved / peaks["hbm_gbs"],
+                        "traffic": traffic_per_launch(name, alg_bytes / launches),
                         "peak_source": f"{peaks['source']} HBM copy bandwidth",
                         "bytes_per_launch": alg_bytes / launches,
                         "launches": launches, "avg_launch_ms": tot_ms / launches,
-                        "share_of_kernel_time": tot_ms / sum(v[1] for v in prof.values())}
+                        "share_of_kernel_time": tot_ms / all_ms}
         else:
-            alg = total_alg.get(name)
+            alg = sum(total_alg.get(l, 0.0) for l in labels)
             peak = FP32_FFMA_PEAK_TFLOPS if args.precision == "fp32" else FP64_DFMA_PEAK_TFLOPS
             if alg:
                 achieved = alg / (tot_ms / 1e3) / 1e12
-                roofline = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
+                roofline = {"bound": "alu", "kernel": name, "roles": labels,
+                            "achieved": achieved, "peak": peak,
                             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                             "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
                                             if args.precision == "fp32" else
                                             "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"),
                             "launches": launches, "avg_launch_ms": tot_ms / launches,
-                            "share_of_kernel_time": tot_ms / sum(v[1] for v in prof.values())}
+                            "share_of_kernel_time": tot_ms / all_ms}
     gpu_launches = int(sum(v[0] for v in prof.values())) if prof else 0
     kernel_table = {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in
                     sorted(prof.items(), key=lambda kv: -kv[1][1])}
@@ -446,6 +586,15 @@ def main():
                  "status": st64, "decisions_equal_to_fp32_path": bool(np.array_equal(dec64, dec)),
                  "speedup_of_headline": p_ms / ms}
 
+    forms = None
+    if args.forms:
+        forms = {"speculative": speculation_form(args, A, b, x, ms),
+                 "batched": batched_form(args)}
+        if plain is not None:
+            for key in ("mlp", "repeat"):
+                forms["speculative"][key]["speedup_vs_plain_fp64"] = (
+                    plain["ms_per_solve"] / forms["speculative"][key]["ms_per_solve"])
+
     if rank != 0:
         return
     cpu = run_cpu_baseline(args)
@@ -456,7 +605,7 @@ def main():
             "eta": eta_gpu, "ir_iters": iters, "status": statuses,
             "lu_fraction": float(np.mean(dec == 1)),
             "plain_fp64": plain, "roofline": roofline, "gpu_launches": gpu_launches,
-            "kernels": kernel_table, "e2e": e2e, "clocks": clk,
+            "kernels": kernel_table, "e2e": e2e, "clocks": clk, "forms": forms,
             "cpu_baseline": cpu_baseline_dict(cpu, args)}
     print(json.dumps(line))
     if world > 1:

@@ -235,8 +235,12 @@ int luqr_gemm_sub_f32(float* C, int64_t ldc, const float* A, int64_t lda, const 
  *            with the autotuner of the Python package or pass a fixed value).
  *   criterion, alpha, opt (precision, mumps_mode), tol, max_iter as for luqr_factor/refine.
  * luqr_batched_run - enqueues one persistent launch on `stream`; it allocates nothing and
- *   synchronises nothing, so it can be captured in a CUDA graph and replayed (the batch's
- *   b_i must be reset by the caller between replays).
+ *   synchronises nothing.  The batch keeps its own copy of every b_i (taken at create), so
+ *   repeated runs solve the same systems and write x_i into the caller's b_i each time.
+ * luqr_batched_run_graph - the same work as a CUDA graph: the first call captures the
+ *   queue reset and the persistent launch into a graph owned by the batch (on a private
+ *   stream), every call launches that graph on `stream`.  LUQR_ERR_CUDA if capture or
+ *   instantiation fails.
  * luqr_batched_results - synchronises the device and copies to HOST arrays (any may be
  *   NULL): per-system decisions (count x nmax, LUQR_DEC_*, 255 past the system's last
  *   step), status, refinement iterations and final eta; *nmax_out = nmax.
@@ -286,6 +290,7 @@ int luqr_batched_create(const double* const* dA, double* const* db, const int* N
                         int count, int criterion, double alpha, const luqr_options* opt,
                         double tol, int max_iter, luqr_batched_t* out);
 int luqr_batched_run(luqr_batched_t b, void* stream);
+int luqr_batched_run_graph(luqr_batched_t b, void* stream);
 int luqr_batched_results(luqr_batched_t b, uint8_t* dec, int* status, int* iters, double* eta,
                          int* nmax_out);
 void luqr_batched_destroy(luqr_batched_t b);

@@ -54,6 +54,12 @@ class Batch:
         if st != luqr.OK:
             raise luqr.LuqrError(st, "luqr_batched_run")
 
+    def run_graph(self, stream=None):
+        """The same solve as one CUDA-graph launch (captured on the first call)."""
+        st = _sigs().luqr_batched_run_graph(self._h, luqr._stream_ptr(stream))
+        if st != luqr.OK:
+            raise luqr.LuqrError(st, "luqr_batched_run_graph")
+
     def results(self):
         L = _sigs()
         nmax = ctypes.c_int()

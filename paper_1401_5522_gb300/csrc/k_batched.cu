@@ -25,7 +25,8 @@ constexpr int TILE = NBMAX * LDS;
 
 struct BatchArgs {
   const double* const* A;   // per system, column-major N x N (lda = N), read only
-  double* const* b;         // per system, length N; overwritten with x
+  double* const* b;         // per system, length N; receives x
+  const double* const* b0;  // per system, the batch's own copy of the right-hand side
   const int* N;             // orders
   const int* nbs;           // tile size per system (32 or 64)
   const int* order;         // processing order (largest first)
@@ -520,6 +521,7 @@ __global__ void __launch_bounds__(BT, 1) k_batched(BatchArgs a) {
     const int n = (N + nb - 1) / nb, Np = n * nb;
     const double* A = a.A[sys];
     double* bx = a.b[sys];
+    const double* b0 = a.b0[sys];
     uint8_t* dec = a.dec + (size_t)sys * a.nmax;
     int st = 0;
     // ---- pack [A | b] into the padded workspace (identity on the padded diagonal)
@@ -527,7 +529,7 @@ __global__ void __launch_bounds__(BT, 1) k_batched(BatchArgs a) {
       const int r = (int)(idx % Np), c = (int)(idx / Np);
       double v;
       if (c < Np) v = (r < N && c < N) ? A[r + (int64_t)c * N] : (r == c ? 1.0 : 0.0);
-      else v = r < N ? bx[r] : 0.0;
+      else v = r < N ? b0[r] : 0.0;
       sl.W[r + (int64_t)c * ldw] = (T)v;
     }
     __syncthreads();
@@ -777,7 +779,7 @@ __global__ void __launch_bounds__(BT, 1) k_batched(BatchArgs a) {
         // r = b - A x (FP64), eta = ||r|| / (||A|| ||x|| + ||b||)
         double rmax = 0.0, xmax = 0.0, bmax = 0.0, amax = 0.0;
         for (int i = threadIdx.x; i < N; i += BT) {
-          double s = bx[i], ra = 0.0;
+          double s = b0[i], ra = 0.0;
           for (int c = 0; c < N; ++c) {
             const double av = A[i + (int64_t)c * N];
             s -= av * sl.x[c];
@@ -786,7 +788,7 @@ __global__ void __launch_bounds__(BT, 1) k_batched(BatchArgs a) {
           sl.r[i] = s;
           rmax = fmax(rmax, fabs(s));
           xmax = fmax(xmax, fabs(sl.x[i]));
-          bmax = fmax(bmax, fabs(bx[i]));
+          bmax = fmax(bmax, fabs(b0[i]));
           amax = fmax(amax, ra);
         }
         double vals[4] = {rmax, xmax, bmax, amax};
@@ -843,6 +845,8 @@ struct luqr_batched {
   BatchArgs args{};
   void* dev = nullptr;      // metadata block
   void* slot_mem = nullptr;
+  double* b0_mem = nullptr; // copies of the right-hand sides (runs are repeatable)
+  cudaGraphExec_t graph = nullptr;   // captured counter reset + persistent launch
 };
 
 namespace {
@@ -850,6 +854,8 @@ void batched_free(luqr_batched* p) {
   if (!p) return;
   if (p->dev) cudaFree(p->dev);
   if (p->slot_mem) cudaFree(p->slot_mem);
+  if (p->b0_mem) cudaFree(p->b0_mem);
+  if (p->graph) cudaGraphExecDestroy(p->graph);
   delete p;
 }
 }  // namespace
@@ -900,6 +906,7 @@ extern "C" int luqr_batched_create(const double* const* dA, double* const* db, c
   size_t off = 0;
   const size_t oA = off; off = al(off + sizeof(void*) * count);
   const size_t oB = off; off = al(off + sizeof(void*) * count);
+  const size_t oB0 = off; off = al(off + sizeof(void*) * count);
   const size_t oN = off; off = al(off + sizeof(int) * count);
   const size_t oNB = off; off = al(off + sizeof(int) * count);
   const size_t oO = off; off = al(off + sizeof(int) * count);
@@ -908,8 +915,11 @@ extern "C" int luqr_batched_create(const double* const* dA, double* const* db, c
   const size_t oE = off; off = al(off + sizeof(double) * count);
   const size_t oS = off; off = al(off + sizeof(int) * count);
   const size_t oC = off; off = al(off + sizeof(int));
+  int64_t total_n = 0;
+  for (int i = 0; i < count; ++i) total_n += N[i];
   cudaError_t e = cudaMalloc(&p->dev, off);
   if (e == cudaSuccess) e = cudaMalloc(&p->slot_mem, p->slot_bytes * p->slots);
+  if (e == cudaSuccess) e = cudaMalloc(&p->b0_mem, sizeof(double) * (size_t)total_n);
   if (e != cudaSuccess) {
     batched_free(p);
     cudaGetLastError();
@@ -918,6 +928,16 @@ extern "C" int luqr_batched_create(const double* const* dA, double* const* db, c
   unsigned char* d = static_cast<unsigned char*>(p->dev);
   cudaMemcpy(d + oA, dA, sizeof(void*) * count, cudaMemcpyHostToDevice);
   cudaMemcpy(d + oB, db, sizeof(void*) * count, cudaMemcpyHostToDevice);
+  {
+    std::vector<const double*> b0p(count);
+    int64_t o0 = 0;
+    for (int i = 0; i < count; ++i) {
+      b0p[i] = p->b0_mem + o0;
+      cudaMemcpy(p->b0_mem + o0, db[i], sizeof(double) * N[i], cudaMemcpyDeviceToDevice);
+      o0 += N[i];
+    }
+    cudaMemcpy(d + oB0, b0p.data(), sizeof(void*) * count, cudaMemcpyHostToDevice);
+  }
   cudaMemcpy(d + oN, N, sizeof(int) * count, cudaMemcpyHostToDevice);
   cudaMemcpy(d + oNB, nb, sizeof(int) * count, cudaMemcpyHostToDevice);
   cudaMemcpy(d + oO, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice);
@@ -925,6 +945,7 @@ extern "C" int luqr_batched_create(const double* const* dA, double* const* db, c
   BatchArgs& a = p->args;
   a.A = reinterpret_cast<const double* const*>(d + oA);
   a.b = reinterpret_cast<double* const*>(d + oB);
+  a.b0 = reinterpret_cast<const double* const*>(d + oB0);
   a.N = reinterpret_cast<const int*>(d + oN);
   a.nbs = reinterpret_cast<const int*>(d + oNB);
   a.order = reinterpret_cast<const int*>(d + oO);
@@ -965,6 +986,37 @@ extern "C" int luqr_batched_run(luqr_batched_t p, void* stream) {
     k_batched<double><<<p->slots, BT, sm, s>>>(p->args);
   }
   return cudaGetLastError() == cudaSuccess ? LUQR_OK : LUQR_ERR_CUDA;
+}
+
+extern "C" int luqr_batched_run_graph(luqr_batched_t p, void* stream) {
+  if (!p) return LUQR_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!p->graph) {
+    const size_t sm = p->fp32 ? batched_smem<float>() : batched_smem<double>();
+    if (p->fp32) ensure_dyn_smem<k_batched<float>>(sm);
+    else ensure_dyn_smem<k_batched<double>>(sm);
+    // capture on a private stream so that the caller's stream is never in capture mode
+    cudaStream_t cs = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaMemsetAsync(p->args.counter, 0, sizeof(int), cs);
+      if (p->fp32) k_batched<float><<<p->slots, BT, sm, cs>>>(p->args);
+      else k_batched<double><<<p->slots, BT, sm, cs>>>(p->args);
+      e = cudaStreamEndCapture(cs, &g);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      p->graph = nullptr;
+      cudaGetLastError();
+      return LUQR_ERR_CUDA;
+    }
+  }
+  ProfScope ps_("k_batched", s);
+  return cudaGraphLaunch(p->graph, s) == cudaSuccess ? LUQR_OK : LUQR_ERR_CUDA;
 }
 
 extern "C" int luqr_batched_results(luqr_batched_t p, uint8_t* dec, int* status, int* iters,

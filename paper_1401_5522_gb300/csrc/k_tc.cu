@@ -727,10 +727,75 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc2v(TcArgs a) {
   __syncthreads();
   tc_fence_after();
   const bool all_ok = *s_fail == 0;
-  if (all_ok) {
-    const int h = warp >> 2;
-    const int lane_base = (warp & 3) * 32;
-    const int64_t row = m0 + h * 128 + lane_base + lane;
+  const float* Csrc = (a.epi == TC_EPI_ADD_OUT) ? C1 : C;
+  const int64_t lds = (a.epi == TC_EPI_ADD_OUT) ? a.ldc1 : a.ldc;
+  const bool staged = a.epi != TC_EPI_OUT && (reinterpret_cast<uintptr_t>(Csrc) % 16) == 0 &&
+                      (lds % 4) == 0;
+  const int h = warp >> 2;
+  const int lane_base = (warp & 3) * 32;
+  const int64_t row = m0 + h * 128 + lane_base + lane;
+  if (all_ok && staged) {
+    fence_async_smem();
+    // The C (or C1) operand of the epilogue comes in through cp.async in four 64-column
+    // segments staged in the now idle pipeline buffers, so its loads are in flight together
+    // instead of one dependent round trip per register batch.
+    unsigned char* buf[4] = {rawbase, smem_v, smem_v + P_STAGE, rawbase};
+    auto load_seg = [&](int seg) {
+      unsigned char* dst = buf[seg];
+      if (n0 + seg * 64 < a.N) {
+        for (int idx = tid; idx < 64 * 64; idx += TC_THREADS) {
+          const int q = idx & 63, c = idx >> 6;
+          const int64_t gc = n0 + seg * 64 + c;
+          const int64_t gr = m0 + 4 * q;
+          const int64_t left = a.M - gr;
+          const uint32_t bytes =
+              (gc < a.N && left > 0) ? (uint32_t)(4 * (left < 4 ? left : 4)) : 0u;
+          const float* src = bytes ? Csrc + gr + gc * lds : Csrc;
+          cp_async16_zfill(dst + (size_t)(c * 256 + 4 * q) * 4, src, bytes);
+        }
+      }
+      cp_async_commit();
+    };
+    auto process_seg = [&](int seg) {
+      const float* sv = reinterpret_cast<const float*>(buf[seg]);
+      if (h >= mh) return;
+      for (int g = 0; g < 2; ++g) {
+        const int col0 = seg * 64 + 32 * g;
+        if (n0 + col0 >= a.N) break;
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(h * P_BN + col0), v);
+        if (row < a.M) {
+          const int lr = h * 128 + lane_base + lane;
+          const int64_t lim = a.N - (n0 + col0);
+          float* Cr = C + row + (n0 + col0) * a.ldc;
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            if (q < lim) {
+              const float old = sv[(32 * g + q) * 256 + lr];
+              Cr[(int64_t)q * a.ldc] = (a.epi == TC_EPI_SUB) ? old - v[q] : v[q] + old;
+            }
+          }
+        }
+      }
+    };
+    load_seg(0);
+    load_seg(1);
+    load_seg(2);
+    cp_async_wait_group<2>();
+    __syncthreads();
+    process_seg(0);
+    __syncthreads();
+    load_seg(3);
+    cp_async_wait_group<2>();
+    __syncthreads();
+    process_seg(1);
+    cp_async_wait_group<1>();
+    __syncthreads();
+    process_seg(2);
+    cp_async_wait_group<0>();
+    __syncthreads();
+    process_seg(3);
+  } else if (all_ok) {
     if (h < mh) {
       for (int cc = 0; cc < P_BN; cc += 32) {
         float v[32];

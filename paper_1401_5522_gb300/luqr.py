@@ -78,6 +78,7 @@ _SIGS = {
                                            ctypes.POINTER(Options), ctypes.c_double, ctypes.c_int,
                                            ctypes.POINTER(_P)]),
     "luqr_batched_run": (ctypes.c_int, [_P, _P]),
+    "luqr_batched_run_graph": (ctypes.c_int, [_P, _P]),
     "luqr_batched_results": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
     "luqr_batched_destroy": (None, [_P]),
     "luqr_mlp_forward": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),

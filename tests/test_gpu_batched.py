@@ -98,3 +98,26 @@ def test_autotuner_returns_a_candidate_per_bucket():
     table = batched.autotune(sizes, make, samples=2, reps=1)
     assert set(table) == {batched.bucket_of(80), batched.bucket_of(300)}
     assert all(v in batched.CANDIDATES for v in table.values())
+
+
+def test_batched_graph_replays_are_repeatable():
+    """The batch keeps its own right-hand sides, so plain runs and CUDA-graph launches
+    solve the same systems every time and agree bit for bit."""
+    from paper_1401_5522_gb300 import batched
+    sizes = [70, 130, 300, 64, 500]
+    nbs = [32, 64, 32, 32, 64]
+    sy = systems(sizes, seed0=40, scaled=(2,))
+    for prec in ("fp64", "fp32"):
+        bs = [b.clone() for _, b in sy]
+        bt = batched.Batch([A for A, _ in sy], bs, nbs, "max", 100.0, prec)
+        bt.run()
+        ref = [b.clone() for b in bs]
+        d0, s0, i0, e0 = bt.results()
+        for _ in range(3):
+            bt.run_graph()
+            d1, s1, i1, e1 = bt.results()
+            assert np.all(s1 == 0) and np.array_equal(d1, d0) and np.array_equal(i1, i0)
+            for x, r in zip(bs, ref):
+                assert torch.equal(x, r)
+        assert np.all(e0 <= 1e-13)
+        bt.close()
