@@ -216,6 +216,13 @@ void launch_multidot(const double* V, int64_t ldv, int64_t N, int cnt, const dou
 void launch_multiaxpy(const double* V, int64_t ldv, int64_t N, int cnt, const double* coef,
                       double* w, double alpha, cudaStream_t s);
 
+// One right-hand side of the second pass (k_qr.cu).
+template <typename T>
+bool qr_apply_vec_fits(int nb);   // its double-buffered V blocks fit in shared memory
+template <typename T>
+void launch_qr_apply_vec(Mat<const T> F, int k, int nb, TileList tl, bool pair, bool tri,
+                         const T* Tk, T* x, const uint8_t* dec, cudaStream_t s);
+
 // Decision predictor and speculation helpers (k_mlp.cu).
 template <typename T>
 void launch_features_spec(const T* W, int64_t ldw, int k, int n, int nb, double alpha,

@@ -607,6 +607,117 @@ __global__ void __launch_bounds__(NT) k_pair_apply(Mat<const T> F, int k, int nb
   }
 }
 
+// ---------------------------------------------------------------- one right-hand side
+// Second pass on a single vector: Q^T of one tile (GEQRT reflectors) or of one tile pair
+// (TS/TT reflectors) applied to x, inner block by inner block,
+//   w = V_b^T x,  w2 = T_b^T w,  x -= V_b w2,
+// with the V and T blocks staged in shared memory and the next block's copy in flight.
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_qr_apply_vec(Mat<const T> F, int k, int nb, TileList tl,
+                                                     int pair, int tri, const T* __restrict__ Tk,
+                                                     T* __restrict__ x,
+                                                     const uint8_t* __restrict__ dec) {
+  if (dec[k] != DEC_QR) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Vb = reinterpret_cast<T*>(smem_raw);           // 2 x (nb x VST)
+  T* Tb = Vb + 2 * (size_t)nb * VST;                // 2 x (IB x TST)
+  T* xs = Tb + 2 * IB * TST;                        // nb: tile i
+  T* xe = xs + nb;                                  // nb: eliminator tile (pairs)
+  T* w = xe + nb;                                   // IB
+  T* w2 = w + IB;                                   // IB
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
+  const int i = tl.i0 + blockIdx.x * tl.istride;
+  const int e = i - tl.eoff;
+  const T* V = F.p + (int64_t)i * nb + (int64_t)k * nb * F.ld;
+  const T* Tslot = Tk + ((size_t)i * 2 + (pair ? 1 : 0)) * IB * nb;
+  T* xi = x + (int64_t)i * nb;
+  T* xg = x + (int64_t)e * nb;
+  auto lo = [&](int jb) { return pair ? 0 : jb; };
+  auto hi = [&](int jb) { return pair ? (tri ? jb + IB : nb) : nb; };
+  // V block of inner block jb: rows [lo, hi) x IB columns, masked to the reflector storage
+  // (single: unit diagonal, zeros above; TT: zeros below the diagonal of the V2 triangle)
+  auto stage = [&](int jb, int buf) {
+    T* vs = Vb + (size_t)buf * nb * VST;
+    const int r0 = lo(jb), rows = hi(jb) - r0;
+    for (int idx = tid; idx < rows * IB; idx += NT) {
+      const int rr = idx % rows, j = idx / rows, r = r0 + rr;
+      if (!pair && r <= jb + j) vs[rr * VST + j] = (r == jb + j) ? (T)1 : (T)0;
+      else if (pair && tri && r > jb + j) vs[rr * VST + j] = (T)0;
+      else cp_async(&vs[rr * VST + j], &V[r + (int64_t)(jb + j) * F.ld]);
+    }
+    T* ts = Tb + buf * IB * TST;
+    for (int idx = tid; idx < IB * IB; idx += NT) {
+      const int a = idx % IB, j = idx / IB;
+      cp_async(&ts[a * TST + j], &Tslot[a + (size_t)(jb + j) * IB]);
+    }
+    cpa_commit();
+  };
+  for (int r = tid; r < nb; r += NT) {
+    xs[r] = xi[r];
+    if (pair) xe[r] = xg[r];
+  }
+  stage(0, 0);
+  for (int jb = 0, b = 0; jb < nb; jb += IB, b ^= 1) {
+    if (jb + IB < nb) stage(jb + IB, b ^ 1);
+    else cpa_commit();
+    cpa_wait1();
+    __syncthreads();
+    const T* vs = Vb + (size_t)b * nb * VST;
+    const T* ts = Tb + b * IB * TST;
+    const int r0 = lo(jb), rows = hi(jb) - r0;
+    // w_j = [e_j-part] + V_b(:, j) . x
+    for (int j = warp; j < IB; j += nw) {
+      T s = (T)0;
+      for (int rr = lane; rr < rows; rr += 32) s += vs[rr * VST + j] * xs[r0 + rr];
+      s = warp_sum<T>(s);
+      if (lane == 0) w[j] = pair ? s + xe[jb + j] : s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      T s = (T)0;
+      for (int a = 0; a <= lane; ++a) s += ts[a * TST + lane] * w[a];
+      w2[lane] = s;
+    }
+    __syncthreads();
+    for (int rr = tid; rr < rows; rr += NT) {
+      T s = (T)0;
+#pragma unroll 8
+      for (int j = 0; j < IB; ++j) s += vs[rr * VST + j] * w2[j];
+      xs[r0 + rr] -= s;
+    }
+    if (pair && tid < IB) xe[jb + tid] -= w2[tid];
+    __syncthreads();
+  }
+  for (int r = tid; r < nb; r += NT) {
+    xi[r] = xs[r];
+    if (pair) xg[r] = xe[r];
+  }
+}
+
+template <typename T>
+static size_t qr_apply_vec_smem(int nb) {
+  return sizeof(T) * (2 * (size_t)nb * VST + 2 * IB * TST + 2 * (size_t)nb + 2 * IB);
+}
+
+template <typename T>
+bool qr_apply_vec_fits(int nb) {
+  return qr_apply_vec_smem<T>(nb) <= (size_t)SMEM_MAX;
+}
+
+template <typename T>
+void launch_qr_apply_vec(Mat<const T> F, int k, int nb, TileList tl, bool pair, bool tri,
+                         const T* Tk, T* x, const uint8_t* dec, cudaStream_t s) {
+  if (tl.count <= 0) return;
+  const size_t smem = qr_apply_vec_smem<T>(nb);
+  ensure_dyn_smem<k_qr_apply_vec<T>>(smem);
+  ProfScope ps_(pair ? (tri ? "k_ttmqr_vec" : "k_tsmqr_vec") : "k_unmqr_vec", s);
+  k_qr_apply_vec<T><<<tl.count, NT, smem, s>>>(F, k, nb, tl, pair ? 1 : 0, tri ? 1 : 0, Tk, x,
+                                               dec);
+}
+
 // ---------------------------------------------------------------- launchers
 // The slab width SW is the widest of {64, 32, 16, 8} whose shared-memory plan fits.
 enum PlanKind { PLAN_GEQRT, PLAN_UNMQR, PLAN_PAIR_QRT, PLAN_PAIR_APPLY };
@@ -705,6 +816,9 @@ void launch_pair_apply(Mat<const T> F, int k, int nb, TileList tl, bool tri, con
 }
 
 #define INST(T)                                                                                  \
+  template void launch_qr_apply_vec<T>(Mat<const T>, int, int, TileList, bool, bool, const T*,   \
+                                       T*, const uint8_t*, cudaStream_t);                        \
+  template bool qr_apply_vec_fits<T>(int);                                                       \
   template void launch_geqrt<T>(Mat<T>, int, int, TileList, T*, int, const uint8_t*,             \
                                 cudaStream_t);                                                   \
   template void launch_unmqr<T>(Mat<const T>, int, int, TileList, const T*, int, Mat<T>,         \

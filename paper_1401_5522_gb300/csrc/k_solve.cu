@@ -24,14 +24,19 @@ __global__ void __launch_bounds__(256) k_trsv_diag(Mat<const T> U, int k, int nb
   for (int bb = nb / 32 - 1; bb >= 0; --bb) {
     const int b0 = bb * 32;
     if (warp == 0) {
+      // lane l holds row b0+l of the 32 x 32 diagonal block (all loads issued at once)
+      T u[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) u[r] = U(r0 + b0 + lane, r0 + b0 + r);
       T x = xs[b0 + lane];
       int bad = -1;
+#pragma unroll
       for (int r = 31; r >= 0; --r) {
-        const T d = U(r0 + b0 + r, r0 + b0 + r);
+        const T d = __shfl_sync(0xffffffffu, u[r], r);
         if (d == (T)0) { bad = b0 + r; break; }
         if (lane == r) x = x / d;
         const T xr = __shfl_sync(0xffffffffu, x, r);
-        if (lane < r) x -= U(r0 + b0 + lane, r0 + b0 + r) * xr;
+        if (lane < r) x -= u[r] * xr;
       }
       xs[b0 + lane] = x;
       if (lane == 0 && bad >= 0) s_bad = bad;

@@ -255,6 +255,7 @@ void enqueue_qr(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, bool do
       if constexpr (is_f32) {
         if (tc) { tc_apply_single(h, k, tl, C, c0, c1, s); return; }
       }
+      if (c1 - c0 == 1 && qr_apply_vec_fits<T>(nb)) { launch_qr_apply_vec<T>(Fc, k, nb, tl, false, false, Tk, C.p + c0 * C.ld, dec, s); return; }
       launch_unmqr<T>(Fc, k, nb, tl, Tk, n, C, c0, c1, dec, s);
     }
   };
@@ -270,6 +271,7 @@ void enqueue_qr(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, bool do
       if constexpr (is_f32) {
         if (tc) { tc_apply_pair(h, k, tl, tri, C, c0, c1, s); return; }
       }
+      if (c1 - c0 == 1 && qr_apply_vec_fits<T>(nb)) { launch_qr_apply_vec<T>(Fc, k, nb, tl, true, tri, Tk, C.p + c0 * C.ld, dec, s); return; }
       launch_pair_apply<T>(Fc, k, nb, tl, tri, Tk, n, C, c0, c1, dec, s);
     }
   };

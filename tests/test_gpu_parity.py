@@ -197,15 +197,16 @@ def test_fp32_decisions_match_float32_oracle():
     assert np.all(np.abs(mg[fin] - f.margin[fin]) <= 1e-2)
 
 
-@pytest.mark.parametrize("tree", ["flat_ts", "binary_tt"])
-def test_fp32_refinement_reaches_fp64_accuracy(tree):
+@pytest.mark.parametrize("tree,nb", [("flat_ts", 128), ("binary_tt", 128), ("binary_tt", 512),
+                                     ("grouped", 256)])
+def test_fp32_refinement_reaches_fp64_accuracy(tree, nb):
     luqr = L()
-    N = 1024
+    N = 1024 if nb < 512 else 1536 + 40
     A = gauss(N, 11)
     dA = cuda_colmajor(A)
     b = torch.from_numpy(A @ np.ones(N)).cuda()
     x = torch.zeros(N, dtype=torch.float64, device="cuda")
-    h = luqr.factor(dA, 128, "max", 100.0, precision="fp32", tree=tree)
+    h = luqr.factor(dA, nb, "max", 100.0, precision="fp32", tree=tree)
     st, iters, eta = h.refine(dA, b, x, tol=1e-14, max_iter=20)
     assert st == 0, (st, iters, eta)
     assert eta <= 1e-14
