@@ -301,57 +301,103 @@ void launch_getrf(const T* W, int64_t ldw, int k, int nb, T* S, int* piv_s, int*
 }
 
 // ---------------------------------------------------------------- ||A_kk^-1||_1
-// One warp per column c of X = U^-1 L^-1 P (FP64 arithmetic on the stored factors);
-// colsum[c] = sum_r |X[r, c]|.  Skipped when the tile has a zero pivot.
+// X = U^-1 L^-1 P (FP64 arithmetic on the stored factors); colsum[c] = sum_r |X[r, c]|.
+// One warp per column c (two per CTA): the column is substituted in shared memory, step
+// by step, with the factor's columns staged INV_CH at a time through cp.async (the next
+// group in flight) and shared by the CTA's warps.  FP64 arithmetic runs at 2 FMA per clock
+// per SM on this part, so the columns are spread over nb/2 CTAs.  Skipped when the tile
+// has a zero pivot.
+constexpr int INV_CH = 8;
+constexpr int INV_WARPS = 2;
+
 template <typename T>
-__global__ void k_invnorm(const T* __restrict__ S, int nb, const int* __restrict__ piv,
-                          double* __restrict__ colsum, const int* status) {
-  extern __shared__ __align__(16) double ys_all[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-  const int c = blockIdx.x * wpb + warp;
-  if (c >= nb) return;
+__global__ void __launch_bounds__(32 * INV_WARPS) k_invnorm(const T* __restrict__ S, int nb,
+                                                           const int* __restrict__ piv,
+                                                           double* __restrict__ colsum,
+                                                           const int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* xs_all = reinterpret_cast<double*>(smem_raw);                 // INV_WARPS x nb
+  T* colbuf = reinterpret_cast<T*>(xs_all + (size_t)INV_WARPS * nb);    // 2 x INV_CH x nb
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c = blockIdx.x * INV_WARPS + warp;
   if (status[ST_ZERO_ROW] >= 0) {
-    if (lane == 0) colsum[c] = INFINITY;
+    if (lane == 0 && c < nb) colsum[c] = INFINITY;
     return;
   }
-  double* ys = ys_all + warp * nb;
+  double* ys = xs_all + (size_t)warp * nb;
   int pos = c;   // row of the single 1 of column c of P
   for (int r = 0; r < nb; ++r) {
-    int p = piv[r];
+    const int p = piv[r];
     if (pos == r) pos = p;
     else if (pos == p) pos = r;
   }
   for (int row = lane; row < nb; row += 32) ys[row] = (row == pos) ? 1.0 : 0.0;
+  auto fetch = [&](int first, int slot) {
+    T* dst = colbuf + (size_t)slot * INV_CH * nb;
+    for (int idx = tid; idx < INV_CH * nb; idx += 32 * INV_WARPS) {
+      const int cc = idx / nb, i = idx - cc * nb, col = first + cc;
+      if (col >= 0 && col < nb) cp_async(&dst[idx], &S[i + (int64_t)col * nb]);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  const int nch = nb / INV_CH;
+  // y <- L^-1 y (unit lower), columns r = 0 .. nb-2
+  fetch(0, 0);
+  for (int g = 0; g < nch; ++g) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    fetch((g + 1) * INV_CH, (g + 1) & 1);
+    const T* base = colbuf + (size_t)(g & 1) * INV_CH * nb;
+    for (int cc = 0; cc < INV_CH; ++cc) {
+      const int r = g * INV_CH + cc;
+      if (r >= nb - 1 || c >= nb) break;
+      __syncwarp();
+      const double yr = ys[r];
+      if (r < pos || yr == 0.0) continue;
+      const T* col = base + (size_t)cc * nb;
+      for (int row = r + 1 + lane; row < nb; row += 32) ys[row] -= (double)col[row] * yr;
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  // x <- U^-1 y, columns r = nb-1 .. 0; group g holds columns [nb-(g+1)*CH, nb-g*CH)
+  fetch(nb - INV_CH, 0);
+  for (int g = 0; g < nch; ++g) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    fetch(nb - (g + 2) * INV_CH, (g + 1) & 1);
+    const T* base = colbuf + (size_t)(g & 1) * INV_CH * nb;
+    if (c < nb) {
+      for (int cc = INV_CH - 1; cc >= 0; --cc) {
+        const int r = nb - (g + 1) * INV_CH + cc;
+        const T* col = base + (size_t)cc * nb;
+        __syncwarp();
+        if (lane == 0) ys[r] = ys[r] / (double)col[r];
+        __syncwarp();
+        const double xr = ys[r];
+        if (xr != 0.0)
+          for (int row = lane; row < r; row += 32) ys[row] -= (double)col[row] * xr;
+      }
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncwarp();
-  for (int r = pos; r < nb - 1; ++r) {          // y <- L^-1 y (unit lower)
-    const double yr = ys[r];
-    if (yr != 0.0)
-      for (int row = r + 1 + lane; row < nb; row += 32) ys[row] -= (double)S[row + r * nb] * yr;
-    __syncwarp();
+  if (c < nb) {
+    double sum = 0.0;
+    for (int row = lane; row < nb; row += 32) sum += fabs(ys[row]);
+    sum = warp_sum_d(sum);
+    if (lane == 0) colsum[c] = sum;
   }
-  for (int r = nb - 1; r >= 0; --r) {           // x <- U^-1 y
-    if (lane == 0) ys[r] = ys[r] / (double)S[r + r * nb];
-    __syncwarp();
-    const double xr = ys[r];
-    if (xr != 0.0)
-      for (int row = lane; row < r; row += 32) ys[row] -= (double)S[row + r * nb] * xr;
-    __syncwarp();
-  }
-  double sum = 0.0;
-  for (int row = lane; row < nb; row += 32) sum += fabs(ys[row]);
-  sum = warp_sum_d(sum);
-  if (lane == 0) colsum[c] = sum;
 }
 
 template <typename T>
 void launch_invnorm(const T* S, int nb, const int* piv_s, double* colsum, const int* status,
                     cudaStream_t s) {
-  const int wpb = 4;
-  {
-    ProfScope ps_("k_invnorm", s);
-    k_invnorm<T><<<(nb + wpb - 1) / wpb, 32 * wpb, wpb * nb * sizeof(double), s>>>(S, nb, piv_s,
-                                                                                  colsum, status);
-  }
+  const size_t smem = sizeof(double) * INV_WARPS * (size_t)nb + sizeof(T) * 2 * INV_CH * (size_t)nb;
+  ensure_dyn_smem<k_invnorm<T>>(smem);
+  ProfScope ps_("k_invnorm", s);
+  k_invnorm<T><<<(nb + INV_WARPS - 1) / INV_WARPS, 32 * INV_WARPS, smem, s>>>(S, nb, piv_s,
+                                                                             colsum, status);
 }
 
 // ---------------------------------------------------------------- decision
