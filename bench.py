@@ -132,7 +132,7 @@ def step_tc_bytes(dec, n, nb, tree, ncols_extra):
 
 # CUDA function behind each launch label of the library's profiler
 KERNEL_OF_LABEL = {
-    **{f"k_tc_{r}": "k_gemm_tc3" for r in ("ttmqr_w", "ttmqr_c1", "ttmqr_c2", "tsmqr_w",
+    **{f"k_tc_{r}": "k_gemm_tc4" for r in ("ttmqr_w", "ttmqr_c1", "ttmqr_c2", "tsmqr_w",
                                             "tsmqr_c1", "tsmqr_c2", "unmqr_w", "unmqr_c",
                                             "lu_gemm")},
     "k_tc_gram": "k_gemm_tc", "k_tc_vt": "k_gemm_tc",

@@ -14,6 +14,8 @@
 //
 // Every wait on an mbarrier is bounded; on expiry the kernel records LUQR_ERR_TIMEOUT in
 // the status word, waits (bounded) for its own MMAs, frees its TMEM and returns.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace luqr {
@@ -1101,6 +1103,253 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc3(TcArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- persistent form
+// Persistent version of the warp-specialised contraction: one CTA per SM walks the
+// 256 x 128 output tiles of the launch, and two TMEM accumulators let the epilogue of tile
+// i (warps 8-11) overlap the main loop of tile i+1.  Without the overlap every SM alternates
+// between a tensor-bound main loop and an HBM-bound epilogue, and the two phases of all SMs
+// line up.  Roles:
+//   warp 0      raw B chunks (cp.async) into a 4-slot ring
+//   warp 1      tcgen05.mma issue (one thread) into accumulator (tile parity)
+//   warp 2      packed A chunks (cp.async.bulk) into a 3-stage ring
+//   warps 4-7   TF32 hi/lo split of B into the stage
+//   warps 8-11  epilogue: TMEM -> registers -> C, then free the accumulator
+// Chunks are numbered across tiles (g = tile_iter * nK + c) for the ring slots and parities.
+#ifndef LUQR_T4_TPC
+#define LUQR_T4_TPC 8
+#endif
+constexpr int T4_BN = 128;
+constexpr int T4_STG = 3;
+constexpr int T4_RAW = 4;
+constexpr int T4_ABYTES = 2 * 2 * P_ABLK;                   // two M halves x (hi, lo)
+constexpr int T4_BBYTES = 2 * T4_BN * P_BK * 4;             // hi + lo
+constexpr int T4_STAGE = T4_ABYTES + T4_BBYTES;             // 48 KB
+constexpr int T4_RAWB = T4_BN * P_BK * 4;                   // 8 KB
+constexpr int T4_SMEM = T4_STG * T4_STAGE + T4_RAW * T4_RAWB + 512;
+
+__global__ void __launch_bounds__(384, 1) k_gemm_tc4(TcArgs a, int mtiles, int ntiles,
+                                                     int total) {
+  if (a.dec != nullptr && a.dec[a.k_step] != a.want) return;
+  if (a.status != nullptr && a.status[ST_CODE] != 0) return;
+  extern __shared__ __align__(1024) unsigned char smem_p4[];
+  unsigned char* rawbase = smem_p4 + T4_STG * T4_STAGE;
+  uint64_t* raw_full = reinterpret_cast<uint64_t*>(rawbase + T4_RAW * T4_RAWB);
+  uint64_t* raw_empty = raw_full + T4_RAW;
+  uint64_t* a_full = raw_empty + T4_RAW;
+  uint64_t* b_full = a_full + T4_STG;
+  uint64_t* st_empty = b_full + T4_STG;
+  uint64_t* acc_full = st_empty + T4_STG;
+  uint64_t* acc_empty = acc_full + 2;
+  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  volatile int* fail = reinterpret_cast<volatile int*>(taddr_slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nK = a.K / P_BK;
+  // tiles of this CTA: tile = blockIdx.x + it * gridDim.x
+  const int ntile_cta = (total - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  auto tile_of = [&](int it, int64_t& t, int64_t& m0, int64_t& n0) {
+    const int tile = (int)blockIdx.x + it * (int)gridDim.x;
+    const int per = mtiles * ntiles;
+    t = tile / per;
+    const int r = tile - (int)t * per;
+    m0 = (int64_t)(r / ntiles) * 256;
+    n0 = (int64_t)(r % ntiles) * T4_BN;
+  };
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(taddr_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    *fail = 0;
+    for (int q = 0; q < T4_RAW; ++q) {
+      mbar_init(&raw_full[q], 32);
+      mbar_init(&raw_empty[q], 4);
+    }
+    for (int q = 0; q < T4_STG; ++q) {
+      mbar_init(&a_full[q], 1);
+      mbar_init(&b_full[q], 4);
+      mbar_init(&st_empty[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&acc_full[q], 1);
+      mbar_init(&acc_empty[q], 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *taddr_slot;
+
+  if (warp == 0) {
+    // ---- raw B producer
+    bool stop = false;
+    for (int it = 0; it < ntile_cta && !stop; ++it) {
+      int64_t t, m0, n0;
+      tile_of(it, t, m0, n0);
+      const float* B = a.B + t * a.sB;
+      for (int c = 0; c < nK; ++c) {
+        const int g = it * nK + c, slot = g % T4_RAW;
+        bool ok = g < T4_RAW || wwait(&raw_empty[slot], (uint32_t)((g / T4_RAW) - 1) & 1, fail);
+        if (!__all_sync(0xffffffffu, ok ? 1 : 0)) { stop = true; break; }
+        unsigned char* raw = rawbase + slot * T4_RAWB;
+        const int k0 = c * P_BK;
+        for (int idx = lane; idx < T4_BN * (P_BK / 4); idx += 32) {
+          const int q = idx & 3, col = idx >> 2;
+          const int64_t gc = n0 + col;
+          const bool in = gc < a.N;
+          const float* src = in ? B + (k0 + 4 * q) + gc * a.ldb : B;
+          cp_async16_zfill(raw + idx * 16, src, in ? 16u : 0u);
+        }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                         smem_u32(&raw_full[slot]))
+                     : "memory");
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (warp == 1) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc_tf32(128, T4_BN);
+      int last_g = -1;
+      bool stop = false;
+      for (int it = 0; it < ntile_cta && !stop; ++it) {
+        int64_t t, m0, n0;
+        tile_of(it, t, m0, n0);
+        const int mh = (a.M - m0) > 128 ? 2 : 1;
+        const int buf = it & 1;
+        if (it >= 2 && !wwait(&acc_empty[buf], (uint32_t)((it / 2) - 1) & 1, fail)) break;
+        tc_fence_after();
+        for (int c = 0; c < nK; ++c) {
+          const int g = it * nK + c, st = g % T4_STG;
+          const uint32_t ph = (uint32_t)(g / T4_STG) & 1;
+          if (!wwait(&a_full[st], ph, fail) || !wwait(&b_full[st], ph, fail)) { stop = true; break; }
+          tc_fence_after();
+          unsigned char* sa = smem_p4 + st * T4_STAGE;
+          const uint32_t sbase = smem_u32(sa + T4_ABYTES);
+#pragma unroll
+          for (int s8 = 0; s8 < P_BK / 8; ++s8) {
+            const uint32_t koff = (uint32_t)s8 * 2 * TC_LBO;
+            const uint64_t bhi = make_desc_sbo(sbase + koff, P_SBO);
+            const uint64_t blo = make_desc_sbo(sbase + T4_BN * P_BK * 4 + koff, P_SBO);
+            for (int h = 0; h < mh; ++h) {
+              const uint32_t abase = smem_u32(sa + h * 2 * P_ABLK);
+              const uint64_t ahi = make_desc_sbo(abase + koff, P_SBO);
+              const uint64_t alo = make_desc_sbo(abase + P_ABLK + koff, P_SBO);
+              const uint32_t d = tmem + (uint32_t)(buf * 256 + h * T4_BN);
+              const uint32_t acc0 = (c > 0 || s8 > 0) ? 1u : 0u;
+              tc_mma(d, alo, bhi, idesc, acc0);
+              tc_mma(d, ahi, blo, idesc, 1u);
+              tc_mma(d, ahi, bhi, idesc, 1u);
+            }
+          }
+          tc_commit(&st_empty[st]);
+          last_g = g;
+        }
+        if (stop) break;
+        tc_commit(&acc_full[buf]);
+      }
+      if (last_g >= 0)
+        wwait(&st_empty[last_g % T4_STG], (uint32_t)(last_g / T4_STG) & 1, fail, false);
+    }
+  } else if (warp == 2) {
+    // ---- packed A producer
+    if (lane == 0) {
+      int last_g = -1;
+      bool stop = false;
+      for (int it = 0; it < ntile_cta && !stop; ++it) {
+        int64_t t, m0, n0;
+        tile_of(it, t, m0, n0);
+        const int mh = (a.M - m0) > 128 ? 2 : 1;
+        const unsigned char* Apk = a.Apk + t * a.sApk;
+        for (int c = 0; c < nK; ++c) {
+          const int g = it * nK + c, st = g % T4_STG;
+          if (g >= T4_STG && !wwait(&st_empty[st], (uint32_t)((g / T4_STG) - 1) & 1, fail)) {
+            stop = true;
+            break;
+          }
+          unsigned char* sa = smem_p4 + st * T4_STAGE;
+          mbar_expect_tx(&a_full[st], (uint32_t)mh * 2 * P_ABLK);
+          for (int h = 0; h < mh; ++h) {
+            const unsigned char* src = Apk + (((int64_t)(m0 / 128 + h) * nK + c) * 2 * P_ABLK);
+            bulk_g2s(sa + h * 2 * P_ABLK, src, 2 * P_ABLK, &a_full[st]);
+          }
+          last_g = g;
+        }
+      }
+      for (int q = last_g; q >= 0 && q > last_g - T4_STG; --q)
+        wwait(&a_full[q % T4_STG], (uint32_t)(q / T4_STG) & 1, fail, false);
+    }
+  } else if (warp >= 4 && warp < 8) {
+    // ---- converters
+    const int ct = tid - 128;
+    bool stop = false;
+    for (int it = 0; it < ntile_cta && !stop; ++it) {
+      for (int c = 0; c < nK; ++c) {
+        const int g = it * nK + c, slot = g % T4_RAW, st = g % T4_STG;
+        bool ok = wwait(&raw_full[slot], (uint32_t)(g / T4_RAW) & 1, fail);
+        if (ok && g >= T4_STG) ok = wwait(&st_empty[st], (uint32_t)((g / T4_STG) - 1) & 1, fail);
+        if (!__all_sync(0xffffffffu, ok ? 1 : 0)) { stop = true; break; }
+        const unsigned char* raw = rawbase + slot * T4_RAWB;
+        unsigned char* bhi = smem_p4 + st * T4_STAGE + T4_ABYTES;
+        unsigned char* blo = bhi + T4_BN * P_BK * 4;
+        for (int idx = ct; idx < T4_BN * (P_BK / 4); idx += 128) {
+          const int q = idx & 3, col = idx >> 2;
+          const float4 x = *reinterpret_cast<const float4*>(raw + idx * 16);
+          uint4 hh, ll;
+          hh.x = tf32_bits(x.x); ll.x = tf32_bits(x.x - __uint_as_float(hh.x));
+          hh.y = tf32_bits(x.y); ll.y = tf32_bits(x.y - __uint_as_float(hh.y));
+          hh.z = tf32_bits(x.z); ll.z = tf32_bits(x.z - __uint_as_float(hh.z));
+          hh.w = tf32_bits(x.w); ll.w = tf32_bits(x.w - __uint_as_float(hh.w));
+          const uint32_t off = kmajor_off16(col, 4 * q);
+          *reinterpret_cast<uint4*>(bhi + off) = hh;
+          *reinterpret_cast<uint4*>(blo + off) = ll;
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive1(&raw_empty[slot]);
+          mbar_arrive1(&b_full[st]);
+        }
+      }
+    }
+  } else if (warp >= 8) {
+    // ---- epilogue (warp 8 + e owns TMEM lanes 32e..32e+31 of each half)
+    const int e = warp - 8;
+    for (int it = 0; it < ntile_cta; ++it) {
+      int64_t t, m0, n0;
+      tile_of(it, t, m0, n0);
+      const int mh = (a.M - m0) > 128 ? 2 : 1;
+      const int buf = it & 1;
+      bool ok = wwait(&acc_full[buf], (uint32_t)(it / 2) & 1, fail);
+      if (!__all_sync(0xffffffffu, ok ? 1 : 0)) break;
+      tc_fence_after();
+      float* C = a.C + t * a.sC;
+      const float* C1 = a.C1 ? a.C1 + t * a.sC1 : nullptr;
+      for (int h = 0; h < mh; ++h) {
+        const int64_t row = m0 + h * 128 + e * 32 + lane;
+        for (int cc = 0; cc < T4_BN; cc += 32) {
+          if (n0 + cc >= a.N) break;
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(e * 32) << 16) + (uint32_t)(buf * 256 + h * T4_BN + cc), v);
+          tc_epi32(a, C, C1, row, n0 + cc, v);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive1(&acc_empty[buf]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && *fail && a.status != nullptr) atomicCAS(&a.status[ST_CODE], 0, -6);
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
 size_t tc_packed_bytes(int64_t M, int K) {
   const int64_t mb = (M + 127) / 128, nK = (K + P_BK - 1) / P_BK;
   return (size_t)(mb * nK) * 2 * P_ABLK;
@@ -1125,8 +1374,21 @@ void launch_tc2(const TcArgs& a, int batch, const char* name, cudaStream_t s) {
                    (reinterpret_cast<uintptr_t>(a.B) % 16) == 0;
   ProfScope ps_(name, s);
   if (vec) {
-    ensure_dyn_smem<k_gemm_tc3>(W_SMEM);
-    k_gemm_tc3<<<grid, 256, W_SMEM, s>>>(a);
+    static int sms = 0;
+    if (sms == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (sms <= 0) sms = 1;
+    }
+    const int mtiles = (int)((a.M + 255) / 256), ntiles = (int)((a.N + T4_BN - 1) / T4_BN);
+    const int64_t total = (int64_t)mtiles * ntiles * batch;
+    // a few tiles per CTA: enough to overlap epilogues with main loops, few enough that SMs
+    // turn over often and the high-priority panel kernels get scheduled between CTAs
+    const int64_t want = (total + LUQR_T4_TPC - 1) / LUQR_T4_TPC;
+    const int ctas = (int)std::min<int64_t>(total, std::max<int64_t>(want, sms));
+    ensure_dyn_smem<k_gemm_tc4>(T4_SMEM);
+    k_gemm_tc4<<<ctas, 384, T4_SMEM, s>>>(a, mtiles, ntiles, (int)total);
   } else {
     ensure_dyn_smem<k_gemm_tc2>(P_SMEM);
     k_gemm_tc2<<<grid, TC_THREADS, P_SMEM, s>>>(a);
