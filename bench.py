@@ -45,10 +45,9 @@ def parse(argv=None):
     p.add_argument("--precision", default="fp32")
     p.add_argument("--tol", type=float, default=1e-13)
     p.add_argument("--fp32-kernels", default="default", choices=["default", "cuda", "tensor"])
-    p.add_argument("--speculate", default="off", choices=["off", "repeat", "mlp"],
-                   help="predicted-branch speculation of the factorization")
-    p.add_argument("--mlp-params", default=None,
-                   help="float32 .npy parameter vector of the decision MLP (speculate=mlp)")
+    p.add_argument("--speculate", default="mlp", choices=["off", "repeat", "mlp"],
+                   help="predicted-branch speculation of the factorization (mlp: the network "
+                        "is trained at startup, outside the timed region)")
     p.add_argument("--fp64-baseline", type=int, default=1, help="also time one plain FP64 solve")
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--cpu-N", type=int, default=2048, help="oracle sample size")
@@ -326,14 +325,12 @@ def batched_form(args, plain_ms_per_normflop=None):
     return out
 
 
-def speculation_form(args, A, b, x, base_ms):
+def train_decision_mlp(args):
     """Trains the decision MLP with the library's kernels on logged (features, decision)
     pairs from N=4096, nb=256 iid N(0,1) matrices with 20% of the diagonal tiles scaled
-    by 1e-8 (Max alpha in {1e4, 3e4, 1e5}), then times the headline solve with MLP and with
-    repeat-previous speculation (same decisions and results as the plain run)."""
+    by 1e-8 (Max alpha in {1e4, 3e4, 1e5}: paper-scale alpha, so both classes occur)."""
     import numpy as np
-    import torch
-    from paper_1401_5522_gb300 import inputs, luqr
+    from paper_1401_5522_gb300 import inputs
     from paper_1401_5522_gb300 import speculation as S
     N0, nb0 = 4096, 256
     runs = []
@@ -345,18 +342,30 @@ def speculation_form(args, A, b, x, base_ms):
     t0 = time.time()
     X, y = S.collect(runs)
     params, losses = S.train(X, y, epochs=200, batch=128, lr=3e-3)
-    train_s = time.time() - t0
-    out = {"training": {"samples": int(len(y)), "lu_fraction": float(np.mean(y)),
-                        "loss_first": losses[0], "loss_last": losses[-1], "seconds": train_s}}
+    info = {"samples": int(len(y)), "lu_fraction": float(np.mean(y)),
+            "loss_first": losses[0], "loss_last": losses[-1], "seconds": time.time() - t0}
+    return params, info
+
+
+def speculation_form(args, A, b, x, head_ms, params, train_info):
+    """Times the headline solve with speculation off and with the repeat-previous predictor
+    (decisions and results are the same in every mode)."""
+    import numpy as np
+    import torch
+    from paper_1401_5522_gb300 import luqr
+    out = {"training": train_info, "headline_mode": args.speculate}
     stream = torch.cuda.current_stream()
-    for mode, extra in (("mlp", {"mlp_params": params}), ("repeat", {})):
+    modes = [("off", {}), ("repeat", {}), ("mlp", {"mlp_params": params})]
+    for mode, extra in modes:
+        if mode == args.speculate:
+            continue
         def solve():
             h = luqr.factor(A, args.nb, args.criterion, args.alpha, tree=args.tree,
                             precision=args.precision, fp32_kernels=args.fp32_kernels,
                             speculate=mode, **extra)
             st, its, eta = h.refine(A, b, x, tol=args.tol, max_iter=30)
             dec, _ = h.decisions()
-            pred = h.features()[1]
+            pred = h.features()[1] if mode != "off" else dec
             h.close()
             return st, eta, dec, pred
         solve()
@@ -369,9 +378,10 @@ def speculation_form(args, A, b, x, base_ms):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
-        out[mode] = {"ms_per_solve": ms, "speedup_vs_speculation_off": base_ms / ms,
-                     "eta": eta, "status": st,
-                     "prediction_accuracy": float(np.mean(pred == dec))}
+        out[mode] = {"ms_per_solve": ms, "headline_speedup_over_this": ms / head_ms,
+                     "eta": eta, "status": st}
+        if mode != "off":
+            out[mode]["prediction_accuracy"] = float(np.mean(pred == dec))
     return out
 
 
@@ -387,7 +397,7 @@ def main():
     config = {"workload": (f"hybrid LU-QR solve, N={args.N}, nb={args.nb}, A=U diag(s) V^T "
                            f"kappa={args.kappa:g}, b=A*1, {args.criterion} alpha={args.alpha:g}, "
                            f"{args.tree} tree, {args.precision} factorization + FP64 refinement to "
-                           f"eta<={args.tol:g}"),
+                           f"eta<={args.tol:g}, {args.speculate} speculation"),
               "N": args.N, "nb": args.nb, "kappa": args.kappa, "criterion": args.criterion,
               "alpha": args.alpha, "tree": args.tree, "factor_precision": args.precision,
               "refinement": "fp64", "fp32_kernels": args.fp32_kernels,
@@ -427,15 +437,17 @@ def main():
     stream = torch.cuda.current_stream()
     info = {}
     spec = {"speculate": args.speculate}
+    mlp_params, train_info = train_decision_mlp(args)
     if args.speculate == "mlp":
-        spec["mlp_params"] = torch.from_numpy(
-            np.load(args.mlp_params).astype(np.float32)).cuda()
+        spec["mlp_params"] = mlp_params
 
     def one_solve():
         h = luqr.factor(A, nb, args.criterion, args.alpha, tree=args.tree, precision=args.precision,
                         fp32_kernels=args.fp32_kernels, **spec)
         st, its, eta = h.refine(A, b, x, tol=args.tol, max_iter=30)
         dec, _ = h.decisions()
+        if args.speculate != "off":
+            info["pred"] = h.features()[1]
         h.close()
         info["iters"] = its
         info["eta"] = eta
@@ -588,12 +600,13 @@ def main():
 
     forms = None
     if args.forms:
-        forms = {"speculative": speculation_form(args, A, b, x, ms),
+        forms = {"speculation": speculation_form(args, A, b, x, ms, mlp_params, train_info),
                  "batched": batched_form(args)}
         if plain is not None:
-            for key in ("mlp", "repeat"):
-                forms["speculative"][key]["speedup_vs_plain_fp64"] = (
-                    plain["ms_per_solve"] / forms["speculative"][key]["ms_per_solve"])
+            for key in ("off", "repeat", "mlp"):
+                if key in forms["speculation"]:
+                    forms["speculation"][key]["speedup_vs_plain_fp64"] = (
+                        plain["ms_per_solve"] / forms["speculation"][key]["ms_per_solve"])
 
     if rank != 0:
         return
@@ -604,6 +617,9 @@ def main():
             "dtype": "f32+f64", "data": "synthetic", "config": config,
             "eta": eta_gpu, "ir_iters": iters, "status": statuses,
             "lu_fraction": float(np.mean(dec == 1)),
+            "speculation": {"mode": args.speculate,
+                            "prediction_accuracy": (float(np.mean(info["pred"] == dec))
+                                                    if "pred" in info else None)},
             "plain_fp64": plain, "roofline": roofline, "gpu_launches": gpu_launches,
             "kernels": kernel_table, "e2e": e2e, "clocks": clk, "forms": forms,
             "cpu_baseline": cpu_baseline_dict(cpu, args)}
