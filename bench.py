@@ -140,8 +140,8 @@ KERNEL_OF_LABEL = {
 }
 
 # DRAM bytes per algorithmic byte of the tensor-core update kernel, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum of a bulk launch at N=8192, see profiles/)
-TRAFFIC_RATIO = {}
+# (dram__bytes_read.sum + dram__bytes_write.sum of two bulk launches at N=8192)
+TRAFFIC_RATIO = {"k_gemm_tc4": 0.95}
 
 
 def traffic_per_launch(kernel, alg_bytes_per_launch):
@@ -437,7 +437,8 @@ def main():
     stream = torch.cuda.current_stream()
     info = {}
     spec = {"speculate": args.speculate}
-    mlp_params, train_info = train_decision_mlp(args)
+    mlp_params, train_info = (train_decision_mlp(args) if args.speculate == "mlp" or args.forms
+                              else (None, None))
     if args.speculate == "mlp":
         spec["mlp_params"] = mlp_params
 

@@ -60,60 +60,106 @@ __global__ void __launch_bounds__(256) k_mlp_forward(const float* __restrict__ p
   }
 }
 
+// Gradient of the mean binary cross-entropy: each block takes chunks of GB samples, keeps
+// their activations and back-propagated errors in shared memory (one warp per sample in
+// the forward and backward passes), then forms the parameter gradients as sums over the
+// chunk's samples with one thread per parameter (no atomics); a block adds its totals to
+// the global gradient once.
+constexpr int GB = 64;
+
 __global__ void __launch_bounds__(256) k_mlp_grad(const float* __restrict__ params,
                                                   const float* __restrict__ X,
                                                   const float* __restrict__ lab, int B,
                                                   float* __restrict__ grad, float* __restrict__ loss) {
-  __shared__ float P[MP];
-  __shared__ float G[MP];
+  extern __shared__ __align__(16) float sm[];
+  float* P = sm;                     // MP
+  float* xs = P + MP + 3;            // GB x MF
+  float* h1 = xs + GB * MF;          // GB x MH (post-activation)
+  float* h2 = h1 + GB * MH;          // GB x MH
+  float* d1 = h2 + GB * MH;          // GB x MH (dL/dz1)
+  float* d2 = d1 + GB * MH;          // GB x MH (dL/dz2)
+  float* dz = d2 + GB * MH;          // GB
   __shared__ float Ls;
-  for (int i = threadIdx.x; i < MP; i += blockDim.x) { P[i] = params[i]; G[i] = 0.f; }
-  if (threadIdx.x == 0) Ls = 0.f;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int i = tid; i < MP; i += blockDim.x) P[i] = params[i];
+  if (tid == 0) Ls = 0.f;
   const float invB = 1.f / (float)B;
-  for (int s = blockIdx.x * nw + warp; s < B; s += gridDim.x * nw) {
-    const float* x = X + (int64_t)s * MF;
-    const float y = lab[s];
-    Act a;
-    warp_forward(P, x, a);
-    const float z = a.out;
-    const float l = fmaxf(z, 0.f) - z * y + log1pf(expf(-fabsf(z)));
-    const float dz = (1.f / (1.f + expf(-z)) - y) * invB;
-    if (lane == 0) {
-      atomicAdd(&Ls, l * invB);
-      atomicAdd(&G[O_B3], dz);
-    }
-    float dz2[2];
+  // per-thread partial sums of the parameters it owns (parameters tid, tid+256, ...)
+  constexpr int PPT = (MP + 255) / 256;
+  float acc[PPT];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int j = lane + 32 * u;
-      atomicAdd(&G[O_W3 + j], dz * a.h2[u]);
-      dz2[u] = a.z2[u] > 0.f ? dz * P[O_W3 + j] : 0.f;
-      atomicAdd(&G[O_B2 + j], dz2[u]);
-    }
-    float dh1[2] = {0.f, 0.f};
-    for (int i = 0; i < MH; ++i) {
-      const float hi = __shfl_sync(0xffffffffu, a.h1[i >> 5], i & 31);
-      atomicAdd(&G[O_W2 + lane * MH + i], dz2[0] * hi);
-      atomicAdd(&G[O_W2 + (lane + 32) * MH + i], dz2[1] * hi);
-      float part = P[O_W2 + lane * MH + i] * dz2[0] + P[O_W2 + (lane + 32) * MH + i] * dz2[1];
-      part = warp_sum_f(part);
-      if ((i & 31) == lane) dh1[i >> 5] = part;
-    }
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int j = lane + 32 * u;
-      const float dz1 = a.z1[u] > 0.f ? dh1[u] : 0.f;
-      atomicAdd(&G[O_B1 + j], dz1);
-#pragma unroll
-      for (int i = 0; i < MF; ++i) atomicAdd(&G[O_W1 + j * MF + i], dz1 * x[i]);
-    }
-  }
+  for (int q = 0; q < PPT; ++q) acc[q] = 0.f;
   __syncthreads();
-  for (int i = threadIdx.x; i < MP; i += blockDim.x)
-    if (G[i] != 0.f) atomicAdd(&grad[i], G[i]);
-  if (threadIdx.x == 0 && loss) atomicAdd(loss, Ls);
+  for (int s0 = blockIdx.x * GB; s0 < B; s0 += gridDim.x * GB) {
+    const int cnt = min(GB, B - s0);
+    for (int i = tid; i < cnt * MF; i += blockDim.x) xs[i] = X[(int64_t)s0 * MF + i];
+    __syncthreads();
+    for (int sl = warp; sl < cnt; sl += nw) {
+      Act a;
+      warp_forward(P, xs + sl * MF, a);
+      const float z = a.out, y = lab[s0 + sl];
+      const float dzz = (1.f / (1.f + expf(-z)) - y) * invB;
+      float dz2v[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int j = lane + 32 * u;
+        h1[sl * MH + j] = a.h1[u];
+        h2[sl * MH + j] = a.h2[u];
+        dz2v[u] = a.z2[u] > 0.f ? dzz * P[O_W3 + j] : 0.f;
+        d2[sl * MH + j] = dz2v[u];
+      }
+      // dL/dh1_i = sum_j W2[j][i] dz2_j, lanes split i
+      float dh1[2] = {0.f, 0.f};
+      for (int i = 0; i < MH; ++i) {
+        float part = P[O_W2 + lane * MH + i] * dz2v[0] + P[O_W2 + (lane + 32) * MH + i] * dz2v[1];
+        part = warp_sum_f(part);
+        if ((i & 31) == lane) dh1[i >> 5] = part;
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) d1[sl * MH + lane + 32 * u] = a.z1[u] > 0.f ? dh1[u] : 0.f;
+      if (lane == 0) {
+        dz[sl] = dzz;
+        atomicAdd(&Ls, (fmaxf(z, 0.f) - z * y + log1pf(expf(-fabsf(z)))) * invB);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      const int p = tid + 256 * q;
+      if (p >= MP) break;
+      float g = 0.f;
+      if (p < O_B1) {                       // W1[j][i] += d1[s][j] x[s][i]
+        const int j = p / MF, i = p % MF;
+        for (int sl = 0; sl < cnt; ++sl) g += d1[sl * MH + j] * xs[sl * MF + i];
+      } else if (p < O_W2) {                // b1[j]
+        const int j = p - O_B1;
+        for (int sl = 0; sl < cnt; ++sl) g += d1[sl * MH + j];
+      } else if (p < O_B2) {                // W2[j][i] += d2[s][j] h1[s][i]
+        const int j = (p - O_W2) / MH, i = (p - O_W2) % MH;
+        for (int sl = 0; sl < cnt; ++sl) g += d2[sl * MH + j] * h1[sl * MH + i];
+      } else if (p < O_W3) {                // b2[j]
+        const int j = p - O_B2;
+        for (int sl = 0; sl < cnt; ++sl) g += d2[sl * MH + j];
+      } else if (p < O_B3) {                // W3[j] += dz[s] h2[s][j]
+        const int j = p - O_W3;
+        for (int sl = 0; sl < cnt; ++sl) g += dz[sl] * h2[sl * MH + j];
+      } else {                              // b3
+        for (int sl = 0; sl < cnt; ++sl) g += dz[sl];
+      }
+      acc[q] += g;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    const int p = tid + 256 * q;
+    if (p < MP && acc[q] != 0.f) atomicAdd(&grad[p], acc[q]);
+  }
+  if (tid == 0 && loss) atomicAdd(loss, Ls);
+}
+
+static size_t mlp_grad_smem() {
+  return sizeof(float) * (MP + 3 + GB * MF + 4 * GB * MH + GB);
 }
 
 __global__ void k_mlp_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -319,11 +365,13 @@ extern "C" int luqr_mlp_grad(const float* dparams, const float* dX, const float*
                              float* dgrad, float* dloss, void* stream) {
   if (!dparams || !dX || !dlabels || !dgrad || B < 1) return LUQR_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int blocks = (B + 255) / 256;
+  int blocks = (B + luqr::GB - 1) / luqr::GB;
   if (blocks > 1024) blocks = 1024;
   {
+    const size_t smem = luqr::mlp_grad_smem();
+    luqr::ensure_dyn_smem<luqr::k_mlp_grad>(smem);
     luqr::ProfScope ps_("k_mlp_grad", s);
-    luqr::k_mlp_grad<<<blocks, 256, 0, s>>>(dparams, dX, dlabels, B, dgrad, dloss);
+    luqr::k_mlp_grad<<<blocks, 256, smem, s>>>(dparams, dX, dlabels, B, dgrad, dloss);
   }
   return cudaGetLastError() == cudaSuccess ? LUQR_OK : LUQR_ERR_CUDA;
 }
