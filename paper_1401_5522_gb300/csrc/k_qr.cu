@@ -358,6 +358,142 @@ __device__ void panel_qr(T* Rs, T* Ps, int nrows, bool tri, int jb, T* tau_s, T*
   __syncthreads();
 }
 
+// Register form of panel_qr (same operations per element): thread (warp w, lane c) keeps
+// rows w + 8q (q < RPT) of panel column c in registers; column j's values reach the other
+// lanes by warp shuffles, so the per-column dot products and updates need no shared-memory
+// traffic.  The panel is loaded from and stored back to Ps around the loop.
+template <typename T, bool SINGLE, int RPT>
+__device__ void panel_qr_reg(T* Rs, T* Ps, int nrows, bool tri, int jb, T* tau_s, T* Ts,
+                             T* scratch) {
+  static_assert(NT == 256 && IB == 32, "thread map assumes 8 warps x 32 columns");
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  T* part = scratch;               // [8][IB]
+  T* nrm = part + 8 * IB;          // [8]
+  T* wv = nrm + 8;                 // [IB]
+  T* sinv = wv + IB;               // [IB]
+  T* sc = sinv + IB;               // [3] tau, inv, beta
+  T* topbuf = sc + 3;              // [IB] row j of the panel (single)
+  auto lo = [&](int j) { return SINGLE ? j + 1 : 0; };
+  auto hi = [&](int j) { return SINGLE ? nrows : (tri ? min(jb + j + 1, nrows) : nrows); };
+  const int c = lane;
+  T x[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int r = w + 8 * q;
+    x[q] = (r < nrows) ? Ps[r * VST + c] : (T)0;
+  }
+  if (c == 0) {
+    T sq = (T)0;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int r = w + 8 * q;
+      if (r >= lo(0) && r < hi(0)) sq += x[q] * x[q];
+    }
+    nrm[w] = sq;
+  }
+  for (int j = 0; j < IB; ++j) {
+    const int l0 = lo(j), h0 = hi(j);
+    // [A] dots of column j with every column; column j shuffled in from lane j
+    T xj[RPT];
+    T d = (T)0;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int r = w + 8 * q;
+      xj[q] = __shfl_sync(0xffffffffu, x[q], j);
+      if (r >= l0 && r < h0) d += xj[q] * x[q];
+      if (SINGLE && r == j) topbuf[c] = x[q];
+    }
+    part[w * IB + c] = (c != j) ? d : (T)0;
+    __syncthreads();
+    // [B] warp 0: reflector, w_c / G column, T column
+    if (w == 0) {
+      T ss = (T)0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) ss += nrm[q];
+      const T a0 = SINGLE ? topbuf[j] : Rs[j * VST + j];
+      T beta, tau, denom;
+      make_reflector<T>(a0, ss, &beta, &tau, &denom);
+      const T inv = (tau == (T)0) ? (T)0 : (T)1 / denom;
+      T dsum = (T)0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) dsum += part[q * IB + c];
+      const T topc = SINGLE ? topbuf[c] : Rs[j * VST + c];
+      if (c > j) wv[c] = topc + inv * dsum;
+      else if (c < j) wv[c] = sinv[c] * (inv * dsum + (SINGLE ? topc : (T)0));
+      __syncwarp();
+      T tcol = (T)0;
+      if (c < j) {
+        T acc = (T)0;
+        for (int b = c; b < j; ++b) acc += Ts[c * TST + b] * wv[b];
+        tcol = -tau * acc;
+      } else if (c == j) {
+        tcol = tau;
+      }
+      Ts[c * TST + j] = tcol;
+      if (c == 0) {
+        if (!SINGLE) Rs[j * VST + j] = beta;
+        tau_s[j] = tau;
+        sinv[j] = inv;
+        sc[0] = tau;
+        sc[1] = inv;
+        sc[2] = beta;
+      }
+    }
+    __syncthreads();
+    // [C] update of the columns right of j; the top row; partial norm of column j+1
+    {
+      const T tau = sc[0], inv = sc[1];
+      const T wc = (c > j) ? wv[c] : (T)0;
+      const T f = tau * inv * wc;
+      const bool upd = c > j && tau != (T)0;
+      T sq = (T)0;
+      const int l1 = lo(j + 1), h1 = hi(j + 1);
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int r = w + 8 * q;
+        if (upd && r >= l0 && r < h0) x[q] -= f * xj[q];
+        if (SINGLE && r == j) {
+          if (c == j) x[q] = sc[2];
+          else if (upd) x[q] -= tau * wc;
+        }
+        if (r >= l1 && r < h1) sq += x[q] * x[q];
+      }
+      if (!SINGLE && w == 0 && upd) Rs[j * VST + c] -= tau * wc;
+      if (j + 1 < IB && c == j + 1) nrm[w] = sq;
+    }
+    __syncthreads();
+  }
+  // scale the reflector columns and store the panel back
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int r = w + 8 * q;
+    if (r < nrows) {
+      T v = x[q];
+      if (r >= lo(c) && r < hi(c)) {
+        const T f = sinv[c];
+        v = (f == (T)0) ? (T)0 : v * f;
+      }
+      Ps[r * VST + c] = v;
+    }
+  }
+  __syncthreads();
+}
+
+// Dispatches FP32 panels to the register form (FP64 shuffles and register pressure make the
+// shared-memory form faster for doubles on this part).
+template <typename T, bool SINGLE>
+__device__ void panel_qr_any(T* Rs, T* Ps, int nrows, bool tri, int jb, T* tau_s, T* Ts,
+                             T* scratch) {
+  if constexpr (sizeof(T) == 8) {
+    panel_qr<T, SINGLE>(Rs, Ps, nrows, tri, jb, tau_s, Ts, scratch);
+    return;
+  }
+  if (nrows <= 64) panel_qr_reg<T, SINGLE, 8>(Rs, Ps, nrows, tri, jb, tau_s, Ts, scratch);
+  else if (nrows <= 128) panel_qr_reg<T, SINGLE, 16>(Rs, Ps, nrows, tri, jb, tau_s, Ts, scratch);
+  else if (nrows <= 256) panel_qr_reg<T, SINGLE, 32>(Rs, Ps, nrows, tri, jb, tau_s, Ts, scratch);
+  else panel_qr_reg<T, SINGLE, 64>(Rs, Ps, nrows, tri, jb, tau_s, Ts, scratch);
+}
+
 // ---------------------------------------------------------------- shared memory plans
 template <typename T, int SW>
 struct Plan {
@@ -405,7 +541,7 @@ __global__ void __launch_bounds__(NT) k_geqrt(Mat<T> F, int k, int nb, TileList 
     }
     cp_async_wait_all();
     __syncthreads();
-    panel_qr<T, true>(nullptr, Ps, nrows, false, jb, tau_s, Ts, Gs);
+    panel_qr_any<T, true>(nullptr, Ps, nrows, false, jb, tau_s, Ts, Gs);
     for (int idx = tid; idx < nrows * IB; idx += NT) {
       const int r = idx % nrows, j = idx / nrows;
       tile[(jb + r) + (int64_t)(jb + j) * F.ld] = Ps[r * VST + j];
@@ -516,7 +652,7 @@ __global__ void __launch_bounds__(NT) k_pair_qrt(Mat<T> F, int k, int nb, TileLi
     }
     cp_async_wait_all();
     __syncthreads();
-    panel_qr<T, false>(Rs, Ps, rl, tri, jb, tau_s, Ts, Gs);
+    panel_qr_any<T, false>(Rs, Ps, rl, tri, jb, tau_s, Ts, Gs);
     for (int idx = tid; idx < IB * IB; idx += NT) {
       const int a = idx % IB, j = idx / IB;
       if (a <= j) R[(jb + a) + (int64_t)(jb + j) * F.ld] = Rs[a * VST + j];
