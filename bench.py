@@ -270,6 +270,21 @@ def cpu_baseline_dict(res, args):
             }
 
 
+# ------------------------------------------------------------------ replicas
+def job_rate(ms_local, world, flops_per_rank, device):
+    """Whole-job rate of `world` replicas: every rank solves its own system; the job's time
+    is the slowest rank's (max over ranks) and the value counts all ranks' work.
+    Returns (ms_max, GFLOP/s)."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, flops_per_rank * world / (ms / 1e3) / 1e9
+
+
 # ------------------------------------------------------------------ other forms
 def batched_form(args, plain_ms_per_normflop=None):
     """4096 independent systems, N uniform in [64, 1024], iid N(0,1), 10% with a 1e-6-scaled
@@ -482,12 +497,8 @@ def main():
     prof = luqr.profile_read()
     luqr.profile(False, True)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     flops = (2.0 / 3.0) * float(N) ** 3
-    value = flops * world / (ms / 1e3) / 1e9
+    ms, value = job_rate(ms, world, flops, "cuda")
     eta_gpu = info["eta"]
     dec = info["dec"]
     n = len(dec)
