@@ -749,6 +749,11 @@ __global__ void __launch_bounds__(NT) k_pair_apply(Mat<const T> F, int k, int nb
 //   w = V_b^T x,  w2 = T_b^T w,  x -= V_b w2,
 // with the V and T blocks staged in shared memory and the next block's copy in flight.
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// 16-byte global -> shared copy (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16_any(void* sdst, const void* gsrc) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(gsrc) : "memory");
+}
 __device__ __forceinline__ void cpa_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 template <typename T>
@@ -758,12 +763,15 @@ __global__ void __launch_bounds__(NT) k_qr_apply_vec(Mat<const T> F, int k, int 
                                                      const uint8_t* __restrict__ dec) {
   if (dec[k] != DEC_QR) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Vb = reinterpret_cast<T*>(smem_raw);           // 2 x (nb x VST)
-  T* Tb = Vb + 2 * (size_t)nb * VST;                // 2 x (IB x TST)
-  T* xs = Tb + 2 * IB * TST;                        // nb: tile i
+  // V blocks column-major (column j of the block at j * nb), copied 16 bytes at a time;
+  // the reflector masks (unit diagonal, zeros above / below) are applied when reading.
+  T* Vb = reinterpret_cast<T*>(smem_raw);           // 2 x (IB x nb)
+  T* Tb = Vb + 2 * (size_t)IB * nb;                 // 2 x (IB x IB), column-major
+  T* xs = Tb + 2 * IB * IB;                         // nb: tile i
   T* xe = xs + nb;                                  // nb: eliminator tile (pairs)
   T* w = xe + nb;                                   // IB
   T* w2 = w + IB;                                   // IB
+  constexpr int VEC = 16 / sizeof(T);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
   const int i = tl.i0 + blockIdx.x * tl.istride;
   const int e = i - tl.eoff;
@@ -773,23 +781,28 @@ __global__ void __launch_bounds__(NT) k_qr_apply_vec(Mat<const T> F, int k, int 
   T* xg = x + (int64_t)e * nb;
   auto lo = [&](int jb) { return pair ? 0 : jb; };
   auto hi = [&](int jb) { return pair ? (tri ? jb + IB : nb) : nb; };
-  // V block of inner block jb: rows [lo, hi) x IB columns, masked to the reflector storage
-  // (single: unit diagonal, zeros above; TT: zeros below the diagonal of the V2 triangle)
   auto stage = [&](int jb, int buf) {
-    T* vs = Vb + (size_t)buf * nb * VST;
-    const int r0 = lo(jb), rows = hi(jb) - r0;
-    for (int idx = tid; idx < rows * IB; idx += NT) {
-      const int rr = idx % rows, j = idx / rows, r = r0 + rr;
-      if (!pair && r <= jb + j) vs[rr * VST + j] = (r == jb + j) ? (T)1 : (T)0;
-      else if (pair && tri && r > jb + j) vs[rr * VST + j] = (T)0;
-      else cp_async(&vs[rr * VST + j], &V[r + (int64_t)(jb + j) * F.ld]);
+    T* vs = Vb + (size_t)buf * IB * nb;
+    const int r0 = lo(jb), rows = hi(jb) - r0, cpc = rows / VEC;   // chunks per column
+    for (int idx = tid; idx < IB * cpc; idx += NT) {
+      const int j = idx / cpc, q = idx - j * cpc;
+      cp_async16_any(&vs[(size_t)j * nb + q * VEC], &V[r0 + q * VEC + (int64_t)(jb + j) * F.ld]);
     }
-    T* ts = Tb + buf * IB * TST;
-    for (int idx = tid; idx < IB * IB; idx += NT) {
-      const int a = idx % IB, j = idx / IB;
-      cp_async(&ts[a * TST + j], &Tslot[a + (size_t)(jb + j) * IB]);
-    }
+    T* ts = Tb + buf * IB * IB;
+    for (int idx = tid; idx < IB * IB / VEC; idx += NT)
+      cp_async16_any(&ts[idx * VEC], &Tslot[(size_t)jb * IB + idx * VEC]);
     cpa_commit();
+  };
+  // value of reflector j of block jb at row r (r in [lo, hi))
+  auto vval = [&](const T* vs, int jb, int r, int j) -> T {
+    const int d = jb + j;
+    if (!pair) {
+      if (r < d) return (T)0;
+      if (r == d) return (T)1;
+    } else if (tri && r > d) {
+      return (T)0;
+    }
+    return vs[(size_t)j * nb + (r - lo(jb))];
   };
   for (int r = tid; r < nb; r += NT) {
     xs[r] = xi[r];
@@ -801,28 +814,27 @@ __global__ void __launch_bounds__(NT) k_qr_apply_vec(Mat<const T> F, int k, int 
     else cpa_commit();
     cpa_wait1();
     __syncthreads();
-    const T* vs = Vb + (size_t)b * nb * VST;
-    const T* ts = Tb + b * IB * TST;
-    const int r0 = lo(jb), rows = hi(jb) - r0;
-    // w_j = [e_j-part] + V_b(:, j) . x
+    const T* vs = Vb + (size_t)b * IB * nb;
+    const T* ts = Tb + b * IB * IB;
+    const int r0 = lo(jb), r1 = hi(jb);
     for (int j = warp; j < IB; j += nw) {
-      T s = (T)0;
-      for (int rr = lane; rr < rows; rr += 32) s += vs[rr * VST + j] * xs[r0 + rr];
-      s = warp_sum<T>(s);
-      if (lane == 0) w[j] = pair ? s + xe[jb + j] : s;
+      T acc = (T)0;
+      for (int r = r0 + lane; r < r1; r += 32) acc += vval(vs, jb, r, j) * xs[r];
+      acc = warp_sum<T>(acc);
+      if (lane == 0) w[j] = pair ? acc + xe[jb + j] : acc;
     }
     __syncthreads();
     if (warp == 0) {
-      T s = (T)0;
-      for (int a = 0; a <= lane; ++a) s += ts[a * TST + lane] * w[a];
-      w2[lane] = s;
+      T acc = (T)0;
+      for (int a = 0; a <= lane; ++a) acc += ts[(size_t)lane * IB + a] * w[a];
+      w2[lane] = acc;
     }
     __syncthreads();
-    for (int rr = tid; rr < rows; rr += NT) {
-      T s = (T)0;
+    for (int r = r0 + tid; r < r1; r += NT) {
+      T acc = (T)0;
 #pragma unroll 8
-      for (int j = 0; j < IB; ++j) s += vs[rr * VST + j] * w2[j];
-      xs[r0 + rr] -= s;
+      for (int j = 0; j < IB; ++j) acc += vval(vs, jb, r, j) * w2[j];
+      xs[r] -= acc;
     }
     if (pair && tid < IB) xe[jb + tid] -= w2[tid];
     __syncthreads();
@@ -835,7 +847,7 @@ __global__ void __launch_bounds__(NT) k_qr_apply_vec(Mat<const T> F, int k, int 
 
 template <typename T>
 static size_t qr_apply_vec_smem(int nb) {
-  return sizeof(T) * (2 * (size_t)nb * VST + 2 * IB * TST + 2 * (size_t)nb + 2 * IB);
+  return sizeof(T) * (2 * (size_t)IB * nb + 2 * IB * IB + 2 * (size_t)nb + 2 * IB);
 }
 
 template <typename T>
