@@ -559,16 +559,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc2(TcArgs a) {
   }
 }
 
-// Same contraction with the B operand streamed by cp.async (16-byte copies, zero fill
-// past N) into a 4-slot raw ring that runs three K chunks ahead of the tensor cores, so
-// that every SM keeps ~48 KB of B loads in flight; the raw chunk is split into TF32 hi/lo
-// in shared memory right before its MMAs.  Requires a column-major B with ldb % 4 == 0,
-// a 16-byte aligned base, sB % 4 == 0 and K % 16 == 0 (checked by the launcher).
-constexpr int V_STAGES = 2;                              // MMA operand stages (A + B hi/lo)
-constexpr int V_RAW = 4;                                 // raw B ring slots
-constexpr int V_RAWB = P_BN * P_BK * 4;                  // 16 KB raw chunk
-constexpr int V_SMEM = V_STAGES * P_STAGE + V_RAW * V_RAWB + 256;
-
+// cp.async helpers of the streamed contraction below (16-byte copies, zero fill past the
+// source bytes given).
 __device__ __forceinline__ void cp_async16_zfill(void* sdst, const void* gsrc, uint32_t src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(sdst)), "l"(gsrc),
                "r"(src_bytes)
@@ -580,256 +572,10 @@ __device__ __forceinline__ void cp_async_wait_group() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Raw chunk layout: column c of the tile at c * 64 bytes (16 consecutive K values).
-__device__ __forceinline__ void v_issue_b(unsigned char* raw, const float* B, int64_t ldb,
-                                          int64_t N, int64_t n0, int k0) {
-  for (int idx = threadIdx.x; idx < P_BN * (P_BK / 4); idx += TC_THREADS) {
-    const int q = idx & 3, c = idx >> 2;
-    const int64_t gc = n0 + c;
-    const bool in = gc < N;
-    const float* src = in ? B + (k0 + 4 * q) + gc * ldb : B;
-    cp_async16_zfill(raw + idx * 16, src, in ? 16u : 0u);
-  }
-}
-
-__device__ __forceinline__ void v_convert_b(unsigned char* bst, const unsigned char* raw) {
-  unsigned char* bhi = bst;
-  unsigned char* blo = bst + P_BN * P_BK * 4;
-  for (int idx = threadIdx.x; idx < P_BN * (P_BK / 4); idx += TC_THREADS) {
-    const int q = idx & 3, c = idx >> 2;
-    const float4 x = *reinterpret_cast<const float4*>(raw + idx * 16);
-    uint4 h, l;
-    h.x = tf32_bits(x.x); l.x = tf32_bits(x.x - __uint_as_float(h.x));
-    h.y = tf32_bits(x.y); l.y = tf32_bits(x.y - __uint_as_float(h.y));
-    h.z = tf32_bits(x.z); l.z = tf32_bits(x.z - __uint_as_float(h.z));
-    h.w = tf32_bits(x.w); l.w = tf32_bits(x.w - __uint_as_float(h.w));
-    const uint32_t off = kmajor_off16(c, 4 * q);
-    *reinterpret_cast<uint4*>(bhi + off) = h;
-    *reinterpret_cast<uint4*>(blo + off) = l;
-  }
-}
-
-__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc2v(TcArgs a) {
-  if (a.dec != nullptr && a.dec[a.k_step] != a.want) return;
-  extern __shared__ __align__(1024) unsigned char smem_v[];
-  unsigned char* rawbase = smem_v + V_STAGES * P_STAGE;
-  uint64_t* full = reinterpret_cast<uint64_t*>(rawbase + V_RAW * V_RAWB);
-  uint64_t* empty = full + V_STAGES;
-  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(empty + V_STAGES);
-  int* s_fail = reinterpret_cast<int*>(taddr_slot + 1);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t m0 = (int64_t)blockIdx.y * 256, n0 = (int64_t)blockIdx.x * P_BN;
-  const int64_t t = blockIdx.z;
-  const int nK = a.K / P_BK;
-  const int mh = (a.M - m0) > 128 ? 2 : 1;
-  const unsigned char* Apk = a.Apk + t * a.sApk;
-  const float* B = a.B + t * a.sB;
-  float* C = a.C + t * a.sC;
-  const float* C1 = a.C1 ? a.C1 + t * a.sC1 : nullptr;
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(taddr_slot)),
-                 "r"(512));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  // tid 0 bookkeeping: last chunk whose A copy was issued / seen landed, last MMA commit
-  int a_issued = -1, a_landed = -1, last_commit = -1;
-  auto issue_a = [&](int c) {
-    const int st = c % V_STAGES;
-    unsigned char* sa = smem_v + st * P_STAGE;
-    mbar_expect_tx(&full[st], (uint32_t)mh * 2 * P_ABLK);
-    for (int h = 0; h < mh; ++h) {
-      const unsigned char* src = Apk + (((int64_t)(m0 / 128 + h) * nK + c) * 2 * P_ABLK);
-      bulk_g2s(sa + h * 2 * P_ABLK, src, 2 * P_ABLK, &full[st]);
-    }
-    a_issued = c;
-  };
-  if (tid == 0) {
-    *s_fail = 0;
-    for (int q = 0; q < V_STAGES; ++q) {
-      mbar_init(&full[q], 1);
-      mbar_init(&empty[q], 1);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *taddr_slot;
-  const uint32_t idesc = make_idesc_tf32(128, P_BN);
-  if (tid == 0)
-    for (int c = 0; c < V_STAGES && c < nK; ++c) issue_a(c);
-  for (int p = 0; p < V_RAW - 1; ++p) {
-    if (p < nK) v_issue_b(rawbase + p * V_RAWB, B, a.ldb, a.N, n0, p * P_BK);
-    cp_async_commit();
-  }
-  for (int c = 0; c < nK; ++c) {
-    const int st = c % V_STAGES;
-    unsigned char* sb = smem_v + st * P_STAGE + P_ASTAGE;
-    const int pf = c + V_RAW - 1;
-    if (pf < nK) v_issue_b(rawbase + (pf % V_RAW) * V_RAWB, B, a.ldb, a.N, n0, pf * P_BK);
-    cp_async_commit();
-    cp_async_wait_group<V_RAW - 1>();
-    __syncthreads();                 // raw chunk c complete in every thread; stage st free
-    if (*s_fail) break;
-    v_convert_b(sb, rawbase + (c % V_RAW) * V_RAWB);
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (tid == 0) {
-      if (!mbar_wait(&full[st], (uint32_t)(c / V_STAGES) & 1)) {
-        *s_fail = 1;
-      } else {
-        a_landed = c;
-        const uint32_t sbase = smem_u32(sb);
-        const unsigned char* sa = smem_v + st * P_STAGE;
-#pragma unroll
-        for (int s8 = 0; s8 < P_BK / 8; ++s8) {
-          const uint32_t koff = (uint32_t)s8 * 2 * TC_LBO;
-          const uint64_t bhi = make_desc_sbo(sbase + koff, P_SBO);
-          const uint64_t blo = make_desc_sbo(sbase + P_BN * P_BK * 4 + koff, P_SBO);
-          for (int h = 0; h < mh; ++h) {
-            const uint32_t abase = smem_u32(sa + h * 2 * P_ABLK);
-            const uint64_t ahi = make_desc_sbo(abase + koff, P_SBO);
-            const uint64_t alo = make_desc_sbo(abase + P_ABLK + koff, P_SBO);
-            const uint32_t d = tmem + (uint32_t)(h * P_BN);
-            const uint32_t acc0 = (c > 0 || s8 > 0) ? 1u : 0u;
-            tc_mma(d, alo, bhi, idesc, acc0);
-            tc_mma(d, ahi, blo, idesc, 1u);
-            tc_mma(d, ahi, bhi, idesc, 1u);
-          }
-        }
-        tc_commit(&empty[st]);
-        last_commit = c;
-        // the next chunk's A goes into the stage of chunk c+1-V_STAGES once its MMAs are done
-        const int nx = c + 1;
-        if (nx < nK && nx >= V_STAGES) {
-          const int pst = nx % V_STAGES;
-          if (!mbar_wait(&empty[pst], (uint32_t)(nx / V_STAGES - 1) & 1)) *s_fail = 1;
-          else issue_a(nx);
-        }
-      }
-    }
-  }
-  cp_async_wait_group<0>();
-  __syncthreads();
-  bool ok = *s_fail == 0;
-  if (tid == 0) {
-    // every issued MMA and every issued copy must be complete before TMEM and shared
-    // memory are released (bounded waits; a timeout leaves the error flag set)
-    if (last_commit >= 0 &&
-        !mbar_wait(&empty[last_commit % V_STAGES], (uint32_t)(last_commit / V_STAGES) & 1))
-      ok = false;
-    for (int q = a_landed + 1; q <= a_issued; ++q)
-      if (!mbar_wait(&full[q % V_STAGES], (uint32_t)(q / V_STAGES) & 1)) ok = false;
-    if (!ok) *s_fail = 1;
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const bool all_ok = *s_fail == 0;
-  const float* Csrc = (a.epi == TC_EPI_ADD_OUT) ? C1 : C;
-  const int64_t lds = (a.epi == TC_EPI_ADD_OUT) ? a.ldc1 : a.ldc;
-  const bool staged = a.epi != TC_EPI_OUT && (reinterpret_cast<uintptr_t>(Csrc) % 16) == 0 &&
-                      (lds % 4) == 0;
-  const int h = warp >> 2;
-  const int lane_base = (warp & 3) * 32;
-  const int64_t row = m0 + h * 128 + lane_base + lane;
-  if (all_ok && staged) {
-    fence_async_smem();
-    // The C (or C1) operand of the epilogue comes in through cp.async in four 64-column
-    // segments staged in the now idle pipeline buffers, so its loads are in flight together
-    // instead of one dependent round trip per register batch.
-    unsigned char* buf[4] = {rawbase, smem_v, smem_v + P_STAGE, rawbase};
-    auto load_seg = [&](int seg) {
-      unsigned char* dst = buf[seg];
-      if (n0 + seg * 64 < a.N) {
-        for (int idx = tid; idx < 64 * 64; idx += TC_THREADS) {
-          const int q = idx & 63, c = idx >> 6;
-          const int64_t gc = n0 + seg * 64 + c;
-          const int64_t gr = m0 + 4 * q;
-          const int64_t left = a.M - gr;
-          const uint32_t bytes =
-              (gc < a.N && left > 0) ? (uint32_t)(4 * (left < 4 ? left : 4)) : 0u;
-          const float* src = bytes ? Csrc + gr + gc * lds : Csrc;
-          cp_async16_zfill(dst + (size_t)(c * 256 + 4 * q) * 4, src, bytes);
-        }
-      }
-      cp_async_commit();
-    };
-    auto process_seg = [&](int seg) {
-      const float* sv = reinterpret_cast<const float*>(buf[seg]);
-      if (h >= mh) return;
-      for (int g = 0; g < 2; ++g) {
-        const int col0 = seg * 64 + 32 * g;
-        if (n0 + col0 >= a.N) break;
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(h * P_BN + col0), v);
-        if (row < a.M) {
-          const int lr = h * 128 + lane_base + lane;
-          const int64_t lim = a.N - (n0 + col0);
-          float* Cr = C + row + (n0 + col0) * a.ldc;
-#pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            if (q < lim) {
-              const float old = sv[(32 * g + q) * 256 + lr];
-              Cr[(int64_t)q * a.ldc] = (a.epi == TC_EPI_SUB) ? old - v[q] : v[q] + old;
-            }
-          }
-        }
-      }
-    };
-    load_seg(0);
-    load_seg(1);
-    load_seg(2);
-    cp_async_wait_group<2>();
-    __syncthreads();
-    process_seg(0);
-    __syncthreads();
-    load_seg(3);
-    cp_async_wait_group<2>();
-    __syncthreads();
-    process_seg(1);
-    cp_async_wait_group<1>();
-    __syncthreads();
-    process_seg(2);
-    cp_async_wait_group<0>();
-    __syncthreads();
-    process_seg(3);
-  } else if (all_ok) {
-    if (h < mh) {
-      for (int cc = 0; cc < P_BN; cc += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(h * P_BN + cc), v);
-        tc_epi32(a, C, C1, row, n0 + cc, v);
-      }
-    }
-  } else if (tid == 0 && a.status != nullptr) {
-    atomicCAS(&a.status[ST_CODE], 0, -6);
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
-  }
-}
-
-// ---------------------------------------------------------------- warp-specialised form
-// The same contraction with each job on its own warps, handing chunks over through
-// mbarriers instead of block-wide barriers:
-//   warp 0      streams raw B chunks (cp.async, completion signalled on raw_full)
-//   warp 1      one thread issues the tcgen05.mma of a chunk once its A and B are in
-//   warp 2      one thread brings the packed A chunks (cp.async.bulk) into the stages
-//   warps 4-7   split raw B into TF32 hi/lo in the stage, then run the epilogue
-// Every wait is bounded by a cycle budget; a timeout (or another warp's) sets the CTA's
-// fail flag, every role stops, outstanding copies and MMAs are waited for, TMEM is freed
-// and the status word gets LUQR_ERR_TIMEOUT.
-constexpr int W_RAW = 4;
-constexpr int W_STG = 2;
+// ---------------------------------------------------------------- bounded mbarrier waits
+// Waits for the phase of the given parity; false when the CTA's fail flag is set (unless
+// honour_fail is false) or the cycle budget runs out (then it sets the flag itself).
 constexpr long long W_WAIT_CYCLES = 1000000000LL;   // ~0.5 s
-constexpr int W_SMEM = W_STG * P_STAGE + W_RAW * V_RAWB + 256;
 
 __device__ __forceinline__ bool wwait(uint64_t* bar, uint32_t parity, volatile int* fail,
                                       bool honour_fail = true) {
@@ -855,256 +601,8 @@ __device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__global__ void __launch_bounds__(256, 1) k_gemm_tc3(TcArgs a) {
-  if (a.dec != nullptr && a.dec[a.k_step] != a.want) return;
-  if (a.status != nullptr && a.status[ST_CODE] != 0) return;   // an earlier launch failed
-  extern __shared__ __align__(1024) unsigned char smem_w[];
-  unsigned char* rawbase = smem_w + W_STG * P_STAGE;
-  uint64_t* raw_full = reinterpret_cast<uint64_t*>(rawbase + W_RAW * V_RAWB);
-  uint64_t* raw_empty = raw_full + W_RAW;
-  uint64_t* a_full = raw_empty + W_RAW;
-  uint64_t* b_full = a_full + W_STG;
-  uint64_t* st_empty = b_full + W_STG;
-  uint64_t* acc_full = st_empty + W_STG;
-  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(acc_full + 1);
-  volatile int* fail = reinterpret_cast<volatile int*>(taddr_slot + 1);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t m0 = (int64_t)blockIdx.y * 256, n0 = (int64_t)blockIdx.x * P_BN;
-  const int64_t t = blockIdx.z;
-  const int nK = a.K / P_BK;
-  const int mh = (a.M - m0) > 128 ? 2 : 1;
-  const unsigned char* Apk = a.Apk + t * a.sApk;
-  const float* B = a.B + t * a.sB;
-  float* C = a.C + t * a.sC;
-  const float* C1 = a.C1 ? a.C1 + t * a.sC1 : nullptr;
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(taddr_slot)),
-                 "r"(512));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    *fail = 0;
-    for (int q = 0; q < W_RAW; ++q) {
-      mbar_init(&raw_full[q], 32);   // one cp.async-tracking arrive per producer lane
-      mbar_init(&raw_empty[q], 4);   // one arrive per converter warp
-    }
-    for (int q = 0; q < W_STG; ++q) {
-      mbar_init(&a_full[q], 1);
-      mbar_init(&b_full[q], 4);
-      mbar_init(&st_empty[q], 1);
-    }
-    mbar_init(acc_full, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *taddr_slot;
-
-  if (warp == 0) {
-    // ---- raw B producer
-    for (int c = 0; c < nK; ++c) {
-      const int slot = c % W_RAW;
-      bool ok = c < W_RAW || wwait(&raw_empty[slot], (uint32_t)((c / W_RAW) - 1) & 1, fail);
-      if (!__all_sync(0xffffffffu, ok ? 1 : 0)) break;
-      unsigned char* raw = rawbase + slot * V_RAWB;
-      const int k0 = c * P_BK;
-      for (int idx = lane; idx < P_BN * (P_BK / 4); idx += 32) {
-        const int q = idx & 3, col = idx >> 2;
-        const int64_t gc = n0 + col;
-        const bool in = gc < a.N;
-        const float* src = in ? B + (k0 + 4 * q) + gc * a.ldb : B;
-        cp_async16_zfill(raw + idx * 16, src, in ? 16u : 0u);
-      }
-      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
-                       smem_u32(&raw_full[slot]))
-                   : "memory");
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-  } else if (warp == 1) {
-    // ---- MMA issuer
-    if (lane == 0) {
-      const uint32_t idesc = make_idesc_tf32(128, P_BN);
-      int last = -1;
-      for (int c = 0; c < nK; ++c) {
-        const int st = c % W_STG;
-        const uint32_t ph = (uint32_t)(c / W_STG) & 1;
-        if (!wwait(&a_full[st], ph, fail) || !wwait(&b_full[st], ph, fail)) break;
-        tc_fence_after();
-        unsigned char* sa = smem_w + st * P_STAGE;
-        const uint32_t sbase = smem_u32(sa + P_ASTAGE);
-#pragma unroll
-        for (int s8 = 0; s8 < P_BK / 8; ++s8) {
-          const uint32_t koff = (uint32_t)s8 * 2 * TC_LBO;
-          const uint64_t bhi = make_desc_sbo(sbase + koff, P_SBO);
-          const uint64_t blo = make_desc_sbo(sbase + P_BN * P_BK * 4 + koff, P_SBO);
-          for (int h = 0; h < mh; ++h) {
-            const uint32_t abase = smem_u32(sa + h * 2 * P_ABLK);
-            const uint64_t ahi = make_desc_sbo(abase + koff, P_SBO);
-            const uint64_t alo = make_desc_sbo(abase + P_ABLK + koff, P_SBO);
-            const uint32_t d = tmem + (uint32_t)(h * P_BN);
-            const uint32_t acc0 = (c > 0 || s8 > 0) ? 1u : 0u;
-            tc_mma(d, alo, bhi, idesc, acc0);
-            tc_mma(d, ahi, blo, idesc, 1u);
-            tc_mma(d, ahi, bhi, idesc, 1u);
-          }
-        }
-        tc_commit(&st_empty[st]);
-        last = c;
-      }
-      if (last == nK - 1) tc_commit(acc_full);
-      // no MMA may be in flight when TMEM and shared memory are released
-      if (last >= 0) wwait(&st_empty[last % W_STG], (uint32_t)(last / W_STG) & 1, fail, false);
-    }
-  } else if (warp == 2) {
-    // ---- packed A producer
-    if (lane == 0) {
-      int issued = -1;
-      for (int c = 0; c < nK; ++c) {
-        const int st = c % W_STG;
-        if (c >= W_STG && !wwait(&st_empty[st], (uint32_t)((c / W_STG) - 1) & 1, fail)) break;
-        unsigned char* sa = smem_w + st * P_STAGE;
-        mbar_expect_tx(&a_full[st], (uint32_t)mh * 2 * P_ABLK);
-        for (int h = 0; h < mh; ++h) {
-          const unsigned char* src = Apk + (((int64_t)(m0 / 128 + h) * nK + c) * 2 * P_ABLK);
-          bulk_g2s(sa + h * 2 * P_ABLK, src, 2 * P_ABLK, &a_full[st]);
-        }
-        issued = c;
-      }
-      // the copies of the last chunk of each stage must land before shared memory is freed
-      for (int q = issued; q >= 0 && q > issued - W_STG; --q)
-        wwait(&a_full[q % W_STG], (uint32_t)(q / W_STG) & 1, fail, false);
-    }
-  } else if (warp >= 4) {
-    // ---- converters, then the epilogue (warps 4..7 own TMEM lanes 32*(warp-4)..)
-    const int ct = tid - 128;
-    for (int c = 0; c < nK; ++c) {
-      const int slot = c % W_RAW, st = c % W_STG;
-      bool ok = wwait(&raw_full[slot], (uint32_t)(c / W_RAW) & 1, fail);
-      if (ok && c >= W_STG) ok = wwait(&st_empty[st], (uint32_t)((c / W_STG) - 1) & 1, fail);
-      if (!__all_sync(0xffffffffu, ok ? 1 : 0)) break;
-      const unsigned char* raw = rawbase + slot * V_RAWB;
-      unsigned char* bhi = smem_w + st * P_STAGE + P_ASTAGE;
-      unsigned char* blo = bhi + P_BN * P_BK * 4;
-      for (int idx = ct; idx < P_BN * (P_BK / 4); idx += 128) {
-        const int q = idx & 3, col = idx >> 2;
-        const float4 x = *reinterpret_cast<const float4*>(raw + idx * 16);
-        uint4 hh, ll;
-        hh.x = tf32_bits(x.x); ll.x = tf32_bits(x.x - __uint_as_float(hh.x));
-        hh.y = tf32_bits(x.y); ll.y = tf32_bits(x.y - __uint_as_float(hh.y));
-        hh.z = tf32_bits(x.z); ll.z = tf32_bits(x.z - __uint_as_float(hh.z));
-        hh.w = tf32_bits(x.w); ll.w = tf32_bits(x.w - __uint_as_float(hh.w));
-        const uint32_t off = kmajor_off16(col, 4 * q);
-        *reinterpret_cast<uint4*>(bhi + off) = hh;
-        *reinterpret_cast<uint4*>(blo + off) = ll;
-      }
-      fence_async_smem();
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive1(&raw_empty[slot]);
-        mbar_arrive1(&b_full[st]);
-      }
-    }
-    // ---- epilogue
-    bool ok = wwait(acc_full, 0, fail);
-    ok = __all_sync(0xffffffffu, ok ? 1 : 0);
-    // every warp of the group must agree before the group's named barriers
-    __shared__ int s_epi_ok;
-    if (ct == 0) s_epi_ok = 1;
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-    if (!ok && lane == 0) s_epi_ok = 0;
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-    if (s_epi_ok) {
-      tc_fence_after();
-      const int e = warp - 4;
-      const float* Csrc = (a.epi == TC_EPI_ADD_OUT) ? C1 : C;
-      const int64_t lds = (a.epi == TC_EPI_ADD_OUT) ? a.ldc1 : a.ldc;
-      const bool staged = a.epi != TC_EPI_OUT &&
-                          (reinterpret_cast<uintptr_t>(Csrc) % 16) == 0 && (lds % 4) == 0;
-      if (staged) {
-        // C (or C1) in four 64-column segments through the idle pipeline buffers
-        unsigned char* buf[4] = {rawbase, smem_w, smem_w + P_STAGE, rawbase};
-        auto load_seg = [&](int seg) {
-          unsigned char* dst = buf[seg];
-          if (n0 + seg * 64 < a.N) {
-            for (int idx = ct; idx < 64 * 64; idx += 128) {
-              const int q = idx & 63, cc = idx >> 6;
-              const int64_t gc = n0 + seg * 64 + cc;
-              const int64_t gr = m0 + 4 * q;
-              const int64_t left = a.M - gr;
-              const uint32_t bytes =
-                  (gc < a.N && left > 0) ? (uint32_t)(4 * (left < 4 ? left : 4)) : 0u;
-              const float* src = bytes ? Csrc + gr + gc * lds : Csrc;
-              cp_async16_zfill(dst + (size_t)(cc * 256 + 4 * q) * 4, src, bytes);
-            }
-          }
-          cp_async_commit();
-        };
-        auto process_seg = [&](int seg) {
-          const float* sv = reinterpret_cast<const float*>(buf[seg]);
-          for (int h = 0; h < mh; ++h) {
-            const int64_t row = m0 + h * 128 + e * 32 + lane;
-            const int lr = h * 128 + e * 32 + lane;
-            for (int g = 0; g < 2; ++g) {
-              const int col0 = seg * 64 + 32 * g;
-              if (n0 + col0 >= a.N) break;
-              float v[32];
-              tmem_ld32(tmem + ((uint32_t)(e * 32) << 16) + (uint32_t)(h * P_BN + col0), v);
-              if (row < a.M) {
-                const int64_t lim = a.N - (n0 + col0);
-                float* Cr = C + row + (n0 + col0) * a.ldc;
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                  if (q < lim) {
-                    const float old = sv[(32 * g + q) * 256 + lr];
-                    Cr[(int64_t)q * a.ldc] = (a.epi == TC_EPI_SUB) ? old - v[q] : v[q] + old;
-                  }
-                }
-              }
-            }
-          }
-        };
-        load_seg(0);
-        load_seg(1);
-        load_seg(2);
-        cp_async_wait_group<2>();
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        process_seg(0);
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        load_seg(3);
-        cp_async_wait_group<2>();
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        process_seg(1);
-        cp_async_wait_group<1>();
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        process_seg(2);
-        cp_async_wait_group<0>();
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        process_seg(3);
-      } else {
-        for (int h = 0; h < mh; ++h) {
-          const int64_t row = m0 + h * 128 + e * 32 + lane;
-          for (int cc = 0; cc < P_BN; cc += 32) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(e * 32) << 16) + (uint32_t)(h * P_BN + cc), v);
-            tc_epi32(a, C, C1, row, n0 + cc, v);
-          }
-        }
-      }
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (tid == 0 && *fail && a.status != nullptr) atomicCAS(&a.status[ST_CODE], 0, -6);
-  if (warp == 0) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
-  }
-}
-
 // ---------------------------------------------------------------- persistent form
-// Persistent version of the warp-specialised contraction: one CTA per SM walks the
+// Persistent, warp-specialised form of the contraction: one CTA per SM walks the
 // 256 x 128 output tiles of the launch, and two TMEM accumulators let the epilogue of tile
 // i (warps 8-11) overlap the main loop of tile i+1.  Without the overlap every SM alternates
 // between a tensor-bound main loop and an HBM-bound epilogue, and the two phases of all SMs
