@@ -490,7 +490,7 @@ __device__ void replay_solve(const BatchArgs& a, const Slot<T>& sl, const uint8_
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BT, 1) k_batched(BatchArgs a) {
+__global__ void __launch_bounds__(BT, sizeof(T) == 4 ? 2 : 1) k_batched(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char bsm[];
   T* S0 = reinterpret_cast<T*>(bsm);
   T* S1 = S0 + TILE;
@@ -901,7 +901,17 @@ extern "C" int luqr_batched_create(const double* const* dA, double* const* db, c
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  p->slots = std::min(count, std::max(1, sms));
+  // as many persistent CTAs as fit at once (two per SM for FP32 tiles)
+  int per_sm = 1;
+  if (p->fp32) {
+    ensure_dyn_smem<k_batched<float>>(batched_smem<float>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched<float>, BT, batched_smem<float>());
+  } else {
+    ensure_dyn_smem<k_batched<double>>(batched_smem<double>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched<double>, BT, batched_smem<double>());
+  }
+  cudaGetLastError();
+  p->slots = std::min(count, std::max(1, sms) * std::max(1, per_sm));
   // metadata block: A ptrs, b ptrs, N, nb, order, dec, iters, eta, status, counter
   size_t off = 0;
   const size_t oA = off; off = al(off + sizeof(void*) * count);
