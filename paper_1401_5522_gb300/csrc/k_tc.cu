@@ -927,7 +927,18 @@ __global__ void __launch_bounds__(256) k_tfull(const float* __restrict__ G, int6
         float y[IB];
 #pragma unroll
         for (int j = 0; j < IB; ++j) y[j] = 0.f;
-        for (int q = r; q < jb; ++q) {
+        // row r of Tf (written by this thread in earlier blocks): 8 loads in flight
+        int q = r;
+        for (; q + 8 <= jb; q += 8) {
+          float tq[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) tq[u] = tf[r + (int64_t)(q + u) * nb];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int j = 0; j < IB; ++j) y[j] += tq[u] * X[q + u][j];
+        }
+        for (; q < jb; ++q) {
           const float tq = tf[r + (int64_t)q * nb];
 #pragma unroll
           for (int j = 0; j < IB; ++j) y[j] += tq * X[q][j];
