@@ -174,47 +174,48 @@ __device__ __forceinline__ void tc_put(unsigned char* hi, unsigned char* lo, uin
 }
 
 // Stages chunk [k0, k0 + 32) of the logical operands A (M x K) and B (K x N) into one
-// stage of shared memory as hi/lo TF32 copies (zero outside the matrices).
+// stage of shared memory as hi/lo TF32 copies (zero outside the matrices).  All 32 global
+// loads of a thread are issued before its shared-memory stores.
 __device__ __forceinline__ void tc_stage(unsigned char* st, const TcArgs& a, const float* A,
                                          const float* B, int64_t m0, int64_t n0, int k0) {
+  constexpr int PER = TC_BM * TC_BK / TC_THREADS;
+  static_assert(TC_BN == TC_BM && PER * TC_THREADS == TC_BM * TC_BK, "staging map");
   unsigned char* ahi = st;
   unsigned char* alo = st + TC_CHUNK_BYTES;
   unsigned char* bhi = st + 2 * TC_CHUNK_BYTES;
   unsigned char* blo = st + 3 * TC_CHUNK_BYTES;
-  if (!a.a_trans) {   // A(m, k) = P[m][k]: consecutive threads walk m (contiguous)
-    for (int idx = threadIdx.x; idx < TC_BM * TC_BK; idx += TC_THREADS) {
-      const int r = idx % TC_BM, k = idx / TC_BM;
-      const int64_t gr = m0 + r;
-      const int gk = k0 + k;
-      const float x = (gr < a.M && gk < a.K) ? tc_fetch(A, a.lda, gr, gk, a.a_mask) : 0.f;
-      tc_put(ahi, alo, kmajor_off(r, k), x);
-    }
-  } else {            // A(m, k) = P[k][m]: consecutive threads walk k (contiguous)
-    for (int idx = threadIdx.x; idx < TC_BM * TC_BK; idx += TC_THREADS) {
-      const int k = idx % TC_BK, r = idx / TC_BK;
-      const int64_t gr = m0 + r;
-      const int gk = k0 + k;
-      const float x = (gr < a.M && gk < a.K) ? tc_fetch(A, a.lda, gk, gr, a.a_mask) : 0.f;
-      tc_put(ahi, alo, kmajor_off(r, k), x);
-    }
+  float xa[PER], xb[PER];
+  uint32_t oa[PER], ob[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int idx = threadIdx.x + u * TC_THREADS;
+    int r, k;
+    if (!a.a_trans) { r = idx % TC_BM; k = idx / TC_BM; }   // consecutive threads walk m
+    else { k = idx % TC_BK; r = idx / TC_BK; }             // consecutive threads walk k
+    const int64_t gr = m0 + r;
+    const int gk = k0 + k;
+    xa[u] = (gr < a.M && gk < a.K) ? (a.a_trans ? tc_fetch(A, a.lda, gk, gr, a.a_mask)
+                                                : tc_fetch(A, a.lda, gr, gk, a.a_mask))
+                                   : 0.f;
+    oa[u] = kmajor_off(r, k);
   }
-  if (!a.b_trans) {   // B(k, n) = P[k][n]: consecutive threads walk k
-    for (int idx = threadIdx.x; idx < TC_BN * TC_BK; idx += TC_THREADS) {
-      const int k = idx % TC_BK, c = idx / TC_BK;
-      const int64_t gc = n0 + c;
-      const int gk = k0 + k;
-      const float x = (gc < a.N && gk < a.K) ? tc_fetch(B, a.ldb, gk, gc, a.b_mask) : 0.f;
-      tc_put(bhi, blo, kmajor_off(c, k), x);
-    }
-  } else {            // B(k, n) = P[n][k]: consecutive threads walk n
-    for (int idx = threadIdx.x; idx < TC_BN * TC_BK; idx += TC_THREADS) {
-      const int c = idx % TC_BN, k = idx / TC_BN;
-      const int64_t gc = n0 + c;
-      const int gk = k0 + k;
-      const float x = (gc < a.N && gk < a.K) ? tc_fetch(B, a.ldb, gc, gk, a.b_mask) : 0.f;
-      tc_put(bhi, blo, kmajor_off(c, k), x);
-    }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int idx = threadIdx.x + u * TC_THREADS;
+    int c, k;
+    if (!a.b_trans) { k = idx % TC_BK; c = idx / TC_BK; }   // consecutive threads walk k
+    else { c = idx % TC_BN; k = idx / TC_BN; }             // consecutive threads walk n
+    const int64_t gc = n0 + c;
+    const int gk = k0 + k;
+    xb[u] = (gc < a.N && gk < a.K) ? (a.b_trans ? tc_fetch(B, a.ldb, gc, gk, a.b_mask)
+                                                : tc_fetch(B, a.ldb, gk, gc, a.b_mask))
+                                   : 0.f;
+    ob[u] = kmajor_off(c, k);
   }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) tc_put(ahi, alo, oa[u], xa[u]);
+#pragma unroll
+  for (int u = 0; u < PER; ++u) tc_put(bhi, blo, ob[u], xb[u]);
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs a) {
