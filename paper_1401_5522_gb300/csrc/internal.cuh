@@ -216,6 +216,10 @@ void launch_multidot(const double* V, int64_t ldv, int64_t N, int cnt, const dou
 void launch_multiaxpy(const double* V, int64_t ldv, int64_t N, int cnt, const double* coef,
                       double* w, double alpha, cudaStream_t s);
 
+// X = L^-1 P of an LU step's committed factor (k_lu.cu, FP32).
+void launch_lu_inverse(const float* W, int64_t ldw, int k, int nb, const int* piv_k, float* X,
+                       const uint8_t* dec, cudaStream_t s);
+
 // One right-hand side of the second pass (k_qr.cu).
 template <typename T>
 bool qr_apply_vec_fits(int nb);   // its double-buffered V blocks fit in shared memory

@@ -87,6 +87,70 @@ void launch_swptrsm(Mat<const T> LU, int nb, const int* piv_k, Mat<T> C, int64_t
   }
 }
 
+// ---------------------------------------------------------------- L^-1 P (FP32)
+// X = L^-1 P (nb x nb, column-major, ld nb) of the committed unit-lower factor of step k,
+// so that the Apply of Alg. 2 on a wide tile row becomes one tensor-core product
+// A_kj <- X A_kj.  One warp per column of X (two per CTA); the factor's columns come into
+// shared memory 8 at a time through cp.async and are shared by the CTA's warps.
+constexpr int LI_CH = 8;
+
+__global__ void __launch_bounds__(64) k_lu_inverse(const float* __restrict__ W, int64_t ldw, int k,
+                                                   int nb, const int* __restrict__ piv,
+                                                   float* __restrict__ X,
+                                                   const uint8_t* __restrict__ dec) {
+  if (dec[k] != DEC_LU) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* ys_all = reinterpret_cast<float*>(smem_raw);          // 2 x nb
+  float* colbuf = ys_all + 2 * (size_t)nb;                     // 2 x LI_CH x nb
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c = blockIdx.x * 2 + warp;
+  const float* L = W + (int64_t)k * nb + (int64_t)k * nb * ldw;
+  float* ys = ys_all + (size_t)warp * nb;
+  int pos = c;   // row of the single 1 of column c of P
+  for (int r = 0; r < nb; ++r) {
+    const int p = piv[r];
+    if (pos == r) pos = p;
+    else if (pos == p) pos = r;
+  }
+  for (int row = lane; row < nb; row += 32) ys[row] = (row == pos) ? 1.f : 0.f;
+  auto fetch = [&](int first, int slot) {
+    float* dst = colbuf + (size_t)slot * LI_CH * nb;
+    for (int idx = tid; idx < LI_CH * nb; idx += 64) {
+      const int cc = idx / nb, i = idx - cc * nb, col = first + cc;
+      if (col < nb) cp_async(&dst[idx], &L[i + (int64_t)col * ldw]);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  const int nch = nb / LI_CH;
+  fetch(0, 0);
+  for (int g = 0; g < nch; ++g) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    fetch((g + 1) * LI_CH, (g + 1) & 1);
+    const float* base = colbuf + (size_t)(g & 1) * LI_CH * nb;
+    for (int cc = 0; cc < LI_CH; ++cc) {
+      const int r = g * LI_CH + cc;
+      if (r >= nb - 1) break;
+      __syncwarp();
+      const float yr = ys[r];
+      if (r < pos || yr == 0.f) continue;
+      const float* col = base + (size_t)cc * nb;
+      for (int row = r + 1 + lane; row < nb; row += 32) ys[row] -= col[row] * yr;
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncwarp();
+  for (int row = lane; row < nb; row += 32) X[row + (int64_t)c * nb] = ys[row];
+}
+
+void launch_lu_inverse(const float* W, int64_t ldw, int k, int nb, const int* piv_k, float* X,
+                       const uint8_t* dec, cudaStream_t s) {
+  const size_t smem = sizeof(float) * (2 * (size_t)nb + 2 * LI_CH * (size_t)nb);
+  ensure_dyn_smem<k_lu_inverse>(smem);
+  ProfScope ps_("k_lu_inverse", s);
+  k_lu_inverse<<<nb / 2, 64, smem, s>>>(W, ldw, k, nb, piv_k, X, dec);
+}
+
 // ---------------------------------------------------------------- TRSM
 // Block = TRB rows of the sub-diagonal panel, all nb columns in shared memory (row
 // stride nb+1), U row c staged per column step.

@@ -56,6 +56,8 @@ struct luqr_handle {
   float* Vt[2] = {nullptr, nullptr};
   unsigned char* Apk[2] = {nullptr, nullptr};   // packed QR operands (V^T, V T^T, T^T) per tile
   unsigned char* Lpk[2] = {nullptr, nullptr};   // packed LU panel (rows below the diagonal)
+  float* Linv[2] = {nullptr, nullptr};          // X = L^-1 P of an LU step (nb x nb)
+  unsigned char* Xpk[2] = {nullptr, nullptr};   // X packed for the tensor-core Apply
   size_t pk_tile = 0;                           // bytes of one packed nb x nb operand
   // decision predictor and speculation (spec_stream factors predicted-QR panels on the
   // shadow copy while the criterion runs on the panel stream)
@@ -291,14 +293,31 @@ void enqueue_qr_extras(luqr_handle* h, int k, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- LU step on a target
+// tc_apply: the Apply (L^-1 P on tile row k) as an in-place tensor-core product with the
+// step's packed X (prepared on the extra stream; only the bulk update uses it).  In place
+// is safe because one CTA tile spans all nb rows (nb <= 256): its B columns are read in
+// full before its epilogue writes them.
 template <typename T>
 void enqueue_lu_apply(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, cudaStream_t s,
-                      bool tc = false) {
+                      bool tc = false, bool tc_apply = false) {
   const int nb = h->nb;
   const int64_t r0 = (int64_t)k * nb, r1 = r0 + nb, ld = h->Npad;
   T* W = wsT<T>(h);
   Mat<const T> LU{W + r0 + r0 * ld, ld};
-  launch_swptrsm<T>(LU, nb, h->piv_all + (size_t)k * nb, C, r0, c0, c1, h->dec, k, s);
+  bool applied = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (tc_apply && h->Xpk[k & 1] != nullptr && c1 - c0 >= 64) {
+      TcArgs a{};
+      a.dec = h->dec; a.k_step = k; a.want = DEC_LU; a.status = h->status;
+      a.M = nb; a.N = c1 - c0; a.K = nb;
+      a.Apk = h->Xpk[k & 1];
+      a.B = C.p + r0 + c0 * C.ld; a.ldb = C.ld;
+      a.C = C.p + r0 + c0 * C.ld; a.ldc = C.ld; a.epi = TC_EPI_OUT;
+      launch_tc2(a, 1, "k_tc_lu_apply", s);
+      applied = true;
+    }
+  }
+  if (!applied) launch_swptrsm<T>(LU, nb, h->piv_all + (size_t)k * nb, C, r0, c0, c1, h->dec, k, s);
   Mat<const T> Ablk{W + r1 + r0 * ld, ld};
   Mat<const T> Brow{C.p + r0 + c0 * C.ld, C.ld};
   Mat<T> Cblk{C.p + r1 + c0 * C.ld, C.ld};
@@ -394,16 +413,25 @@ void enqueue_factor(luqr_handle* h) {
     cudaEventRecord(h->ev_fact[k], s);
     // ---- tensor-core operands of the QR step (Gram, full T, V T^T, packing) off the
     //      panel's critical path; only the bulk update consumes them
-    if (tcqr) {
+    const bool lu_x = std::is_same<T, float>::value && h->Xpk[k & 1] != nullptr;
+    if (tcqr || lu_x) {
       cudaStreamWaitEvent(sx, h->ev_fact[k], 0);
-      if constexpr (std::is_same<T, float>::value) enqueue_qr_extras(h, k, sx);
+      if constexpr (std::is_same<T, float>::value) {
+        if (tcqr) enqueue_qr_extras(h, k, sx);
+        if (lu_x) {
+          launch_lu_inverse(reinterpret_cast<const float*>(W), ld, k, nb,
+                            h->piv_all + (size_t)k * nb, h->Linv[k & 1], h->dec, sx);
+          launch_tc_pack(h->Linv[k & 1], nb, 0, 0, TC_MASK_NONE, nb, nb, h->Xpk[k & 1], 0, 1,
+                         h->dec, k, DEC_LU, sx);
+        }
+      }
       cudaEventRecord(h->ev_extra[k], sx);
     }
     // ---- bulk update of columns >= k+2 (and b) on the update stream
     if (la_end < h->Wc) {
       cudaStreamWaitEvent(su, h->ev_fact[k], 0);
-      if (tcqr) cudaStreamWaitEvent(su, h->ev_extra[k], 0);
-      enqueue_lu_apply<T>(h, k, F, la_end, h->Wc, su, true);
+      if (tcqr || lu_x) cudaStreamWaitEvent(su, h->ev_extra[k], 0);
+      enqueue_lu_apply<T>(h, k, F, la_end, h->Wc, su, true, true);
       enqueue_qr<T>(h, k, F, la_end, h->Wc, false, true, su, true);
     }
     cudaEventRecord(h->ev_rest[k], su);
@@ -491,6 +519,7 @@ void free_handle(luqr_handle* h) {
                   h->rhs,    h->status,   h->forced,   h->rhs_ws, h->ref,    h->Wbuf,
                   h->Gbuf,   h->Tfull[0], h->Tfull[1], h->Vt[0], h->Vt[1], h->gm,
                   h->Apk[0], h->Apk[1],   h->Lpk[0],   h->Lpk[1], h->feat, h->spec,
+                  h->Linv[0], h->Linv[1], h->Xpk[0],   h->Xpk[1],
                   h->qrfac,  h->cmt,      h->shadow};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -699,7 +728,13 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   h->use_tc_qr = (h->prec == LUQR_PREC_FP32) && (o.fp32_kernels != 1);
   h->pk_tile = tc_packed_bytes(nb, nb);
   if (h->use_tc) {
-    for (int q = 0; q < 2; ++q) A((void**)&h->Lpk[q], tc_packed_bytes(h->Npad, nb));
+    for (int q = 0; q < 2; ++q) {
+      A((void**)&h->Lpk[q], tc_packed_bytes(h->Npad, nb));
+      if (nb <= 256) {
+        A((void**)&h->Linv[q], sizeof(float) * (size_t)nb * nb);
+        A((void**)&h->Xpk[q], tc_packed_bytes(nb, nb));
+      }
+    }
   }
   if (h->use_tc_qr) {
     for (int q = 0; q < 2; ++q) A((void**)&h->Apk[q], (size_t)n * 2 * 3 * h->pk_tile);
