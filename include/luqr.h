@@ -201,6 +201,19 @@ void luqr_destroy(luqr_handle_t h);
 int luqr_profile(int enable, int reset);
 
 /*
+ * luqr_profile_trace - the launch timeline recorded while luqr_profile(2, .) (trace mode)
+ * was on: for up to cap launches, in the order they were enqueued, the kernel's name
+ * (static string owned by the library), start and end in milliseconds since trace mode
+ * was switched on (device clock, CUDA events), and the stream the launch ran on (an
+ * opaque id).  Waits for the recorded events.  Any array may be NULL.  Returns the number
+ * of recorded launches (which may exceed cap; at most 4M are kept).  Enabling with
+ * enable == 2 records a base event on the legacy default stream.  Returns LUQR_ERR_INVALID
+ * from luqr_profile for enable outside 0..2.
+ */
+int luqr_profile_trace(const char** names, float* t0_ms, float* t1_ms, uint64_t* stream,
+                       int64_t cap);
+
+/*
  * luqr_profile_read - waits for the recorded events, then writes up to cap entries
  * (host arrays): kernel names (static strings owned by the library), launch counts
  * and total device milliseconds.  Any array may be NULL.  Returns the entry count.

@@ -175,6 +175,9 @@ struct TcArgs {
   const uint8_t* dec; int k_step; uint8_t want;
   int* status;
   const unsigned char* Apk; int64_t sApk;   // packed A (launch_tc2)
+  // packed A known to be triangular (exact zeros): 1 lower (A[m][q] = 0 for q > m), 2 upper
+  // (A[m][q] = 0 for q < m); the persistent kernel skips the products of zero blocks
+  int a_tri;
 };
 void launch_tc(const TcArgs& a, int batch, const char* name, cudaStream_t s);
 // Packed-A form: pack A once (launch_tc_pack), then launch_tc2 with a.Apk/a.sApk set.

@@ -617,6 +617,7 @@ __device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
 #ifndef LUQR_T4_TPC
 #define LUQR_T4_TPC 8
 #endif
+constexpr int T4_THREADS = 384;
 constexpr int T4_BN = 128;
 constexpr int T4_STG = 3;
 constexpr int T4_RAW = 4;
@@ -626,7 +627,7 @@ constexpr int T4_STAGE = T4_ABYTES + T4_BBYTES;             // 48 KB
 constexpr int T4_RAWB = T4_BN * P_BK * 4;                   // 8 KB
 constexpr int T4_SMEM = T4_STG * T4_STAGE + T4_RAW * T4_RAWB + 512;
 
-__global__ void __launch_bounds__(384, 1) k_gemm_tc4(TcArgs a, int mtiles, int ntiles,
+__global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles, int ntiles,
                                                      int total) {
   if (a.dec != nullptr && a.dec[a.k_step] != a.want) return;
   if (a.status != nullptr && a.status[ST_CODE] != 0) return;
@@ -720,6 +721,7 @@ __global__ void __launch_bounds__(384, 1) k_gemm_tc4(TcArgs a, int mtiles, int n
         const int buf = it & 1;
         if (it >= 2 && !wwait(&acc_empty[buf], (uint32_t)((it / 2) - 1) & 1, fail)) break;
         tc_fence_after();
+        bool started[2] = {false, false};
         for (int c = 0; c < nK; ++c) {
           const int g = it * nK + c, st = g % T4_STG;
           const uint32_t ph = (uint32_t)(g / T4_STG) & 1;
@@ -733,11 +735,15 @@ __global__ void __launch_bounds__(384, 1) k_gemm_tc4(TcArgs a, int mtiles, int n
             const uint64_t bhi = make_desc_sbo(sbase + koff, P_SBO);
             const uint64_t blo = make_desc_sbo(sbase + T4_BN * P_BK * 4 + koff, P_SBO);
             for (int h = 0; h < mh; ++h) {
+              // rows [r0, r0 + 128) of a triangular A meet only part of K
+              const int64_t r0 = m0 + h * 128, q0 = (int64_t)c * P_BK + s8 * 8;
+              if ((a.a_tri == 1 && q0 >= r0 + 128) || (a.a_tri == 2 && q0 + 8 <= r0)) continue;
               const uint32_t abase = smem_u32(sa + h * 2 * P_ABLK);
               const uint64_t ahi = make_desc_sbo(abase + koff, P_SBO);
               const uint64_t alo = make_desc_sbo(abase + P_ABLK + koff, P_SBO);
               const uint32_t d = tmem + (uint32_t)(buf * 256 + h * T4_BN);
-              const uint32_t acc0 = (c > 0 || s8 > 0) ? 1u : 0u;
+              const uint32_t acc0 = started[h] ? 1u : 0u;
+              started[h] = true;
               tc_mma(d, alo, bhi, idesc, acc0);
               tc_mma(d, ahi, blo, idesc, 1u);
               tc_mma(d, ahi, bhi, idesc, 1u);
@@ -868,6 +874,13 @@ void launch_tc_pack(const float* A, int64_t lda, int64_t sA, int a_trans, int a_
 void launch_tc2(const TcArgs& a, int batch, const char* name, cudaStream_t s) {
   if (a.M <= 0 || a.N <= 0 || a.K <= 0 || batch <= 0) return;
   dim3 grid((unsigned)((a.N + P_BN - 1) / P_BN), (unsigned)((a.M + 255) / 256), (unsigned)batch);
+  // a triangular A must leave every row some nonzero K (M <= K); else no skipping
+  if (a.a_tri != 0 && a.M > a.K) {
+    TcArgs b = a;
+    b.a_tri = 0;
+    launch_tc2(b, batch, name, s);
+    return;
+  }
   const bool vec = !a.b_trans && a.b_mask == TC_MASK_NONE && (a.K % P_BK) == 0 &&
                    (a.ldb % 4) == 0 && (a.sB % 4) == 0 &&
                    (reinterpret_cast<uintptr_t>(a.B) % 16) == 0;
@@ -887,7 +900,7 @@ void launch_tc2(const TcArgs& a, int batch, const char* name, cudaStream_t s) {
     const int64_t want = (total + LUQR_T4_TPC - 1) / LUQR_T4_TPC;
     const int ctas = (int)std::min<int64_t>(total, std::max<int64_t>(want, sms));
     ensure_dyn_smem<k_gemm_tc4>(T4_SMEM);
-    k_gemm_tc4<<<ctas, 384, T4_SMEM, s>>>(a, mtiles, ntiles, (int)total);
+    k_gemm_tc4<<<ctas, T4_THREADS, T4_SMEM, s>>>(a, mtiles, ntiles, (int)total);
   } else {
     ensure_dyn_smem<k_gemm_tc2>(P_SMEM);
     k_gemm_tc2<<<grid, TC_THREADS, P_SMEM, s>>>(a);
@@ -897,81 +910,121 @@ void launch_tc2(const TcArgs& a, int batch, const char* name, cudaStream_t s) {
 // ---------------------------------------------------------------- full compact-WY T
 // Tf (nb x nb, upper triangular, column-major, ld nb) such that Q = I - V Tf V^T for all
 // nb reflectors of a tile, from the Gram matrix G = V^T V (upper part used) and the stored
-// IB x IB diagonal blocks (T slot: block b at columns b*IB.., IB rows):
-//   Tf[blk b, blk b] = T_b;  Tf[0:jb, blk b] = -Tf[0:jb, 0:jb] G[0:jb, blk b] T_b.
-// One CTA per tile of the batch; thread r owns row r of the current block column.
+// IB x IB diagonal blocks (T slot: block b at columns b*IB.., IB rows).  Built by recursive
+// bisection of the nb/IB blocks: for a node whose leading blocks are A and trailing blocks
+// B, Q = Q_A Q_B gives
+//   Tf[A,A] = T_A,  Tf[B,B] = T_B,  Tf[A,B] = -T_A G[A,B] T_B.
+// Nodes at depth d cover blocks [floor(i nblk / 2^d), floor((i+1) nblk / 2^d)); the deepest
+// level goes first, so both children of a node are complete when it is formed.  The
+// intermediate P = G[A,B] T_B is kept transposed in the node's block below the diagonal,
+// Tf[B,A], and cleared after use (Tf is zero below the diagonal when the kernel ends).
+// One CTA (256 threads) per tile; each product runs in 64 x 64 output tiles, 4 x 4 outputs
+// per thread, operands staged in 32-deep chunks in shared memory.
+constexpr int TF_T = 64, TF_Q = 32, TF_LD = TF_T + 4;
+
+// out(i, j) = sum_{q in [qlo(i0), qhi(j0))} X(i, q) Y(q, j) for one 64 x 64 tile of an m x n
+// product.  YQ: Y's consecutive q are contiguous in memory (else consecutive j).
+template <bool YQ, class FX, class FY, class FO>
+__device__ __forceinline__ void tf_tile(int m, int n, int i0, int j0, int q0, int q1, FX X, FY Y,
+                                        FO out, float* Xs, float* Ys) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  for (int qc = q0; qc < q1; qc += TF_Q) {
+    for (int idx = tid; idx < TF_T * TF_Q; idx += 256) {
+      const int i = idx % TF_T, q = idx / TF_T;
+      Xs[q * TF_LD + i] = (i0 + i < m && qc + q < q1) ? X(i0 + i, qc + q) : 0.f;
+    }
+    for (int idx = tid; idx < TF_T * TF_Q; idx += 256) {
+      const int q = YQ ? idx % TF_Q : idx / TF_T, j = YQ ? idx / TF_Q : idx % TF_T;
+      Ys[q * TF_LD + j] = (j0 + j < n && qc + q < q1) ? Y(qc + q, j0 + j) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int q = 0; q < TF_Q; ++q) {
+      const float4 xa = *reinterpret_cast<const float4*>(&Xs[q * TF_LD + ty * 4]);
+      const float4 yb = *reinterpret_cast<const float4*>(&Ys[q * TF_LD + tx * 4]);
+      const float xv[4] = {xa.x, xa.y, xa.z, xa.w}, yv[4] = {yb.x, yb.y, yb.z, yb.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xv[a], yv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = i0 + ty * 4 + a, j = j0 + tx * 4 + b;
+      if (i < m && j < n) out(i, j, acc[a][b]);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_tfull(const float* __restrict__ G, int64_t sG,
                                                const float* __restrict__ Tslots, int64_t sT,
                                                float* __restrict__ Tf, int64_t sTf, int nb,
                                                const uint8_t* __restrict__ dec, int k) {
   if (dec[k] != DEC_QR) return;
-  extern __shared__ __align__(16) float tf_smem[];
-  float(*X)[IB + 1] = reinterpret_cast<float(*)[IB + 1]>(tf_smem);                  // nb rows
-  float(*Tb)[IB + 1] = reinterpret_cast<float(*)[IB + 1]>(tf_smem + (size_t)nb * (IB + 1));
+  __shared__ __align__(16) float Xs[TF_Q * TF_LD];
+  __shared__ __align__(16) float Ys[TF_Q * TF_LD];
   const int64_t t = blockIdx.x;
   const float* g = G + t * sG;
   const float* ts = Tslots + t * sT;
   float* tf = Tf + t * sTf;
   const int tid = threadIdx.x;
-  for (int jb = 0; jb < nb; jb += IB) {
-    for (int idx = tid; idx < IB * IB; idx += blockDim.x) {
-      const int a = idx % IB, j = idx / IB;
-      Tb[a][j] = ts[a + (int64_t)(jb + j) * IB];
-    }
-    for (int idx = tid; idx < jb * IB; idx += blockDim.x) {
-      const int r = idx % jb, j = idx / jb;
-      X[r][j] = g[r + (int64_t)(jb + j) * nb];
-    }
-    __syncthreads();
-    for (int r = tid; r < nb; r += blockDim.x) {
-      if (r < jb) {
-        float y[IB];
-#pragma unroll
-        for (int j = 0; j < IB; ++j) y[j] = 0.f;
-        // row r of Tf (written by this thread in earlier blocks): 8 loads in flight
-        int q = r;
-        for (; q + 8 <= jb; q += 8) {
-          float tq[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) tq[u] = tf[r + (int64_t)(q + u) * nb];
-#pragma unroll
-          for (int u = 0; u < 8; ++u)
-#pragma unroll
-            for (int j = 0; j < IB; ++j) y[j] += tq[u] * X[q + u][j];
-        }
-        for (; q < jb; ++q) {
-          const float tq = tf[r + (int64_t)q * nb];
-#pragma unroll
-          for (int j = 0; j < IB; ++j) y[j] += tq * X[q][j];
-        }
-#pragma unroll
-        for (int j = 0; j < IB; ++j) {
-          float z = 0.f;
-#pragma unroll
-          for (int q = 0; q <= j; ++q) z += y[q] * Tb[q][j];
-          tf[r + (int64_t)(jb + j) * nb] = -z;
-        }
-      } else if (r < jb + IB) {
-#pragma unroll
-        for (int j = 0; j < IB; ++j)
-          tf[r + (int64_t)(jb + j) * nb] = (r - jb <= j) ? Tb[r - jb][j] : 0.f;
-      } else {
-#pragma unroll
-        for (int j = 0; j < IB; ++j) tf[r + (int64_t)(jb + j) * nb] = 0.f;
+  const int nblk = nb / IB;
+  // diagonal blocks from the T slots; zero below them
+  for (int idx = tid; idx < nb * nb; idx += 256) {
+    const int r = idx % nb, c = idx / nb, rb = r / IB, cb = c / IB;
+    if (rb == cb) tf[idx] = (r <= c) ? ts[(r - cb * IB) + (int64_t)c * IB] : 0.f;
+    else if (rb > cb) tf[idx] = 0.f;
+  }
+  __syncthreads();
+  int D = 0;
+  while ((1 << D) < nblk) ++D;
+  for (int d = D - 1; d >= 0; --d) {
+    for (int i = 0; i < (1 << d); ++i) {
+      const int lo = (int)(((int64_t)i * nblk) >> d), hi = (int)(((int64_t)(i + 1) * nblk) >> d);
+      const int mid = (int)(((int64_t)(2 * i + 1) * nblk) >> (d + 1));
+      if (mid <= lo || hi <= mid) continue;
+      const int a0 = lo * IB, b0 = mid * IB, ma = (mid - lo) * IB, nbB = (hi - mid) * IB;
+      // P = G[A,B] T_B (T_B upper triangular: q <= j), stored as P^T in Tf[B,A]
+      for (int i0 = 0; i0 < ma; i0 += TF_T)
+        for (int j0 = 0; j0 < nbB; j0 += TF_T)
+          tf_tile<true>(
+              ma, nbB, i0, j0, 0, min(nbB, j0 + TF_T),
+              [&](int ii, int q) { return g[(a0 + ii) + (int64_t)(b0 + q) * nb]; },
+              [&](int q, int j) { return tf[(b0 + q) + (int64_t)(b0 + j) * nb]; },
+              [&](int ii, int j, float v) { tf[(b0 + j) + (int64_t)(a0 + ii) * nb] = v; }, Xs, Ys);
+      __syncthreads();
+      // Tf[A,B] = -T_A P (T_A upper triangular: q >= i)
+      for (int i0 = 0; i0 < ma; i0 += TF_T)
+        for (int j0 = 0; j0 < nbB; j0 += TF_T)
+          tf_tile<false>(
+              ma, nbB, i0, j0, i0, ma,
+              [&](int ii, int q) { return tf[(a0 + ii) + (int64_t)(a0 + q) * nb]; },
+              [&](int q, int j) { return tf[(b0 + j) + (int64_t)(a0 + q) * nb]; },
+              [&](int ii, int j, float v) { tf[(a0 + ii) + (int64_t)(b0 + j) * nb] = -v; }, Xs, Ys);
+      __syncthreads();
+      for (int idx = tid; idx < ma * nbB; idx += 256) {
+        const int j = idx % nbB, ii = idx / nbB;
+        tf[(b0 + j) + (int64_t)(a0 + ii) * nb] = 0.f;
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
 void launch_tfull(const float* G, int64_t sG, const float* Tslots, int64_t sT, float* Tf,
                   int64_t sTf, int nb, int batch, const uint8_t* dec, int k, cudaStream_t s) {
   if (batch <= 0) return;
-  const size_t smem = sizeof(float) * ((size_t)nb + IB) * (IB + 1);
-  ensure_dyn_smem<k_tfull>(smem);
   {
     ProfScope ps_("k_tfull", s);
-    k_tfull<<<batch, 256, smem, s>>>(G, sG, Tslots, sT, Tf, sTf, nb, dec, k);
+    k_tfull<<<batch, 256, 0, s>>>(G, sG, Tslots, sT, Tf, sTf, nb, dec, k);
   }
 }
 

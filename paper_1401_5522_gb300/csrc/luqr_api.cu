@@ -151,13 +151,13 @@ void tc_apply_single(luqr_handle* h, int k, TileList tl, Mat<float> C, int64_t c
   TcArgs a{};
   a.dec = h->dec; a.k_step = k; a.want = DEC_QR; a.status = h->status;
   a.M = nb; a.N = c1 - c0; a.K = nb; a.sApk = spk;
-  // W = V^T C
-  a.Apk = pk;
+  // W = V^T C  (V unit lower triangular: V^T upper)
+  a.Apk = pk; a.a_tri = 2;
   a.B = C.p + (int64_t)tl.i0 * nb + c0 * C.ld; a.ldb = C.ld; a.sB = rstride;
   a.C = h->Wbuf + (int64_t)tl.i0 * nb + c0 * ld; a.ldc = ld; a.sC = rstride; a.epi = TC_EPI_OUT;
   launch_tc2(a, tl.count, "k_tc_unmqr_w", s);
-  // C -= (V T^T) W
-  a.Apk = pk + h->pk_tile;
+  // C -= (V T^T) W  (lower triangular times lower triangular)
+  a.Apk = pk + h->pk_tile; a.a_tri = 1;
   a.B = h->Wbuf + (int64_t)tl.i0 * nb + c0 * ld; a.ldb = ld; a.sB = rstride;
   a.C = C.p + (int64_t)tl.i0 * nb + c0 * C.ld; a.ldc = C.ld; a.sC = rstride; a.epi = TC_EPI_SUB;
   launch_tc2(a, tl.count, "k_tc_unmqr_c", s);
@@ -175,20 +175,20 @@ void tc_apply_pair(luqr_handle* h, int k, TileList tl, bool tri, Mat<float> C, i
   TcArgs a{};
   a.dec = h->dec; a.k_step = k; a.want = DEC_QR; a.status = h->status;
   a.M = nb; a.N = c1 - c0; a.K = nb; a.sApk = spk;
-  // W = C1 + V2^T C2
-  a.Apk = pk;
+  // W = C1 + V2^T C2  (TT: V2 upper triangular, V2^T lower)
+  a.Apk = pk; a.a_tri = tri ? 1 : 0;
   a.B = C.p + i0r + c0 * C.ld; a.ldb = C.ld; a.sB = rstride;
   a.C1 = C.p + e0r + c0 * C.ld; a.ldc1 = C.ld; a.sC1 = rstride;
   a.C = Wp; a.ldc = ld; a.sC = rstride; a.epi = TC_EPI_ADD_OUT;
   launch_tc2(a, tl.count, tri ? "k_tc_ttmqr_w" : "k_tc_tsmqr_w", s);
   a.C1 = nullptr;
-  // C1 -= T^T W
-  a.Apk = pk + 2 * h->pk_tile;
+  // C1 -= T^T W  (T^T lower triangular)
+  a.Apk = pk + 2 * h->pk_tile; a.a_tri = 1;
   a.B = Wp; a.ldb = ld; a.sB = rstride;
   a.C = C.p + e0r + c0 * C.ld; a.ldc = C.ld; a.sC = rstride; a.epi = TC_EPI_SUB;
   launch_tc2(a, tl.count, tri ? "k_tc_ttmqr_c1" : "k_tc_tsmqr_c1", s);
   // C2 -= (V2 T^T) W
-  a.Apk = pk + h->pk_tile;
+  a.Apk = pk + h->pk_tile; a.a_tri = 0;
   a.C = C.p + i0r + c0 * C.ld;
   launch_tc2(a, tl.count, tri ? "k_tc_ttmqr_c2" : "k_tc_tsmqr_c2", s);
 }

@@ -1,7 +1,11 @@
 // Launch profiler of the library: when enabled, every kernel launch is bracketed by
-// CUDA events recorded on its own stream and attributed to the kernel's name.
+// CUDA events recorded on its own stream and attributed to the kernel's name.  In trace
+// mode each launch's start and end are also kept, relative to an event recorded when
+// tracing was switched on, with the stream it ran on.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstdint>
 #include <map>
 #include <mutex>
 #include <string>
@@ -15,7 +19,17 @@ namespace {
 struct Rec {
   int id;
   cudaEvent_t e0, e1;
+  cudaStream_t s;
 };
+struct TraceRec {
+  int id;
+  float t0, t1;
+  cudaStream_t s;
+};
+bool g_trace = false;
+cudaEvent_t g_base = nullptr;
+std::vector<TraceRec> g_trace_recs;
+constexpr size_t kMaxTrace = 4u << 20;
 std::mutex g_mtx;
 bool g_enabled = false;
 std::vector<Rec> g_recs;
@@ -40,8 +54,13 @@ cudaEvent_t take_event() {
 void drain_locked() {
   for (Rec& r : g_recs) {
     float ms = 0.f;
-    if (cudaEventSynchronize(r.e1) == cudaSuccess && cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess)
+    if (cudaEventSynchronize(r.e1) == cudaSuccess && cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
       g_ms[r.id] += ms;
+      float t0 = 0.f;
+      if (g_trace && g_base && g_trace_recs.size() < kMaxTrace &&
+          cudaEventElapsedTime(&t0, g_base, r.e0) == cudaSuccess)
+        g_trace_recs.push_back(TraceRec{r.id, t0, t0 + ms, r.s});
+    }
     g_launches[r.id] += 1;
     g_pool.push_back(r.e0);
     g_pool.push_back(r.e1);
@@ -65,7 +84,7 @@ void prof_begin(const char* name, cudaStream_t s) {
     id = it->second;
   }
   if (g_recs.size() >= 200000) drain_locked();   // bound the number of live events
-  Rec r{id, take_event(), take_event()};
+  Rec r{id, take_event(), take_event(), s};
   cudaEventRecord(r.e0, s);
   g_recs.push_back(r);
   t_open = (int)g_recs.size() - 1;
@@ -82,13 +101,37 @@ void prof_end(cudaStream_t s) {
 
 extern "C" int luqr_profile(int enable, int reset) {
   std::lock_guard<std::mutex> lk(luqr::g_mtx);
+  if (enable < 0 || enable > 2) return LUQR_ERR_INVALID;
   if (reset) {
     luqr::drain_locked();
     std::fill(luqr::g_launches.begin(), luqr::g_launches.end(), 0);
     std::fill(luqr::g_ms.begin(), luqr::g_ms.end(), 0.0);
+    luqr::g_trace_recs.clear();
   }
+  if (enable == 2 && !luqr::g_trace) {
+    luqr::drain_locked();
+    if (!luqr::g_base && cudaEventCreate(&luqr::g_base) != cudaSuccess) return LUQR_ERR_CUDA;
+    if (cudaEventRecord(luqr::g_base, 0) != cudaSuccess) return LUQR_ERR_CUDA;
+    luqr::g_trace_recs.clear();
+  }
+  luqr::g_trace = enable == 2;
   luqr::g_enabled = enable != 0;
   return LUQR_OK;
+}
+
+extern "C" int luqr_profile_trace(const char** names, float* t0_ms, float* t1_ms,
+                                  uint64_t* stream, int64_t cap) {
+  std::lock_guard<std::mutex> lk(luqr::g_mtx);
+  luqr::drain_locked();
+  const int64_t n = std::min<int64_t>(cap, (int64_t)luqr::g_trace_recs.size());
+  for (int64_t i = 0; i < n; ++i) {
+    const luqr::TraceRec& r = luqr::g_trace_recs[(size_t)i];
+    if (names) names[i] = luqr::g_names[r.id].c_str();
+    if (t0_ms) t0_ms[i] = r.t0;
+    if (t1_ms) t1_ms[i] = r.t1;
+    if (stream) stream[i] = (uint64_t)(uintptr_t)r.s;
+  }
+  return (int)std::min<int64_t>((int64_t)luqr::g_trace_recs.size(), INT32_MAX);
 }
 
 extern "C" int luqr_profile_read(const char** names, int64_t* launches, double* total_ms, int cap) {

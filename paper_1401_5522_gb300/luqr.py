@@ -71,6 +71,9 @@ _SIGS = {
     "luqr_profile": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "luqr_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    "luqr_profile_trace": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
+                                          ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64),
+                                          _I64]),
     "luqr_gemm_sub_f32": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _I64, _I64, _I64, _I64, _P, _P]),
     "luqr_panel_test_noalloc": (ctypes.c_int, [_P, _I64, _I64, ctypes.c_int, ctypes.c_int,
                                                ctypes.c_double, ctypes.c_int, _P, _P, _P]),
@@ -309,9 +312,26 @@ def version():
     return lib().luqr_version().decode()
 
 
-def profile(enable=True, reset=True):
-    """Start (or stop) the library's per-launch CUDA-event profiler."""
-    return lib().luqr_profile(1 if enable else 0, 1 if reset else 0)
+def profile(enable=True, reset=True, trace=False):
+    """Start (or stop) the library's per-launch CUDA-event profiler; trace=True also keeps
+    every launch's start and end (see profile_trace)."""
+    mode = (2 if trace else 1) if enable else 0
+    st = lib().luqr_profile(mode, 1 if reset else 0)
+    if st != OK:
+        raise LuqrError(st, "luqr_profile")
+    return st
+
+
+def profile_trace():
+    """Launch timeline of trace mode: list of (kernel name, start ms, end ms, stream id)."""
+    L = lib()
+    n = L.luqr_profile_trace(None, None, None, None, 0)
+    names = (ctypes.c_char_p * max(n, 1))()
+    t0 = (ctypes.c_float * max(n, 1))()
+    t1 = (ctypes.c_float * max(n, 1))()
+    sid = (ctypes.c_uint64 * max(n, 1))()
+    n = min(n, L.luqr_profile_trace(names, t0, t1, sid, n))
+    return [(names[i].decode(), float(t0[i]), float(t1[i]), int(sid[i])) for i in range(n)]
 
 
 def profile_read(cap=64):
