@@ -358,21 +358,27 @@ __device__ void panel_qr(T* Rs, T* Ps, int nrows, bool tri, int jb, T* tau_s, T*
   __syncthreads();
 }
 
-// Register form of panel_qr (same operations per element): thread (warp w, lane c) keeps
-// rows w + 8q (q < RPT) of panel column c in registers; column j's values reach the other
-// lanes by warp shuffles, so the per-column dot products and updates need no shared-memory
-// traffic.  The panel is loaded from and stored back to Ps around the loop.
+// Register form of panel_qr (same operations per element, same summation orders, so the
+// same bits): thread (warp w, lane c) keeps rows w + 8q (q < RPT) of panel column c in
+// registers; column j's values reach the other lanes by warp shuffles.  One block barrier
+// per column: every warp reads the eight partial norms and dot products of column j,
+// forms the reflector itself (identical inputs, identical results), updates its rows and
+// writes the partials of column j+1 into the other half of a double buffer.  The G
+// entries of each column are parked below the diagonal of Ts (G[c][j] at Ts[j][c]) and T
+// is formed after the loop, one row per lane (T[c][j] = -tau_j sum_{b=c}^{j-1} T[c][b]
+// G[b][j]: rows are independent); the parked entries are cleared afterwards.  For pairs,
+// row j of R is read into registers during column j-1 (nobody writes it then), because
+// warp 0 updates it during column j while the other warps still form the reflector.
+// scratch: >= 2*8*IB + 2*8 + 2*IB + IB elements.
 template <typename T, bool SINGLE, int RPT>
 __device__ void panel_qr_reg(T* Rs, T* Ps, int nrows, bool tri, int jb, T* tau_s, T* Ts,
                              T* scratch) {
   static_assert(NT == 256 && IB == 32, "thread map assumes 8 warps x 32 columns");
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  T* part = scratch;               // [8][IB]
-  T* nrm = part + 8 * IB;          // [8]
-  T* wv = nrm + 8;                 // [IB]
-  T* sinv = wv + IB;               // [IB]
-  T* sc = sinv + IB;               // [3] tau, inv, beta
-  T* topbuf = sc + 3;              // [IB] row j of the panel (single)
+  T* part = scratch;               // [2][8][IB] partial dots (double buffered by column)
+  T* nrm = part + 2 * 8 * IB;      // [2][8] partial squared norms
+  T* topbuf = nrm + 2 * 8;         // [2][IB] row j of the panel (single)
+  T* sinv = topbuf + 2 * IB;       // [IB]
   auto lo = [&](int j) { return SINGLE ? j + 1 : 0; };
   auto hi = [&](int j) { return SINGLE ? nrows : (tri ? min(jb + j + 1, nrows) : nrows); };
   const int c = lane;
@@ -382,86 +388,113 @@ __device__ void panel_qr_reg(T* Rs, T* Ps, int nrows, bool tri, int jb, T* tau_s
     const int r = w + 8 * q;
     x[q] = (r < nrows) ? Ps[r * VST + c] : (T)0;
   }
-  if (c == 0) {
-    T sq = (T)0;
+  // partials of column 0 (its dots with every column, its partial norm, row 0 when single)
+  {
+    const int l0 = lo(0), h0 = hi(0);
+    T d = (T)0, sq = (T)0;
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
       const int r = w + 8 * q;
-      if (r >= lo(0) && r < hi(0)) sq += x[q] * x[q];
-    }
-    nrm[w] = sq;
-  }
-  for (int j = 0; j < IB; ++j) {
-    const int l0 = lo(j), h0 = hi(j);
-    // [A] dots of column j with every column; column j shuffled in from lane j
-    T xj[RPT];
-    T d = (T)0;
-#pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-      const int r = w + 8 * q;
-      xj[q] = __shfl_sync(0xffffffffu, x[q], j);
-      if (r >= l0 && r < h0) d += xj[q] * x[q];
-      if (SINGLE && r == j) topbuf[c] = x[q];
-    }
-    part[w * IB + c] = (c != j) ? d : (T)0;
-    __syncthreads();
-    // [B] warp 0: reflector, w_c / G column, T column
-    if (w == 0) {
-      T ss = (T)0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) ss += nrm[q];
-      const T a0 = SINGLE ? topbuf[j] : Rs[j * VST + j];
-      T beta, tau, denom;
-      make_reflector<T>(a0, ss, &beta, &tau, &denom);
-      const T inv = (tau == (T)0) ? (T)0 : (T)1 / denom;
-      T dsum = (T)0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) dsum += part[q * IB + c];
-      const T topc = SINGLE ? topbuf[c] : Rs[j * VST + c];
-      if (c > j) wv[c] = topc + inv * dsum;
-      else if (c < j) wv[c] = sinv[c] * (inv * dsum + (SINGLE ? topc : (T)0));
-      __syncwarp();
-      T tcol = (T)0;
-      if (c < j) {
-        T acc = (T)0;
-        for (int b = c; b < j; ++b) acc += Ts[c * TST + b] * wv[b];
-        tcol = -tau * acc;
-      } else if (c == j) {
-        tcol = tau;
+      const T xj = __shfl_sync(0xffffffffu, x[q], 0);
+      if (r >= l0 && r < h0) {
+        d += xj * x[q];
+        sq += x[q] * x[q];
       }
-      Ts[c * TST + j] = tcol;
+      if (SINGLE && r == 0) topbuf[c] = x[q];
+    }
+    part[w * IB + c] = (c != 0) ? d : (T)0;
+    if (c == 0) nrm[w] = sq;
+  }
+  T ra0 = (T)0, rc = (T)0;   // pairs: R[j][j] and R[j][c] as they stand before column j
+  if (!SINGLE) {
+    ra0 = Rs[0];
+    rc = Rs[c];
+  }
+  __syncthreads();
+  for (int j = 0; j < IB; ++j) {
+    const int cur = j & 1, nxt = cur ^ 1;
+    const int l0 = lo(j), h0 = hi(j);
+    const T* pc = part + cur * 8 * IB;
+    // reflector of column j (every warp, identical arithmetic)
+    T ss = (T)0, dsum = (T)0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ss += nrm[cur * 8 + q];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) dsum += pc[q * IB + c];
+    const T a0 = SINGLE ? topbuf[cur * IB + j] : ra0;
+    T beta, tau, denom;
+    make_reflector<T>(a0, ss, &beta, &tau, &denom);
+    const T inv = (tau == (T)0) ? (T)0 : (T)1 / denom;
+    const T topc = SINGLE ? topbuf[cur * IB + c] : rc;
+    const T wc = (c > j) ? topc + inv * dsum : (T)0;
+    if (w == 0) {
+      if (c < j) Ts[j * TST + c] = sinv[c] * (inv * dsum + (SINGLE ? topc : (T)0));
       if (c == 0) {
-        if (!SINGLE) Rs[j * VST + j] = beta;
         tau_s[j] = tau;
         sinv[j] = inv;
-        sc[0] = tau;
-        sc[1] = inv;
-        sc[2] = beta;
+      }
+      if (!SINGLE) {
+        if (c == j) Rs[j * VST + j] = beta;
+        else if (c > j && tau != (T)0) Rs[j * VST + c] -= tau * wc;
       }
     }
-    __syncthreads();
-    // [C] update of the columns right of j; the top row; partial norm of column j+1
-    {
-      const T tau = sc[0], inv = sc[1];
-      const T wc = (c > j) ? wv[c] : (T)0;
-      const T f = tau * inv * wc;
-      const bool upd = c > j && tau != (T)0;
-      T sq = (T)0;
-      const int l1 = lo(j + 1), h1 = hi(j + 1);
+    // update of the columns right of j on this warp's rows, then the partials of j+1
+    const T f = tau * inv * wc;
+    const bool upd = c > j && tau != (T)0;
+    const int l1 = lo(j + 1), h1 = hi(j + 1);
+    T d = (T)0, sq = (T)0;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int r = w + 8 * q;
+      const T xj = __shfl_sync(0xffffffffu, x[q], j);
+      if (upd && r >= l0 && r < h0) x[q] -= f * xj;
+      if (SINGLE && r == j) {
+        if (c == j) x[q] = beta;
+        else if (upd) x[q] -= tau * wc;
+      }
+    }
+    if (j + 1 < IB) {
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         const int r = w + 8 * q;
-        if (upd && r >= l0 && r < h0) x[q] -= f * xj[q];
-        if (SINGLE && r == j) {
-          if (c == j) x[q] = sc[2];
-          else if (upd) x[q] -= tau * wc;
+        const T xj1 = __shfl_sync(0xffffffffu, x[q], j + 1);
+        if (r >= l1 && r < h1) {
+          d += xj1 * x[q];
+          sq += x[q] * x[q];
         }
-        if (r >= l1 && r < h1) sq += x[q] * x[q];
+        if (SINGLE && r == j + 1) topbuf[nxt * IB + c] = x[q];
       }
-      if (!SINGLE && w == 0 && upd) Rs[j * VST + c] -= tau * wc;
-      if (j + 1 < IB && c == j + 1) nrm[w] = sq;
+      part[nxt * 8 * IB + w * IB + c] = (c != j + 1) ? d : (T)0;
+      if (c == j + 1) nrm[nxt * 8 + w] = sq;
+      if (!SINGLE) {
+        ra0 = Rs[(j + 1) * VST + j + 1];
+        rc = Rs[(j + 1) * VST + c];
+      }
     }
     __syncthreads();
+  }
+  // T, one row per lane of warp 0 (reads G below the diagonal, writes on and above it)
+  if (w == 0) {
+    T trow[IB];
+#pragma unroll
+    for (int j = 0; j < IB; ++j) {
+      T v = (T)0;
+      if (j == c) {
+        v = tau_s[j];
+      } else if (j > c) {
+        T acc = (T)0;
+#pragma unroll
+        for (int b = 0; b < IB; ++b)
+          if (b >= c && b < j) acc += trow[b] * Ts[j * TST + b];
+        v = -tau_s[j] * acc;
+      }
+      trow[j] = v;
+      if (j >= c) Ts[c * TST + j] = v;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < IB; ++j)
+      if (j < c) Ts[c * TST + j] = (T)0;
   }
   // scale the reflector columns and store the panel back
 #pragma unroll
@@ -470,8 +503,8 @@ __device__ void panel_qr_reg(T* Rs, T* Ps, int nrows, bool tri, int jb, T* tau_s
     if (r < nrows) {
       T v = x[q];
       if (r >= lo(c) && r < hi(c)) {
-        const T f = sinv[c];
-        v = (f == (T)0) ? (T)0 : v * f;
+        const T fs = sinv[c];
+        v = (fs == (T)0) ? (T)0 : v * fs;
       }
       Ps[r * VST + c] = v;
     }

@@ -614,9 +614,6 @@ __device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
 //   warps 4-7   TF32 hi/lo split of B into the stage
 //   warps 8-11  epilogue: TMEM -> registers -> C, then free the accumulator
 // Chunks are numbered across tiles (g = tile_iter * nK + c) for the ring slots and parities.
-#ifndef LUQR_T4_TPC
-#define LUQR_T4_TPC 8
-#endif
 constexpr int T4_THREADS = 384;
 constexpr int T4_BN = 128;
 constexpr int T4_STG = 3;
@@ -895,10 +892,10 @@ void launch_tc2(const TcArgs& a, int batch, const char* name, cudaStream_t s) {
     }
     const int mtiles = (int)((a.M + 255) / 256), ntiles = (int)((a.N + T4_BN - 1) / T4_BN);
     const int64_t total = (int64_t)mtiles * ntiles * batch;
-    // a few tiles per CTA: enough to overlap epilogues with main loops, few enough that SMs
-    // turn over often and the high-priority panel kernels get scheduled between CTAs
-    const int64_t want = (total + LUQR_T4_TPC - 1) / LUQR_T4_TPC;
-    const int ctas = (int)std::min<int64_t>(total, std::max<int64_t>(want, sms));
+    // persistent over all but about a ninth of the SMs: the high-priority panel, look-ahead
+    // and operand kernels of the next steps keep SMs of their own (a grid over every SM held
+    // them off for whole launches; short-lived CTAs cost the pipeline fill and drain of each)
+    const int ctas = (int)std::min<int64_t>(total, std::max(1, sms - sms / 9));
     ensure_dyn_smem<k_gemm_tc4>(T4_SMEM);
     k_gemm_tc4<<<ctas, T4_THREADS, T4_SMEM, s>>>(a, mtiles, ntiles, (int)total);
   } else {

@@ -197,6 +197,27 @@ def test_fp32_decisions_match_float32_oracle():
     assert np.all(np.abs(mg[fin] - f.margin[fin]) <= 1e-2)
 
 
+@pytest.mark.parametrize("tree,nb,kernels", [("binary_tt", 64, "tensor"), ("flat_ts", 64, "cuda"),
+                                             ("grouped", 128, "tensor"), ("binary_tt", 256, "cuda"),
+                                             ("flat_ts", 128, "tensor")])
+def test_fp32_qr_factor_matches_float32_oracle(tree, nb, kernels):
+    """All-QR FP32 runs (no pivot choice can flip, no growth) against the oracle's float32
+    emulation, triangle element by element.  Rounding-order differences of FP32 sums (and
+    the 3xTF32 operand split, ~2^-22 relative) stay within 2e-4 of max |U|."""
+    N = 768 + 40
+    A = gauss(N, 13)
+    b = A @ np.ones(N)
+    _, f = O.solve(A, b, nb, O.CRIT_FORCE_QR, 0.0, tree=ORACLE_TREE[tree], group=3,
+                   dtype=np.float32)
+    luqr = L()
+    h = luqr.factor(cuda_colmajor(A), nb, "force_qr", 0.0, precision="fp32", tree=tree, group=3,
+                    fp32_kernels=kernels)
+    U = np.triu(h.factor_data()[:N, :N]).astype(np.float64)
+    h.close()
+    Uo = np.asarray(f.U, dtype=np.float64)
+    assert np.max(np.abs(U - Uo)) <= 2e-4 * np.max(np.abs(Uo)), np.max(np.abs(U - Uo))
+
+
 @pytest.mark.parametrize("tree,nb", [("flat_ts", 128), ("binary_tt", 128), ("binary_tt", 512),
                                      ("grouped", 256)])
 def test_fp32_refinement_reaches_fp64_accuracy(tree, nb):
