@@ -139,9 +139,10 @@ KERNEL_OF_LABEL = {
     "k_ttmqr": "k_pair_apply", "k_tsmqr": "k_pair_apply",
 }
 
-# DRAM bytes per algorithmic byte of the tensor-core update kernel, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum of two bulk launches at N=8192)
-TRAFFIC_RATIO = {"k_gemm_tc4": 0.95}
+# DRAM bytes per algorithmic byte of the tensor-core update kernel, from one ncu capture of
+# the current kernel (dram__bytes_read.sum + dram__bytes_write.sum of the two bulk QR
+# launches of step 0 at N=8192: 473.7 / 511.7 MB and 725.2 / 763.4 MB; profiles/)
+TRAFFIC_RATIO = {"k_gemm_tc4": 0.94}
 
 
 def traffic_per_launch(kernel, alg_bytes_per_launch):
