@@ -94,7 +94,12 @@ typedef struct luqr_options {
                               (read with luqr_features); implied by speculate != 0 */
   const float* mlp_params; /* DEVICE, LUQR_MLP_PARAMS floats (layout at luqr_mlp_forward);
                               read during the factorization, caller-owned */
-  int reserved[8];
+  int norm_mode;           /* ||A_kk^-1||_1 for Max and Sum: 0 exact (default, X = U^-1 L^-1 P);
+                              1 the Hager-Higham estimate (Sec. III-D's iterative O(nb^2)
+                              estimate; a lower bound of the exact norm, so LU is admitted at
+                              least as often).  luqr_factor only (the batched solver
+                              returns LUQR_ERR_INVALID for 1). */
+  int reserved[7];
 } luqr_options;
 
 typedef struct luqr_handle* luqr_handle_t;

@@ -53,7 +53,9 @@ INJECT_SCALE = 2.0 ** -27   # run-time tile-row scaling used to force a QR step
 
 READINGS = {
     "pivot": "partial pivoting inside the diagonal tile only; pivot = first row of maximal |a|",
-    "inverse_norm": "||A_kk^-1||_1 computed exactly from the L and U factors (X = U^-1 L^-1 P)",
+    "inverse_norm": "||A_kk^-1||_1 computed exactly from the L and U factors (X = U^-1 L^-1 P); "
+                    "norm_mode=1: the Hager-Higham estimate (a lower bound, so the test admits "
+                    "LU at least as often)",
     "tie": ">= in Eq. 2-4 selects LU",
     "zero_pivot": "an exact zero pivot in the diagonal GETRF selects QR (FORCE_LU raises Singular)",
     "alpha_zero": "alpha = 0 selects QR at every step, the last one included",
@@ -294,6 +296,77 @@ def inv_norm1(LU, piv):
     return norm1(X)
 
 
+def _solve_t(L64, piv, x):
+    """A^-T x for A = P^T L U: U^-T, then L^-T (unit), then P^T (swaps in reverse order)."""
+    p = L64.shape[0]
+    w = np.array(x, dtype=np.float64)
+    for r in range(p):                      # U^T w = x, forward
+        w[r] = (w[r] - np.dot(L64[:r, r], w[:r])) / L64[r, r]
+    for r in reversed(range(p)):            # L^T v = w, backward, unit diagonal
+        w[r] = w[r] - np.dot(L64[r + 1:, r], w[r + 1:])
+    for r in reversed(range(p)):
+        s = piv[r]
+        if s != r:
+            w[[r, s]] = w[[s, r]]
+    return w
+
+
+def _solve(L64, piv, x):
+    """A^-1 x for A = P^T L U: P, then L^-1 (unit), then U^-1."""
+    y = np.array(x, dtype=np.float64).reshape(-1, 1)
+    apply_row_swaps(y, piv)
+    unit_lower_solve(L64, y)
+    upper_solve(L64, y)
+    return y[:, 0]
+
+
+def _sign(v):
+    return np.where(v >= 0.0, 1.0, -1.0)
+
+
+def inv_norm1_est(LU, piv):
+    """Estimate of ||A_kk^-1||_1 in O(nb^2) per iteration (the paper's Sec. III-D uses an
+    iterative estimate; this is the Hager (1984) / Higham (1988) 1-norm estimator).
+
+    f(x) = ||A^-1 x||_1 is convex, so its maximum over the unit 1-norm ball is reached at a
+    vertex e_j and equals the largest column sum of |A^-1|.  Starting from the centre
+    x = e/n, each iteration takes the sub-gradient z = A^-T sign(A^-1 x) and moves to the
+    vertex e_j of the largest |z_j|; it stops when the sign vector repeats, the value stops
+    growing, the best vertex stays the same, or after five iterations.  A last probe with
+    the alternating vector x_i = (-1)^i (1 + i/(n-1)) guards against unlucky paths; its
+    value 2||A^-1 x||_1 / (3n) is taken when larger.  Every value is ||A^-1 w||_1 for some
+    ||w||_1 <= 1, so the estimate never exceeds the exact norm (up to rounding)."""
+    p = LU.shape[0]
+    L64 = LU.astype(np.float64)
+    if p == 1:
+        return abs(1.0 / L64[0, 0])
+    y = _solve(L64, piv, np.full(p, 1.0 / p))
+    est = float(np.sum(np.abs(y)))
+    xi = _sign(y)
+    z = _solve_t(L64, piv, xi)
+    j = int(np.argmax(np.abs(z)))
+    it = 2
+    while True:
+        e = np.zeros(p)
+        e[j] = 1.0
+        y = _solve(L64, piv, e)
+        est_old = est
+        est = float(np.sum(np.abs(y)))
+        if np.array_equal(_sign(y), xi) or est <= est_old:
+            break
+        xi = _sign(y)
+        z = _solve_t(L64, piv, xi)
+        jlast = j
+        j = int(np.argmax(np.abs(z)))
+        if abs(z[jlast]) == abs(z[j]) or it >= 5:
+            break
+        it += 1
+    i = np.arange(p, dtype=np.float64)
+    alt = np.where(np.arange(p) % 2 == 0, 1.0, -1.0) * (1.0 + i / (p - 1))
+    t = 2.0 * float(np.sum(np.abs(_solve(L64, piv, alt)))) / (3.0 * p)
+    return max(est, t)
+
+
 @dataclass
 class StepDecision:
     dec: int
@@ -303,7 +376,7 @@ class StepDecision:
 
 
 def decide(criterion, alpha, LU, piv, zero_row, norms_below, local_max, away_max,
-           mumps_mode=0):
+           mumps_mode=0, norm_mode=0):
     """Robustness test of Sec. III.
 
     Max (Eq. 2):   alpha * (1/||A_kk^-1||_1) >= max_{i>k} ||A_ik||_1
@@ -318,7 +391,7 @@ def decide(criterion, alpha, LU, piv, zero_row, norms_below, local_max, away_max
     if zero_row >= 0:
         return StepDecision(DEC_QR, -math.inf, 0.0)
     if criterion in (CRIT_MAX, CRIT_SUM):
-        inv = inv_norm1(LU, piv)
+        inv = inv_norm1(LU, piv) if norm_mode == 0 else inv_norm1_est(LU, piv)
         lhs = alpha * (1.0 / inv)
         if criterion == CRIT_MAX:
             rhs = max(norms_below) if len(norms_below) else 0.0
@@ -460,7 +533,8 @@ def tile_bounds(i, nb, N):
 
 
 def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
-           forced=None, inject=(), dtype=np.float64, track_growth=False, on_step=None):
+           forced=None, inject=(), dtype=np.float64, track_growth=False, on_step=None,
+           norm_mode=0):
     """Run Alg. 1 on the augmented matrix [A | b] and return the Factorization.
 
     A: N x N; b: None, N or N x nrhs.  dtype float32 emulates the whole factorization
@@ -468,6 +542,7 @@ def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
     ``forced``: optional per-step decisions replacing the criterion (replay).
     ``inject``: steps whose tile row is scaled by 2^-27 before the criterion.
     ``on_step(k, aug_before, fact)``: test hook called before each step.
+    ``norm_mode``: 0 exact ||A_kk^-1||_1, 1 the Hager-Higham estimate (inv_norm1_est).
     """
     A = np.asarray(A)
     N = A.shape[0]
@@ -523,7 +598,7 @@ def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
             sd = StepDecision(d, math.inf if d == DEC_LU else -math.inf)
         else:
             sd = decide(criterion, alpha, LU, piv, zero_row, norms[1:], local_max,
-                        away_max, mumps_mode)
+                        away_max, mumps_mode, norm_mode)
         if sd.dec == DEC_LU and zero_row >= 0:
             raise Singular(k, r0 + zero_row)
         fact.dec[k] = sd.dec

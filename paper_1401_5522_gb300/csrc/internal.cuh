@@ -114,6 +114,9 @@ void launch_getrf(const T* W, int64_t ldw, int k, int nb, T* S, int* piv_s, int*
 template <typename T>
 void launch_invnorm(const T* S, int nb, const int* piv_s, double* colsum, const int* status,
                     cudaStream_t s);
+template <typename T>
+void launch_invnorm_est(const T* S, int nb, const int* piv_s, double* colsum, const int* status,
+                        cudaStream_t s);
 
 struct DecideArgs {
   int k, n, nb, criterion, mumps_mode;

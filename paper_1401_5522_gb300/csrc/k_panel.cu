@@ -400,6 +400,250 @@ void launch_invnorm(const T* S, int nb, const int* piv_s, double* colsum, const 
                                                                              colsum, status);
 }
 
+// ---------------------------------------------------------------- ||A_kk^-1||_1 estimate
+// Hager-Higham estimator of ||A^-1||_1 for A = P^T L U (norm_mode = 1; the paper's
+// Sec. III-D uses an iterative O(nb^2) estimate): maximise the convex f(x) = ||A^-1 x||_1
+// over the unit 1-norm ball by moving from the centre e/nb to the vertex e_j of the
+// largest |z_j|, z = A^-T sign(A^-1 x); stop when the sign vector repeats, the value stops
+// growing, the vertex stays, or after five iterations; finally probe the alternating
+// vector x_i = (-1)^i (1 + i/(nb-1)) and keep 2||A^-1 x||_1 / (3 nb) when larger.  One CTA;
+// every solve is blocked by 32: a warp solves the diagonal block with shuffles, the block
+// then updates the remaining rows.  FP64 arithmetic on the stored factors.  The estimate
+// goes to colsum[0] (the other entries are 0), so the decision kernel is unchanged.
+constexpr int EST_T = 256;
+
+__device__ double est_block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum_d(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < EST_T / 32; ++w) t += red[w];
+  return t;
+}
+
+// First index of the largest |z_i|.
+__device__ int est_block_argmax(const double* z, int nb, double* redv, int* redi) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double bv = -1.0;
+  int bi = nb;
+  for (int i = threadIdx.x; i < nb; i += EST_T) {
+    const double a = fabs(z[i]);
+    if (a > bv) { bv = a; bi = i; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+  }
+  __syncthreads();
+  if (lane == 0) { redv[warp] = bv; redi[warp] = bi; }
+  __syncthreads();
+  double rv = -1.0;
+  int ri = nb;
+  for (int w = 0; w < EST_T / 32; ++w)
+    if (redv[w] > rv || (redv[w] == rv && redi[w] < ri)) { rv = redv[w]; ri = redi[w]; }
+  return ri;
+}
+
+// v <- A^-1 v = U^-1 L^-1 P v  (perm: (P v)[i] = v[perm[i]])
+template <typename T>
+__device__ void est_solve(const T* __restrict__ S, int nb, double* v, double* tmp,
+                          const int* perm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < nb; i += EST_T) tmp[i] = v[perm[i]];
+  __syncthreads();
+  for (int i = tid; i < nb; i += EST_T) v[i] = tmp[i];
+  __syncthreads();
+  for (int b0 = 0; b0 < nb; b0 += 32) {            // L y = P v, unit lower, forward
+    if (warp == 0) {
+      double a[32];   // row b0+lane of the diagonal block, loaded before the dependent chain
+#pragma unroll
+      for (int j = 0; j < 32; ++j) a[j] = (double)S[(b0 + lane) + (int64_t)(b0 + j) * nb];
+      double yi = v[b0 + lane];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const double yj = __shfl_sync(0xffffffffu, yi, j);
+        if (lane > j) yi -= a[j] * yj;
+      }
+      v[b0 + lane] = yi;
+    }
+    __syncthreads();
+    for (int i = b0 + 32 + tid; i < nb; i += EST_T) {
+      double acc = 0.0;
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j) acc += (double)S[i + (int64_t)(b0 + j) * nb] * v[b0 + j];
+      v[i] -= acc;
+    }
+    __syncthreads();
+  }
+  for (int b0 = nb - 32; b0 >= 0; b0 -= 32) {      // U x = y, backward
+    if (warp == 0) {
+      double a[32];   // row b0+lane of the diagonal block (a[lane] is the pivot)
+#pragma unroll
+      for (int j = 0; j < 32; ++j) a[j] = (double)S[(b0 + lane) + (int64_t)(b0 + j) * nb];
+      double xi = v[b0 + lane];
+#pragma unroll
+      for (int j = 31; j >= 0; --j) {
+        if (lane == j) xi = xi / a[j];
+        const double xj = __shfl_sync(0xffffffffu, xi, j);
+        if (lane < j) xi -= a[j] * xj;
+      }
+      v[b0 + lane] = xi;
+    }
+    __syncthreads();
+    for (int i = tid; i < b0; i += EST_T) {
+      double acc = 0.0;
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j) acc += (double)S[i + (int64_t)(b0 + j) * nb] * v[b0 + j];
+      v[i] -= acc;
+    }
+    __syncthreads();
+  }
+}
+
+// v <- A^-T v = P^T L^-T U^-T v
+template <typename T>
+__device__ void est_solve_t(const T* __restrict__ S, int nb, double* v, double* tmp,
+                            const int* perm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int b0 = 0; b0 < nb; b0 += 32) {            // U^T w = v, forward (column i of U)
+    if (warp == 0) {
+      double a[32];   // column b0+lane of the diagonal block (a[lane] is the pivot)
+#pragma unroll
+      for (int j = 0; j < 32; ++j) a[j] = (double)S[(b0 + j) + (int64_t)(b0 + lane) * nb];
+      double wi = v[b0 + lane];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        if (lane == j) wi = wi / a[j];
+        const double wj = __shfl_sync(0xffffffffu, wi, j);
+        if (lane > j) wi -= a[j] * wj;
+      }
+      v[b0 + lane] = wi;
+    }
+    __syncthreads();
+    for (int i = b0 + 32 + tid; i < nb; i += EST_T) {
+      const T* col = S + (int64_t)i * nb + b0;
+      double acc = 0.0;
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j) acc += (double)col[j] * v[b0 + j];
+      v[i] -= acc;
+    }
+    __syncthreads();
+  }
+  for (int b0 = nb - 32; b0 >= 0; b0 -= 32) {      // L^T u = w, backward, unit
+    if (warp == 0) {
+      double a[32];   // column b0+lane of the diagonal block
+#pragma unroll
+      for (int j = 0; j < 32; ++j) a[j] = (double)S[(b0 + j) + (int64_t)(b0 + lane) * nb];
+      double ui = v[b0 + lane];
+#pragma unroll
+      for (int j = 31; j >= 0; --j) {
+        const double uj = __shfl_sync(0xffffffffu, ui, j);
+        if (lane < j) ui -= a[j] * uj;
+      }
+      v[b0 + lane] = ui;
+    }
+    __syncthreads();
+    for (int i = tid; i < b0; i += EST_T) {
+      const T* col = S + (int64_t)i * nb + b0;
+      double acc = 0.0;
+#pragma unroll 8
+      for (int j = 0; j < 32; ++j) acc += (double)col[j] * v[b0 + j];
+      v[i] -= acc;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < nb; i += EST_T) tmp[perm[i]] = v[i];
+  __syncthreads();
+  for (int i = tid; i < nb; i += EST_T) v[i] = tmp[i];
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(EST_T) k_invnorm_est(const T* __restrict__ S, int nb,
+                                                       const int* __restrict__ piv,
+                                                       double* __restrict__ colsum,
+                                                       const int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* v = reinterpret_cast<double*>(smem_raw);   // nb
+  double* z = v + nb;                                  // nb
+  double* tmp = z + nb;                                // nb
+  double* red = tmp + nb;                              // 32
+  int* perm = reinterpret_cast<int*>(red + 32);        // nb
+  int* redi = perm + nb;                               // 32
+  signed char* xi = reinterpret_cast<signed char*>(redi + 32);   // nb
+  const int tid = threadIdx.x;
+  if (status[ST_ZERO_ROW] >= 0) {
+    for (int c = tid; c < nb; c += EST_T) colsum[c] = INFINITY;
+    return;
+  }
+  if (tid == 0) {
+    for (int i = 0; i < nb; ++i) perm[i] = i;
+    for (int r = 0; r < nb; ++r) {
+      const int p = piv[r];
+      if (p != r) { const int t = perm[r]; perm[r] = perm[p]; perm[p] = t; }
+    }
+  }
+  for (int i = tid; i < nb; i += EST_T) v[i] = 1.0 / nb;
+  __syncthreads();
+  est_solve<T>(S, nb, v, tmp, perm);
+  double part = 0.0;
+  for (int i = tid; i < nb; i += EST_T) part += fabs(v[i]);
+  double est = est_block_sum(part, red);
+  for (int i = tid; i < nb; i += EST_T) {
+    xi[i] = v[i] >= 0.0 ? 1 : -1;
+    z[i] = v[i] >= 0.0 ? 1.0 : -1.0;
+  }
+  __syncthreads();
+  est_solve_t<T>(S, nb, z, tmp, perm);
+  int j = est_block_argmax(z, nb, red, redi);
+  for (int it = 2;; ++it) {
+    for (int i = tid; i < nb; i += EST_T) v[i] = (i == j) ? 1.0 : 0.0;
+    __syncthreads();
+    est_solve<T>(S, nb, v, tmp, perm);
+    part = 0.0;
+    bool same = true;
+    for (int i = tid; i < nb; i += EST_T) {
+      part += fabs(v[i]);
+      same = same && ((v[i] >= 0.0 ? 1 : -1) == xi[i]);
+    }
+    const double est_old = est;
+    est = est_block_sum(part, red);
+    const bool all_same = __syncthreads_and(same ? 1 : 0) != 0;
+    if (all_same || est <= est_old) break;
+    for (int i = tid; i < nb; i += EST_T) {
+      xi[i] = v[i] >= 0.0 ? 1 : -1;
+      z[i] = v[i] >= 0.0 ? 1.0 : -1.0;
+    }
+    __syncthreads();
+    est_solve_t<T>(S, nb, z, tmp, perm);
+    const int jlast = j;
+    j = est_block_argmax(z, nb, red, redi);
+    if (fabs(z[jlast]) == fabs(z[j]) || it >= 5) break;
+  }
+  for (int i = tid; i < nb; i += EST_T)
+    v[i] = ((i & 1) ? -1.0 : 1.0) * (1.0 + (double)i / (double)(nb - 1));
+  __syncthreads();
+  est_solve<T>(S, nb, v, tmp, perm);
+  part = 0.0;
+  for (int i = tid; i < nb; i += EST_T) part += fabs(v[i]);
+  const double t = 2.0 * est_block_sum(part, red) / (3.0 * nb);
+  if (t > est) est = t;
+  for (int c = tid; c < nb; c += EST_T) colsum[c] = (c == 0) ? est : 0.0;
+}
+
+template <typename T>
+void launch_invnorm_est(const T* S, int nb, const int* piv_s, double* colsum, const int* status,
+                        cudaStream_t s) {
+  const size_t smem = sizeof(double) * (3 * (size_t)nb + 32) + sizeof(int) * ((size_t)nb + 32) +
+                      (size_t)nb;
+  ensure_dyn_smem<k_invnorm_est<T>>(smem);
+  ProfScope ps_("k_invnorm_est", s);
+  k_invnorm_est<T><<<1, EST_T, smem, s>>>(S, nb, piv_s, colsum, status);
+}
+
 // ---------------------------------------------------------------- decision
 __device__ double log2_ratio(double lhs, double rhs) {
   if (rhs == 0.0) return lhs > 0.0 ? INFINITY : (lhs == 0.0 ? 0.0 : -INFINITY);
@@ -497,6 +741,8 @@ void launch_decide(const DecideArgs& a, const T* S, cudaStream_t s) {
                                       cudaStream_t);                                             \
   template void launch_getrf<T>(const T*, int64_t, int, int, T*, int*, int*, cudaStream_t);      \
   template void launch_invnorm<T>(const T*, int, const int*, double*, const int*, cudaStream_t); \
+  template void launch_invnorm_est<T>(const T*, int, const int*, double*, const int*,           \
+                                      cudaStream_t);                                            \
   template void launch_decide<T>(const DecideArgs&, const T*, cudaStream_t);
 INST(double)
 INST(float)

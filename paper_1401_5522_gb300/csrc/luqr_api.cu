@@ -22,6 +22,7 @@ using namespace luqr;
 struct luqr_handle {
   int64_t N = 0, Npad = 0, Wc = 0;
   int nb = 0, n = 0, prec = 0, criterion = 0, tree = 0, group = 4, mumps_mode = 0;
+  int norm_mode = 0;   // 0 exact ||A_kk^-1||_1, 1 Hager-Higham estimate
   double alpha = 0.0;
   bool has_rhs = false;
   cudaStream_t stream = nullptr;
@@ -383,7 +384,10 @@ void enqueue_factor(luqr_handle* h) {
       cudaEventRecord(h->ev_spec[k], sp);
     }
     launch_getrf<T>(W, ld, k, nb, S, h->piv_s, h->status, s);
-    if (need_inv) launch_invnorm<T>(S, nb, h->piv_s, h->colsum, h->status, s);
+    if (need_inv) {
+      if (h->norm_mode == 1) launch_invnorm_est<T>(S, nb, h->piv_s, h->colsum, h->status, s);
+      else launch_invnorm<T>(S, nb, h->piv_s, h->colsum, h->status, s);
+    }
     DecideArgs da{k,        n,         nb,       h->criterion, h->mumps_mode, h->alpha,
                   h->norms + (size_t)k * n, h->colsum, h->local, h->away,     h->forced,
                   h->dec,   h->margin, h->lhs,   h->rhs,       h->status};
@@ -679,6 +683,7 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   if (o.tree < 0 || o.tree > 2 || o.precision < 0 || o.precision > 1) return LUQR_ERR_INVALID;
   if (o.fp32_kernels < 0 || o.fp32_kernels > 2) return LUQR_ERR_INVALID;
   if (o.mumps_mode < 0 || o.mumps_mode > 1 || o.n_inject < 0) return LUQR_ERR_INVALID;
+  if (o.norm_mode < 0 || o.norm_mode > 1) return LUQR_ERR_INVALID;
   if (o.speculate < 0 || o.speculate > 2 || (o.speculate == 1 && !o.mlp_params))
     return LUQR_ERR_INVALID;
   luqr_handle* h = new (std::nothrow) luqr_handle();
@@ -696,6 +701,7 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   h->tree = o.tree;
   h->group = o.group;
   h->mumps_mode = o.mumps_mode;
+  h->norm_mode = o.norm_mode;
   h->stream = static_cast<cudaStream_t>(stream);
   h->injected.assign(h->n, 0);
   for (int q = 0; q < o.n_inject; ++q) {

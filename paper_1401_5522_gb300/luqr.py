@@ -42,7 +42,7 @@ class Options(ctypes.Structure):
                 ("inject", ctypes.POINTER(ctypes.c_int)), ("n_inject", ctypes.c_int),
                 ("fp32_kernels", ctypes.c_int), ("speculate", ctypes.c_int),
                 ("log_features", ctypes.c_int), ("mlp_params", ctypes.c_void_p),
-                ("reserved", ctypes.c_int * 8)]
+                ("norm_mode", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 _lib = None
@@ -260,13 +260,18 @@ class Handle:
         self.close()
 
 
+NORM_MODE = {"exact": 0, "estimate": 1}
+
+
 def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
            precision="fp64", mumps_mode=0, forced=None, inject=None, stream=None,
-           fp32_kernels="default", speculate="off", mlp_params=None, log_features=False):
+           fp32_kernels="default", speculate="off", mlp_params=None, log_features=False,
+           norm_mode="exact"):
     """luqr_factor on a column-major float64 CUDA matrix; b (if given) is overwritten by x.
 
     speculate: "off", "mlp" (mlp_params: float32 CUDA tensor of MLP_PARAMS values, kept
-    alive by the caller until the factorization has run) or "repeat"."""
+    alive by the caller until the factorization has run) or "repeat".
+    norm_mode: "exact" ||A_kk^-1||_1 or "estimate" (Hager-Higham)."""
     N = A.shape[0]
     lda = _check_matrix(A)
     crit = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
@@ -275,6 +280,7 @@ def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
     opt.group = int(group)
     opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     opt.mumps_mode = int(mumps_mode)
+    opt.norm_mode = NORM_MODE[norm_mode] if isinstance(norm_mode, str) else int(norm_mode)
     opt.fp32_kernels = {"default": 0, "cuda": 1, "tensor": 2}[fp32_kernels]
     opt.speculate = SPECULATE[speculate] if isinstance(speculate, str) else int(speculate)
     opt.log_features = 1 if log_features else 0

@@ -182,6 +182,40 @@ def test_nonfinite_and_singular_reported():
     assert st == luqr.ERR_SINGULAR and step == 1
 
 
+# --------------------------------------------------- Hager-Higham estimate (norm_mode = 1)
+@pytest.mark.parametrize("precision,crit,alpha", [("fp64", "max", 3000.0), ("fp64", "sum", 20000.0),
+                                                  ("fp32", "max", 3000.0)])
+def test_norm_estimate_matches_oracle(precision, crit, alpha):
+    """The GPU estimator (FP64 arithmetic on the stored factors, blocked solves) against the
+    oracle's: identical decisions, margins to 1e-9 (rounding order of the solves), and
+    never a smaller margin than the exact norm at step 0 (same tile, lower-bound norm)."""
+    N, nb = 1024, 64
+    A = gauss(N, 31)
+    b = A @ np.ones(N)
+    dt = np.float32 if precision == "fp32" else np.float64
+    _, f = O.solve(A, b, nb, ORACLE_CRIT[crit], alpha, dtype=dt, norm_mode=1)
+    luqr = L()
+    h = luqr.factor(cuda_colmajor(A), nb, crit, alpha, precision=precision, norm_mode="estimate")
+    dec, mg = h.decisions()
+    h.close()
+    assert np.array_equal(dec, f.dec)
+    assert set(dec.tolist()) == {0, 1}
+    fin = np.isfinite(f.margin)
+    tol = 1e-9 if precision == "fp64" else 1e-2
+    assert np.all(np.abs(mg[fin] - f.margin[fin]) <= tol)
+    h0 = luqr.factor(cuda_colmajor(A), nb, crit, alpha, precision=precision)
+    _, mg0 = h0.decisions()
+    h0.close()
+    assert mg[0] >= mg0[0] - 1e-9
+
+
+def test_norm_mode_out_of_range_rejected():
+    luqr = L()
+    A = cuda_colmajor(gauss(128, 1))
+    with pytest.raises(luqr.LuqrError):
+        luqr.factor(A, 32, "max", 10.0, norm_mode=2)
+
+
 # --------------------------------------------------- FP32 factorization + FP64 refinement
 def test_fp32_decisions_match_float32_oracle():
     A = gauss(512, 10)
