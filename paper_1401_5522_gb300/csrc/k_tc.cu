@@ -930,16 +930,30 @@ __device__ __forceinline__ void tf_tile(int m, int n, int i0, int j0, int q0, in
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-  for (int qc = q0; qc < q1; qc += TF_Q) {
-    for (int idx = tid; idx < TF_T * TF_Q; idx += 256) {
+  // operands of the next chunk are loaded into registers while this chunk is multiplied
+  constexpr int PER = TF_T * TF_Q / 256;
+  float xr[PER], yr[PER];
+  auto fetch = [&](int qc) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int idx = tid + u * 256;
       const int i = idx % TF_T, q = idx / TF_T;
-      Xs[q * TF_LD + i] = (i0 + i < m && qc + q < q1) ? X(i0 + i, qc + q) : 0.f;
+      xr[u] = (i0 + i < m && qc + q < q1) ? X(i0 + i, qc + q) : 0.f;
+      const int qy = YQ ? idx % TF_Q : idx / TF_T, j = YQ ? idx / TF_Q : idx % TF_T;
+      yr[u] = (j0 + j < n && qc + qy < q1) ? Y(qc + qy, j0 + j) : 0.f;
     }
-    for (int idx = tid; idx < TF_T * TF_Q; idx += 256) {
-      const int q = YQ ? idx % TF_Q : idx / TF_T, j = YQ ? idx / TF_Q : idx % TF_T;
-      Ys[q * TF_LD + j] = (j0 + j < n && qc + q < q1) ? Y(qc + q, j0 + j) : 0.f;
+  };
+  if (q0 < q1) fetch(q0);
+  for (int qc = q0; qc < q1; qc += TF_Q) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int idx = tid + u * 256;
+      Xs[(idx / TF_T) * TF_LD + idx % TF_T] = xr[u];
+      const int qy = YQ ? idx % TF_Q : idx / TF_T, j = YQ ? idx / TF_Q : idx % TF_T;
+      Ys[qy * TF_LD + j] = yr[u];
     }
     __syncthreads();
+    if (qc + TF_Q < q1) fetch(qc + TF_Q);
 #pragma unroll 8
     for (int q = 0; q < TF_Q; ++q) {
       const float4 xa = *reinterpret_cast<const float4*>(&Xs[q * TF_LD + ty * 4]);
