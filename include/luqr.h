@@ -54,7 +54,13 @@ enum { LUQR_DEC_QR = 0, LUQR_DEC_LU = 1, LUQR_DEC_ABORTED = 2 };
 
 /* Robustness criteria (Sec. III).  FORCE_LU is the alpha = infinity limit and
  * FORCE_QR the alpha = 0 limit of Sec. V-B. */
-enum { LUQR_MAX = 0, LUQR_SUM = 1, LUQR_MUMPS = 2, LUQR_FORCE_LU = 3, LUQR_FORCE_QR = 4 };
+enum { LUQR_MAX = 0, LUQR_SUM = 1, LUQR_MUMPS = 2, LUQR_FORCE_LU = 3, LUQR_FORCE_QR = 4,
+       LUQR_RANDOM = 5 };
+/* LUQR_RANDOM: the random choice of Sec. V-B (Fig. 2, fourth row): step k is LU with
+ * probability alpha/100 (alpha in percent; alpha >= 100 always LU), drawn as
+ * u_k = (SplitMix64 output k of the stream seeded with opt->seed >> 11) * 2^-53 and
+ * LU iff u_k < alpha/100; a zero pivot in the diagonal GETRF still selects QR.  The
+ * margin is log2((alpha/100) / u_k). */
 
 /* QR elimination trees (Alg. 3: the eliminator of each tile is free). */
 enum {
@@ -99,7 +105,8 @@ typedef struct luqr_options {
                               estimate; a lower bound of the exact norm, so LU is admitted at
                               least as often).  luqr_factor only (the batched solver
                               returns LUQR_ERR_INVALID for 1). */
-  int reserved[7];
+  uint64_t seed;           /* LUQR_RANDOM: SplitMix64 seed of the per-step draws */
+  int reserved[4];
 } luqr_options;
 
 typedef struct luqr_handle* luqr_handle_t;
@@ -110,7 +117,7 @@ typedef struct luqr_handle* luqr_handle_t;
  *   db        device FP64 vector of length N or NULL.  When given, b is carried as an
  *             augmented column through every step (Sec. II-D) and, after the N x N
  *             triangular solve, overwritten in place with the solution x.
- *   criterion LUQR_MAX / SUM / MUMPS / FORCE_LU / FORCE_QR; alpha >= 0 (may be +inf).
+ *   criterion LUQR_MAX / SUM / MUMPS / FORCE_LU / FORCE_QR / RANDOM; alpha >= 0 (may be +inf).
  *             alpha = 0 selects QR at every step.
  *   opt       may be NULL.
  *   stream    CUDA stream; all work is enqueued, nothing is synchronised.

@@ -44,6 +44,24 @@ CRIT_SUM = 1       # Eq. 3
 CRIT_MUMPS = 2     # Eq. 4
 CRIT_FORCE_LU = 3  # alpha = infinity limit (Sec. V-B, "LU NoPiv" inside the tile)
 CRIT_FORCE_QR = 4  # alpha = 0 limit (Sec. V-B)
+CRIT_RANDOM = 5    # random choice, LU with probability alpha/100 (Sec. V-B, Fig. 2 fourth row)
+
+_M64 = (1 << 64) - 1
+
+
+def splitmix64_at(seed, i):
+    """Output i (0-based) of the SplitMix64 generator started at state `seed` (Steele, Lea
+    and Flood 2014): the state advances by 0x9E3779B97F4A7C15 per output, and each output
+    is the state mixed by two xor-shift-multiply rounds and a final xor-shift."""
+    z = (seed + (i + 1) * 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def random_draw(seed, k):
+    """u_k in [0, 1): the top 53 bits of SplitMix64 output k, times 2^-53 (exact)."""
+    return float(splitmix64_at(seed, k) >> 11) * 2.0 ** -53
 
 TREE_FLAT_TS = 0   # eliminator(i,k) = k, Alg. 4(a)
 TREE_BINARY_TT = 1  # pairwise binary reduction, Alg. 4(b)
@@ -376,7 +394,7 @@ class StepDecision:
 
 
 def decide(criterion, alpha, LU, piv, zero_row, norms_below, local_max, away_max,
-           mumps_mode=0, norm_mode=0):
+           mumps_mode=0, norm_mode=0, seed=0, k=0):
     """Robustness test of Sec. III.
 
     Max (Eq. 2):   alpha * (1/||A_kk^-1||_1) >= max_{i>k} ||A_ik||_1
@@ -390,6 +408,10 @@ def decide(criterion, alpha, LU, piv, zero_row, norms_below, local_max, away_max
         return StepDecision(DEC_QR, -math.inf)
     if zero_row >= 0:
         return StepDecision(DEC_QR, -math.inf, 0.0)
+    if criterion == CRIT_RANDOM:
+        lhs = alpha / 100.0
+        rhs = random_draw(seed, k)
+        return StepDecision(DEC_LU if rhs < lhs else DEC_QR, _log2_ratio(lhs, rhs), lhs, rhs)
     if criterion in (CRIT_MAX, CRIT_SUM):
         inv = inv_norm1(LU, piv) if norm_mode == 0 else inv_norm1_est(LU, piv)
         lhs = alpha * (1.0 / inv)
@@ -534,7 +556,7 @@ def tile_bounds(i, nb, N):
 
 def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
            forced=None, inject=(), dtype=np.float64, track_growth=False, on_step=None,
-           norm_mode=0):
+           norm_mode=0, seed=0):
     """Run Alg. 1 on the augmented matrix [A | b] and return the Factorization.
 
     A: N x N; b: None, N or N x nrhs.  dtype float32 emulates the whole factorization
@@ -543,6 +565,7 @@ def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
     ``inject``: steps whose tile row is scaled by 2^-27 before the criterion.
     ``on_step(k, aug_before, fact)``: test hook called before each step.
     ``norm_mode``: 0 exact ||A_kk^-1||_1, 1 the Hager-Higham estimate (inv_norm1_est).
+    ``seed``: SplitMix64 seed of CRIT_RANDOM's per-step draws.
     """
     A = np.asarray(A)
     N = A.shape[0]
@@ -598,7 +621,7 @@ def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
             sd = StepDecision(d, math.inf if d == DEC_LU else -math.inf)
         else:
             sd = decide(criterion, alpha, LU, piv, zero_row, norms[1:], local_max,
-                        away_max, mumps_mode, norm_mode)
+                        away_max, mumps_mode, norm_mode, seed, k)
         if sd.dec == DEC_LU and zero_row >= 0:
             raise Singular(k, r0 + zero_row)
         fact.dec[k] = sd.dec

@@ -131,6 +131,7 @@ struct DecideArgs {
   double* lhs;
   double* rhs;
   int* status;
+  unsigned long long seed;           // LUQR_RANDOM draws
 };
 template <typename T>
 void launch_decide(const DecideArgs& a, const T* S, cudaStream_t s);

@@ -652,8 +652,20 @@ __device__ double log2_ratio(double lhs, double rhs) {
   return log2(lhs / rhs);
 }
 
+// Output i (0-based) of the SplitMix64 generator whose state starts at `seed` (Steele, Lea
+// and Flood, 2014): state advanced by the golden-ratio increment, then two xor-shift /
+// multiply rounds and a final xor-shift.
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed,
+                                                           unsigned long long i) {
+  unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 // Single thread: Eq. 2 (Max), Eq. 3 (Sum), Eq. 4 (MUMPS) with the readings listed in the
-// oracle (">=" selects LU, alpha = 0 or a zero pivot selects QR, last step compares to 0).
+// oracle (">=" selects LU, alpha = 0 or a zero pivot selects QR, last step compares to 0),
+// and the random choice of Sec. V-B (LU with probability alpha/100).
 template <typename T>
 __global__ void k_decide(DecideArgs a, const T* __restrict__ S) {
   if (threadIdx.x != 0) return;
@@ -678,6 +690,11 @@ __global__ void k_decide(DecideArgs a, const T* __restrict__ S) {
     d = DEC_QR; mg = -INFINITY;
   } else if (zr >= 0) {
     d = DEC_QR; mg = -INFINITY; L = 0.0;
+  } else if (crit == 5) {
+    L = a.alpha / 100.0;
+    R = (double)(splitmix64_at(a.seed, (unsigned long long)k) >> 11) * 0x1.0p-53;
+    d = (R < L) ? DEC_LU : DEC_QR;
+    mg = log2_ratio(L, R);
   } else if (crit == 0 || crit == 1) {
     double inv = 0.0;
     for (int c = 0; c < a.nb; ++c) inv = fmax(inv, a.colsum[c]);

@@ -23,6 +23,7 @@ struct luqr_handle {
   int64_t N = 0, Npad = 0, Wc = 0;
   int nb = 0, n = 0, prec = 0, criterion = 0, tree = 0, group = 4, mumps_mode = 0;
   int norm_mode = 0;   // 0 exact ||A_kk^-1||_1, 1 Hager-Higham estimate
+  unsigned long long seed = 0;   // LUQR_RANDOM
   double alpha = 0.0;
   bool has_rhs = false;
   cudaStream_t stream = nullptr;
@@ -391,6 +392,7 @@ void enqueue_factor(luqr_handle* h) {
     DecideArgs da{k,        n,         nb,       h->criterion, h->mumps_mode, h->alpha,
                   h->norms + (size_t)k * n, h->colsum, h->local, h->away,     h->forced,
                   h->dec,   h->margin, h->lhs,   h->rhs,       h->status};
+    da.seed = h->seed;
     launch_decide<T>(da, S, s);
     if (spec) launch_spec_resolve(k, h->dec, h->spec, h->qrfac, h->cmt, s);
     // ---- factor the panel: LU (Alg. 2: commit + TRSM) or QR (GEQRT + TS/TT chain)
@@ -679,7 +681,7 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   if (o.group <= 0) o.group = 4;
   if (!dA || N < 1 || nb < 32 || nb > 512 || (nb % 32) != 0 || lda < N) return LUQR_ERR_INVALID;
   if (!(alpha >= 0.0)) return LUQR_ERR_INVALID;   // rejects NaN too
-  if (criterion < LUQR_MAX || criterion > LUQR_FORCE_QR) return LUQR_ERR_INVALID;
+  if (criterion < LUQR_MAX || criterion > LUQR_RANDOM) return LUQR_ERR_INVALID;
   if (o.tree < 0 || o.tree > 2 || o.precision < 0 || o.precision > 1) return LUQR_ERR_INVALID;
   if (o.fp32_kernels < 0 || o.fp32_kernels > 2) return LUQR_ERR_INVALID;
   if (o.mumps_mode < 0 || o.mumps_mode > 1 || o.n_inject < 0) return LUQR_ERR_INVALID;
@@ -702,6 +704,7 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   h->group = o.group;
   h->mumps_mode = o.mumps_mode;
   h->norm_mode = o.norm_mode;
+  h->seed = o.seed;
   h->stream = static_cast<cudaStream_t>(stream);
   h->injected.assign(h->n, 0);
   for (int q = 0; q < o.n_inject; ++q) {

@@ -22,7 +22,9 @@ MAX, SUM, MUMPS, FORCE_LU, FORCE_QR = 0, 1, 2, 3, 4
 TREE_FLAT_TS, TREE_BINARY_TT, TREE_GROUPED = 0, 1, 2
 PREC_FP64, PREC_FP32 = 0, 1
 
-CRITERIA = {"max": MAX, "sum": SUM, "mumps": MUMPS, "force_lu": FORCE_LU, "force_qr": FORCE_QR}
+RANDOM = 5
+CRITERIA = {"max": MAX, "sum": SUM, "mumps": MUMPS, "force_lu": FORCE_LU, "force_qr": FORCE_QR,
+            "random": RANDOM}
 TREES = {"flat_ts": TREE_FLAT_TS, "binary_tt": TREE_BINARY_TT, "grouped": TREE_GROUPED}
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32}
 SPECULATE = {"off": 0, "mlp": 1, "repeat": 2}
@@ -42,7 +44,8 @@ class Options(ctypes.Structure):
                 ("inject", ctypes.POINTER(ctypes.c_int)), ("n_inject", ctypes.c_int),
                 ("fp32_kernels", ctypes.c_int), ("speculate", ctypes.c_int),
                 ("log_features", ctypes.c_int), ("mlp_params", ctypes.c_void_p),
-                ("norm_mode", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("norm_mode", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("reserved", ctypes.c_int * 4)]
 
 
 _lib = None
@@ -266,12 +269,13 @@ NORM_MODE = {"exact": 0, "estimate": 1}
 def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
            precision="fp64", mumps_mode=0, forced=None, inject=None, stream=None,
            fp32_kernels="default", speculate="off", mlp_params=None, log_features=False,
-           norm_mode="exact"):
+           norm_mode="exact", seed=0):
     """luqr_factor on a column-major float64 CUDA matrix; b (if given) is overwritten by x.
 
     speculate: "off", "mlp" (mlp_params: float32 CUDA tensor of MLP_PARAMS values, kept
     alive by the caller until the factorization has run) or "repeat".
-    norm_mode: "exact" ||A_kk^-1||_1 or "estimate" (Hager-Higham)."""
+    norm_mode: "exact" ||A_kk^-1||_1 or "estimate" (Hager-Higham).
+    criterion "random": LU with probability alpha/100 per step (SplitMix64 draws from seed)."""
     N = A.shape[0]
     lda = _check_matrix(A)
     crit = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
@@ -281,6 +285,7 @@ def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
     opt.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     opt.mumps_mode = int(mumps_mode)
     opt.norm_mode = NORM_MODE[norm_mode] if isinstance(norm_mode, str) else int(norm_mode)
+    opt.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     opt.fp32_kernels = {"default": 0, "cuda": 1, "tensor": 2}[fp32_kernels]
     opt.speculate = SPECULATE[speculate] if isinstance(speculate, str) else int(speculate)
     opt.log_features = 1 if log_features else 0

@@ -209,6 +209,24 @@ def test_norm_estimate_matches_oracle(precision, crit, alpha):
     assert mg[0] >= mg0[0] - 1e-9
 
 
+@pytest.mark.parametrize("seed", [0, 17])
+def test_random_criterion_matches_oracle(seed):
+    """Random choice (Sec. V-B): LU with probability alpha/100 per step from SplitMix64
+    draws computed independently on both sides; identical decisions and margins, and a
+    backward error within the LU-step bar."""
+    N, nb = 1024, 64
+    A = gauss(N, 40 + seed)
+    b = A @ np.ones(N)
+    _, f = O.solve(A, b, nb, O.CRIT_RANDOM, 50.0, seed=seed)
+    h, dec, mg, x, st = gpu_solve(A, b, nb, "random", 50.0, seed=seed)
+    h.close()
+    assert st == 0
+    assert np.array_equal(dec, f.dec)
+    assert set(dec.tolist()) == {0, 1}
+    assert np.all(np.abs(mg - f.margin) <= 1e-9)
+    assert O.backward_error(A, x, b) <= 1e-12
+
+
 def test_norm_mode_out_of_range_rejected():
     luqr = L()
     A = cuda_colmajor(gauss(128, 1))
