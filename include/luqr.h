@@ -213,6 +213,15 @@ void luqr_destroy(luqr_handle_t h);
 int luqr_profile(int enable, int reset);
 
 /*
+ * luqr_profile_select - restricts the profiler's CUDA events to the launches whose kernel
+ * name is one of names[0..count) (host strings, copied); the other launches are still
+ * counted by luqr_profile_read, with 0 ms.  count == 0 times every launch again (default).
+ * Keeps the event overhead off a timed run that needs only some kernels' durations.
+ * Returns LUQR_ERR_INVALID for count < 0 or names == NULL with count > 0.
+ */
+int luqr_profile_select(const char* const* names, int count);
+
+/*
  * luqr_profile_trace - the launch timeline recorded while luqr_profile(2, .) (trace mode)
  * was on: for up to cap launches, in the order they were enqueued, the kernel's name
  * (static string owned by the library), start and end in milliseconds since trace mode

@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <map>
 #include <mutex>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -27,6 +28,7 @@ struct TraceRec {
   cudaStream_t s;
 };
 bool g_trace = false;
+std::set<std::string> g_select;   // when non-empty, only these kernels get events
 cudaEvent_t g_base = nullptr;
 std::vector<TraceRec> g_trace_recs;
 constexpr size_t kMaxTrace = 4u << 20;
@@ -83,6 +85,11 @@ void prof_begin(const char* name, cudaStream_t s) {
   } else {
     id = it->second;
   }
+  if (!g_select.empty() && g_select.count(g_names[id]) == 0) {
+    g_launches[id] += 1;   // counted, not timed
+    t_open = -1;
+    return;
+  }
   if (g_recs.size() >= 200000) drain_locked();   // bound the number of live events
   Rec r{id, take_event(), take_event(), s};
   cudaEventRecord(r.e0, s);
@@ -116,6 +123,15 @@ extern "C" int luqr_profile(int enable, int reset) {
   }
   luqr::g_trace = enable == 2;
   luqr::g_enabled = enable != 0;
+  return LUQR_OK;
+}
+
+extern "C" int luqr_profile_select(const char* const* names, int count) {
+  std::lock_guard<std::mutex> lk(luqr::g_mtx);
+  if (count < 0 || (count > 0 && names == nullptr)) return LUQR_ERR_INVALID;
+  luqr::g_select.clear();
+  for (int i = 0; i < count; ++i)
+    if (names[i]) luqr::g_select.insert(names[i]);
   return LUQR_OK;
 }
 

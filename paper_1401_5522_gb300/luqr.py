@@ -74,6 +74,7 @@ _SIGS = {
     "luqr_profile": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "luqr_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    "luqr_profile_select": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.c_int]),
     "luqr_profile_trace": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_float),
                                           ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint64),
                                           _I64]),
@@ -330,6 +331,16 @@ def profile(enable=True, reset=True, trace=False):
     st = lib().luqr_profile(mode, 1 if reset else 0)
     if st != OK:
         raise LuqrError(st, "luqr_profile")
+    return st
+
+
+def profile_select(names=None):
+    """Time only the launches of these kernel names (others are counted); None: all."""
+    names = list(names or [])
+    arr = (ctypes.c_char_p * max(len(names), 1))(*[n.encode() for n in names])
+    st = lib().luqr_profile_select(arr, len(names))
+    if st != OK:
+        raise LuqrError(st, "luqr_profile_select")
     return st
 
 
