@@ -46,3 +46,21 @@ def test_profile_counts_and_trace_agree():
 def test_profile_rejects_bad_mode():
     from paper_1401_5522_gb300 import luqr
     assert luqr.lib().luqr_profile(3, 0) == luqr.ERR_INVALID
+
+
+def test_profile_select_times_only_named_kernels():
+    from paper_1401_5522_gb300 import luqr
+    A = inputs.gaussian(512, 4, device="cuda")
+    luqr.profile(True, True)
+    try:
+        luqr.profile_select(["k_getrf"])
+        h = luqr.factor(A, 64, "max", 100.0)
+        h.sync()
+        h.close()
+        sel = luqr.profile_read()
+    finally:
+        luqr.profile_select(None)
+        luqr.profile(False, True)
+    assert sel["k_getrf"][0] == 512 // 64 and sel["k_getrf"][1] > 0.0
+    others = {k: v for k, v in sel.items() if k != "k_getrf"}
+    assert others and all(v[0] > 0 and v[1] == 0.0 for v in others.values())
