@@ -22,9 +22,11 @@ factor), pivots are searched with a plain arg-max, and the triangular solves are
 scalar loops, so that every kernel can be checked against its textbook definition
 by eye.  Readings of points the paper leaves open are listed in ``READINGS``.
 
-Parity status: every function here is pinned by tests/test_oracle_*.py except the
-MUMPS criterion at sizes above the hand-worked 2x2-tile example ("parity unpinned"
-beyond that example: the paper prints no MUMPS numbers to pin it to).
+Parity status: every function here is pinned by tests/test_oracle_*.py.  The MUMPS
+criterion is pinned to the closed forms of both readings (default: LU iff alpha >=
+max_j away(j)/local(j); cumulative: a log-domain prefix-sum threshold) and to a
+hand-worked 2x2-tile example; which reading the paper intends stays open, because it
+prints no MUMPS numbers (only alpha = 2.1).
 """
 from __future__ import annotations
 

@@ -306,3 +306,43 @@ def test_table2_metric_arithmetic():
         if name.startswith("LUQR") or name == "HQR":
             assert abs(O.true_gflops(N, t, plu / 100.0) / true - 1) < 3e-3, name
         assert abs(100 * fake / peak - fpk) < 0.1, name   # printed to 0.1%
+
+
+def _mumps_case(seed, p=16):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((p, p))
+    local = np.max(np.abs(A), axis=0)
+    away = rng.uniform(0.2, 3.0, p) * local          # column maxima of the tiles below
+    LU = A.copy()
+    piv, zr = O.getrf(LU)
+    assert zr < 0
+    return LU, piv, local, away
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_mumps_default_reading_closed_form(seed):
+    """Default reading: est(j) = away(j) pivot(j) / local(j) and LU iff alpha pivot(j) >=
+    est(j) for every j, i.e. LU iff alpha >= max_j away(j) / local(j), with margin
+    min_j log2(alpha local(j) / away(j)).  Alphas sit between the sorted thresholds."""
+    LU, piv, local, away = _mumps_case(seed)
+    thr = np.sort(away / local)
+    for a in np.concatenate([[thr[0] / 2], np.sqrt(thr[:-1] * thr[1:]), [thr[-1] * 2]]):
+        sd = O.decide(O.CRIT_MUMPS, float(a), LU, piv, -1, [1.0], local, away, mumps_mode=0)
+        assert sd.dec == (O.DEC_LU if a >= thr[-1] else O.DEC_QR)
+        assert sd.margin == pytest.approx(float(np.min(np.log2(a * local / away))), abs=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_mumps_cumulative_reading_closed_form(seed):
+    """Cumulative reading: est(j) = away(j) prod_{l<j} pivot(l)/local(l).  In logs, LU iff
+    log alpha >= max_j [log away(j) + sum_{l<j} (log pivot(l) - log local(l)) - log pivot(j)]
+    (prefix sums computed independently of the oracle's running product)."""
+    LU, piv, local, away = _mumps_case(100 + seed)
+    lp = np.log(np.abs(np.diag(LU)))
+    prefix = np.concatenate([[0.0], np.cumsum(lp - np.log(local))[:-1]])
+    t = np.log(away) + prefix - lp
+    tmax = float(np.max(t))
+    for a in (np.exp(tmax - 1.0), np.exp(tmax + 1.0), np.exp(tmax - 0.01), np.exp(tmax + 0.01)):
+        sd = O.decide(O.CRIT_MUMPS, float(a), LU, piv, -1, [1.0], local, away, mumps_mode=1)
+        assert sd.dec == (O.DEC_LU if np.log(a) >= tmax else O.DEC_QR)
+        assert sd.margin == pytest.approx(float(np.min(np.log(a) - t)) / np.log(2.0), abs=1e-9)
