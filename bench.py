@@ -101,7 +101,9 @@ def step_tc_bytes(dec, n, nb, tree, ncols_extra):
     """Algorithmic HBM bytes per tensor-core update kernel for one FP32 factorization:
     every launch reads its B operand and C (when accumulated), writes C, and reads its
     nb x nb FP32 A operand once.  W = V^T C (UNMQR) / W = C1 + V2^T C2 (TT pair);
-    C -= (V T^T) W; C1 -= T^T W; C2 -= (V2 T^T) W; LU: C -= L U."""
+    C -= (V T^T) W; C1 -= T^T W; C2 -= (V2 T^T) W; LU: row k <- X row k (X = L^-1 P, in
+    place) and C -= L U.  The tensor-core kernels update the bulk columns only: tile
+    column k+1 goes through the look-ahead's CUDA-core kernels."""
     out = {}
 
     def add(k, v):
@@ -110,11 +112,13 @@ def step_tc_bytes(dec, n, nb, tree, ncols_extra):
     a_op = 4.0 * nb * nb
     for k in range(n):
         m = n - 1 - k
-        cols = m * nb + ncols_extra
+        cols = (m - 1) * nb + ncols_extra
         if cols <= 0:
             continue
         if dec[k] == 1:
             rows = m * nb
+            if cols >= 64 and nb <= 256:
+                add("k_tc_lu_apply", 8.0 * nb * cols + a_op)
             add("k_tc_lu_gemm", 4.0 * (rows * nb + nb * cols + 2.0 * rows * cols))
             continue
         if tree == "binary_tt":
