@@ -87,3 +87,46 @@ def test_bad_options_rejected(L):
     out = ctypes.c_void_p()
     assert L.luqr_factor(ctypes.c_void_p(0x1000), 64, None, 64, 32, 0, 1.0, ctypes.byref(opt),
                          None, ctypes.byref(out)) == luqr.ERR_INVALID
+
+
+@pytest.mark.parametrize("field,value", [("norm_mode", 2), ("norm_mode", -1), ("speculate", 3),
+                                         ("speculate", 1), ("mumps_mode", 2), ("tree", 3),
+                                         ("precision", 2), ("fp32_kernels", 3)])
+def test_invalid_options_rejected_before_any_device_work(L, field, value):
+    # speculate = 1 without mlp_params is invalid too
+    from paper_1401_5522_gb300 import luqr
+    opt = luqr.Options()
+    setattr(opt, field, value)
+    out = ctypes.c_void_p(123)
+    st = L.luqr_factor(ctypes.c_void_p(0x1000), 100, None, 100, 64, 0, 1.0, ctypes.byref(opt),
+                       None, ctypes.byref(out))
+    assert st == luqr.ERR_INVALID
+    assert not out.value
+
+
+def test_unknown_criterion_after_random_rejected(L):
+    from paper_1401_5522_gb300 import luqr
+    out = ctypes.c_void_p(123)
+    assert L.luqr_factor(ctypes.c_void_p(0x1000), 100, None, 100, 64, luqr.RANDOM + 1, 50.0,
+                         None, None, ctypes.byref(out)) == luqr.ERR_INVALID
+
+
+def test_options_layout_matches_header(L):
+    # the binding's struct mirrors luqr_options: same size as the header's fields imply
+    from paper_1401_5522_gb300 import luqr
+    names = [f[0] for f in luqr.Options._fields_]
+    assert names[-1] == "reserved" and "seed" in names and "norm_mode" in names
+    text = open(os.path.join(ROOT, "include", "luqr.h")).read()
+    body = text[text.index("typedef struct luqr_options {"):text.index("} luqr_options;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b([a-z_0-9]+)\s*(?:\[\d+\])?\s*;", body)
+    assert fields == names
+
+
+def test_profiler_argument_checks(L):
+    from paper_1401_5522_gb300 import luqr
+    assert L.luqr_profile(3, 0) == luqr.ERR_INVALID
+    assert L.luqr_profile(-1, 0) == luqr.ERR_INVALID
+    assert L.luqr_profile_select(None, 1) == luqr.ERR_INVALID
+    assert L.luqr_profile_select(None, -1) == luqr.ERR_INVALID
+    assert L.luqr_profile_select(None, 0) == luqr.OK
