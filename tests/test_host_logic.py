@@ -1,0 +1,43 @@
+"""Host-side logic of the Python package that needs no GPU: folding the feature
+standardisation into the MLP's first layer, the repeat-previous predictor, and the batched
+solver's size buckets."""
+import numpy as np
+
+from oracle import mlp_oracle as M
+from paper_1401_5522_gb300 import batched as Bt
+from paper_1401_5522_gb300 import speculation as S
+
+
+def test_folded_parameters_take_raw_features():
+    rng = np.random.default_rng(0)
+    p = S.init_params(3).astype(np.float64)
+    p[1024:1088] = 0.1 * rng.standard_normal(64)          # nonzero first-layer biases
+    X = rng.standard_normal((50, 16)) * 5.0 + 2.0
+    mu = X.mean(axis=0)
+    sigma = X.std(axis=0)
+    folded = S.fold_standardisation(p, mu, sigma).astype(np.float64)
+    want = M.forward(p, (X - mu) / sigma)
+    got = M.forward(folded, X)
+    assert np.max(np.abs(got - want)) <= 1e-5 * max(1.0, np.max(np.abs(want)))
+
+
+def test_init_params_layout():
+    p = S.init_params(0)
+    assert p.shape == (M.NPARAMS,) and p.dtype == np.float32
+    assert np.all(p[1024:1088] == 0) and p[-1] == 0          # zero biases
+
+
+def test_repeat_previous():
+    out = S.repeat_previous([[0, 1, 1, 0], []])
+    assert out[0].tolist() == [1.0, 0.0, 1.0, 1.0]
+    assert len(out[1]) == 0
+
+
+def test_size_buckets_cover_every_size_once():
+    seen = [Bt.bucket_of(N) for N in range(1, 2049)]
+    assert min(seen) == 0 and max(seen) == len(Bt.BUCKETS) - 1
+    assert all(a <= b for a, b in zip(seen, seen[1:]))      # monotone in N
+    for i, (lo, hi) in enumerate(Bt.BUCKETS):
+        assert Bt.bucket_of(lo) == i and Bt.bucket_of(hi) == i
+    table = {0: 32, 3: 64}
+    assert Bt.nb_for([Bt.BUCKETS[0][0], Bt.BUCKETS[3][1], Bt.BUCKETS[1][0]], table, 48) == [32, 64, 48]
