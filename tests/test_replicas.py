@@ -34,7 +34,9 @@ def _worker(rank, world, port, out):
 def test_job_rate_takes_the_slowest_rank_and_counts_all_work():
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    # the manager's server process is started by spawn as well: a fork of this
+    # (multi-threaded) interpreter may deadlock
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
