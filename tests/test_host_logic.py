@@ -41,3 +41,13 @@ def test_size_buckets_cover_every_size_once():
         assert Bt.bucket_of(lo) == i and Bt.bucket_of(hi) == i
     table = {0: 32, 3: 64}
     assert Bt.nb_for([Bt.BUCKETS[0][0], Bt.BUCKETS[3][1], Bt.BUCKETS[1][0]], table, 48) == [32, 64, 48]
+
+
+def test_bench_defaults_follow_the_measurement_contract():
+    import bench
+    a = bench.parse([])
+    assert a.gpus == 1 and a.impl == "luqr"
+    assert a.warmup >= 3 and a.steps >= 1
+    assert (a.N, a.nb, a.kappa, a.criterion, a.alpha, a.tree) == (32768, 256, 1e5, "max", 100.0,
+                                                                     "binary_tt")
+    assert a.tol == 1e-13 and a.e2e_steps >= 1
