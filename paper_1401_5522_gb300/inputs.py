@@ -14,6 +14,7 @@ Recipes:
 * ``worst_case_max``   the tile form of the growth example of Sec. III-A.
 * ``block_diag_dominant`` random off-diagonal tiles with dominant diagonal tiles (Sec. III-B).
 * ``scale_diag_tiles`` multiplies the diagonal tile of chosen panels by a factor.
+* ``special``       the formula-defined special matrices of Table III.
 
 Matrices are returned as torch tensors whose storage is column-major (stride (1, N)),
 the layout the C interface takes; ``.numpy()`` of such a tensor is the same matrix.
@@ -141,6 +142,44 @@ def block_diag_dominant(n, nb, seed, slack=1.01):
                 tot += float(np.max(np.sum(np.abs(A[i * nb:(i + 1) * nb, cs]), axis=0)))
         A[cs, cs] = np.eye(nb) * (slack * tot)
     return torch.from_numpy(A).t().contiguous().t()
+
+
+SPECIAL = ("house", "parter", "ris", "lehmer", "hilb", "orthogo", "demmel")
+
+
+def special(name, N, seed=0):
+    """Formula-defined special matrices of Table III (1-based i, j), column-major float64:
+
+    house    I - beta v v^T with v ~ N(0, 1) (seeded) and beta = 2 / (v^T v)
+    parter   1 / (i - j + 0.5)                      (Toeplitz; singular values near pi)
+    ris      0.5 / (n - i - j + 1.5)                (Hankel; eigenvalues near -pi/2, pi/2)
+    lehmer   i / j for j >= i, symmetric            (positive definite, tridiagonal inverse)
+    hilb     1 / (i + j - 1)
+    orthogo  sqrt(2 / (n + 1)) sin(i j pi / (n + 1))  (symmetric orthogonal)
+    demmel   D (I + 1e-7 R), D = diag(10^(14 (k - 1) / n)), R ~ U(0, 1) (seeded)
+    """
+    i = np.arange(1, N + 1, dtype=np.float64).reshape(-1, 1)
+    j = np.arange(1, N + 1, dtype=np.float64).reshape(1, -1)
+    rng = np.random.default_rng(seed)
+    if name == "house":
+        v = rng.standard_normal(N)
+        A = np.eye(N) - (2.0 / float(v @ v)) * np.outer(v, v)
+    elif name == "parter":
+        A = 1.0 / (i - j + 0.5)
+    elif name == "ris":
+        A = 0.5 / (N - i - j + 1.5)
+    elif name == "lehmer":
+        A = np.minimum(i, j) / np.maximum(i, j)
+    elif name == "hilb":
+        A = 1.0 / (i + j - 1.0)
+    elif name == "orthogo":
+        A = np.sqrt(2.0 / (N + 1)) * np.sin(i * j * np.pi / (N + 1))
+    elif name == "demmel":
+        d = 10.0 ** (14.0 * np.arange(N) / N)
+        A = d.reshape(-1, 1) * (np.eye(N) + 1e-7 * rng.random((N, N)))
+    else:
+        raise ValueError(f"unknown special matrix {name}")
+    return torch.from_numpy(np.asfortranarray(A)).t().contiguous().t()
 
 
 def choose_panels(n, frac, seed):
