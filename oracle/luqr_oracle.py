@@ -72,7 +72,9 @@ TREE_GROUPED = 2   # flat TS inside groups of g tiles, binary TT across group he
 INJECT_SCALE = 2.0 ** -27   # run-time tile-row scaling used to force a QR step
 
 READINGS = {
-    "pivot": "partial pivoting inside the diagonal tile only; pivot = first row of maximal |a|",
+    "pivot": "partial pivoting inside the diagonal tile only; pivot = first row of maximal |a|; "
+             "domain=d: across tiles k..k+d-1 (Sec. II-B variant), exchanges applied to "
+             "columns k.. only (earlier multipliers stay, as the replay applies steps in order)",
     "inverse_norm": "||A_kk^-1||_1 computed exactly from the L and U factors (X = U^-1 L^-1 P); "
                     "norm_mode=1: the Hager-Higham estimate (a lower bound, so the test admits "
                     "LU at least as often)",
@@ -111,13 +113,15 @@ class Singular(Exception):
 # LU kernels (Alg. 2, Sec. II-A)
 # ---------------------------------------------------------------------------
 def getrf(T):
-    """GETRF: P T = L U with partial pivoting restricted to the tile, in place.
+    """GETRF: P T = L U with partial pivoting over the rows of T, in place.
 
+    T is the diagonal tile (square) or, for the diagonal-domain variant, the stacked
+    tiles of the domain (tall: the pivot search covers every row below).
     Returns (piv, zero_row): piv[r] is the row exchanged with row r at elimination
     step r (0-based LAPACK ipiv convention); zero_row is the first r whose pivot is
     exactly zero (that column is then left unscaled), or -1.
     """
-    p = T.shape[0]
+    p = min(T.shape)
     piv = np.arange(p)
     zero_row = -1
     for r in range(p):
@@ -542,6 +546,7 @@ class Factorization:
     flops: float = 0.0
     growth: list = field(default_factory=list)    # max_{i,j>=k} ||A_ij^(k)||_1 per step
     norms: dict = field(default_factory=dict)     # k -> ||A_ik^(k)||_1, i = k..n-1
+    domain_piv: dict = field(default_factory=dict)  # k -> (tiles, ipiv) of a domain LU step
 
     @property
     def U(self):
@@ -558,7 +563,7 @@ def tile_bounds(i, nb, N):
 
 def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
            forced=None, inject=(), dtype=np.float64, track_growth=False, on_step=None,
-           norm_mode=0, seed=0):
+           norm_mode=0, seed=0, domain=1):
     """Run Alg. 1 on the augmented matrix [A | b] and return the Factorization.
 
     A: N x N; b: None, N or N x nrhs.  dtype float32 emulates the whole factorization
@@ -568,6 +573,11 @@ def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
     ``on_step(k, aug_before, fact)``: test hook called before each step.
     ``norm_mode``: 0 exact ||A_kk^-1||_1, 1 the Hager-Higham estimate (inv_norm1_est).
     ``seed``: SplitMix64 seed of CRIT_RANDOM's per-step draws.
+    ``domain``: tiles of the diagonal domain (Sec. II-B variant): the Factor step pivots
+    across tiles k .. k+domain-1 of the panel (a tall GETRF on a scratch copy); the
+    criterion sees the pivoted panel; an LU step first applies the domain's row
+    exchanges to columns k.. of those rows (and b), then runs Alg. 2 on the pivoted
+    diagonal tile.  1 = pivoting inside the diagonal tile only.
     """
     A = np.asarray(A)
     N = A.shape[0]
@@ -608,15 +618,34 @@ def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
                                    for i in range(k, n) for j in range(k, n)
                                    for (a0, a1) in [tile_bounds(i, nb, N)]
                                    for (c0, c1) in [tile_bounds(j, nb, N)]))
-        Akk = aug[r0:r1, r0:r1]
+        dd = min(max(int(domain), 1), n - k)
+        if dd > 1:
+            # -- factor across the diagonal domain: tall GETRF of a scratch copy of the
+            #    stacked tiles k .. k+dd-1; the criterion sees the pivoted panel
+            q1 = tile_bounds(k + dd - 1, nb, N)[1]
+            S = aug[r0:q1, r0:r1].copy()
+            dpiv, zero_row = getrf(S)
+            panel = aug[r0:N, r0:r1].copy()
+            apply_row_swaps(panel[:q1 - r0], dpiv)
+            norms = [norm1(panel[a0 - r0:a1 - r0]) for i in range(k, n)
+                     for (a0, a1) in [tile_bounds(i, nb, N)]]
+            fact.norms[k] = np.array(norms)
+            Akk = panel[:r1 - r0]
+            LU = S[:r1 - r0].copy()
+            piv = np.arange(r1 - r0)
+            away_src = panel[r1 - r0:]
+        else:
+            Akk = aug[r0:r1, r0:r1]
+            away_src = aug[r1:N, r0:r1]
         local_max = np.max(np.abs(Akk.astype(np.float64)), axis=0)
         if m > 0:
-            away_max = np.max(np.abs(aug[r1:N, r0:r1].astype(np.float64)), axis=0)
+            away_max = np.max(np.abs(away_src.astype(np.float64)), axis=0)
         else:
             away_max = np.zeros(r1 - r0)
-        # -- factor: GETRF of a scratch copy of the diagonal tile (Alg. 1, "Factor")
-        LU = Akk.copy()
-        piv, zero_row = getrf(LU)
+        if dd == 1:
+            # -- factor: GETRF of a scratch copy of the diagonal tile (Alg. 1, "Factor")
+            LU = Akk.copy()
+            piv, zero_row = getrf(LU)
         # -- check (Alg. 1, "Check")
         if forced is not None:
             d = int(forced[k])
@@ -632,6 +661,9 @@ def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
         fact.rhs[k] = sd.rhs
         fact.flops += step_flops(sd.dec, m, nb)
         if sd.dec == DEC_LU:
+            if dd > 1:
+                apply_row_swaps(aug[r0:q1, r0:W], dpiv)
+                fact.domain_piv[k] = (dd, dpiv)
             _lu_step(aug, k, n, nb, N, W, LU, piv)
             fact.piv[k] = piv
         else:
@@ -707,6 +739,9 @@ def apply_transforms(fact, b):
             y[r0:r1] *= aug.dtype.type(INJECT_SCALE)
         if fact.dec[k] == DEC_LU:
             LU = aug[r0:r1, r0:r1]
+            if k in fact.domain_piv:
+                dd, dpiv = fact.domain_piv[k]
+                apply_row_swaps(y[r0:tile_bounds(k + dd - 1, nb, N)[1]], dpiv)
             swptrsm(y[r0:r1], LU, fact.piv[k])
             if r1 < N:
                 y[r1:N] -= aug[r1:N, r0:r1] @ y[r0:r1]
