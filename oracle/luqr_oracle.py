@@ -78,6 +78,8 @@ READINGS = {
     "inverse_norm": "||A_kk^-1||_1 computed exactly from the L and U factors (X = U^-1 L^-1 P); "
                     "norm_mode=1: the Hager-Higham estimate (a lower bound, so the test admits "
                     "LU at least as often)",
+    "lu_variant": "A1 (GETRF of the tile) by default; A2 factors the tile by GEQRT, a zero "
+                  "diagonal entry of R playing the zero pivot's part",
     "tie": ">= in Eq. 2-4 selects LU",
     "zero_pivot": "an exact zero pivot in the diagonal GETRF selects QR (FORCE_LU raises Singular)",
     "alpha_zero": "alpha = 0 selects QR at every step, the last one included",
@@ -320,6 +322,17 @@ def inv_norm1(LU, piv):
     return norm1(X)
 
 
+def inv_norm1_qr(QR, tau):
+    """||A_kk^-1||_1 from a GEQRT of the tile (LU variant A2): X = U^-1 Q^T, max column
+    abs sum (float64)."""
+    p = QR.shape[0]
+    Q64 = QR.astype(np.float64)
+    X = np.eye(p)
+    unmqr(Q64, np.asarray(tau, dtype=np.float64), X)
+    upper_solve(Q64, X)
+    return norm1(X)
+
+
 def _solve_t(L64, piv, x):
     """A^-T x for A = P^T L U: U^-T, then L^-T (unit), then P^T (swaps in reverse order)."""
     p = L64.shape[0]
@@ -400,7 +413,7 @@ class StepDecision:
 
 
 def decide(criterion, alpha, LU, piv, zero_row, norms_below, local_max, away_max,
-           mumps_mode=0, norm_mode=0, seed=0, k=0):
+           mumps_mode=0, norm_mode=0, seed=0, k=0, qr_tau=None):
     """Robustness test of Sec. III.
 
     Max (Eq. 2):   alpha * (1/||A_kk^-1||_1) >= max_{i>k} ||A_ik||_1
@@ -419,7 +432,10 @@ def decide(criterion, alpha, LU, piv, zero_row, norms_below, local_max, away_max
         rhs = random_draw(seed, k)
         return StepDecision(DEC_LU if rhs < lhs else DEC_QR, _log2_ratio(lhs, rhs), lhs, rhs)
     if criterion in (CRIT_MAX, CRIT_SUM):
-        inv = inv_norm1(LU, piv) if norm_mode == 0 else inv_norm1_est(LU, piv)
+        if qr_tau is not None:        # LU variant A2: the tile was factored by GEQRT
+            inv = inv_norm1_qr(LU, qr_tau)
+        else:
+            inv = inv_norm1(LU, piv) if norm_mode == 0 else inv_norm1_est(LU, piv)
         lhs = alpha * (1.0 / inv)
         if criterion == CRIT_MAX:
             rhs = max(norms_below) if len(norms_below) else 0.0
@@ -547,6 +563,7 @@ class Factorization:
     growth: list = field(default_factory=list)    # max_{i,j>=k} ||A_ij^(k)||_1 per step
     norms: dict = field(default_factory=dict)     # k -> ||A_ik^(k)||_1, i = k..n-1
     domain_piv: dict = field(default_factory=dict)  # k -> (tiles, ipiv) of a domain LU step
+    lu_tau: dict = field(default_factory=dict)      # k -> tau of an A2 LU step (GEQRT)
 
     @property
     def U(self):
@@ -563,7 +580,7 @@ def tile_bounds(i, nb, N):
 
 def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
            forced=None, inject=(), dtype=np.float64, track_growth=False, on_step=None,
-           norm_mode=0, seed=0, domain=1):
+           norm_mode=0, seed=0, domain=1, lu_variant="A1"):
     """Run Alg. 1 on the augmented matrix [A | b] and return the Factorization.
 
     A: N x N; b: None, N or N x nrhs.  dtype float32 emulates the whole factorization
@@ -578,7 +595,12 @@ def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
     criterion sees the pivoted panel; an LU step first applies the domain's row
     exchanges to columns k.. of those rows (and b), then runs Alg. 2 on the pivoted
     diagonal tile.  1 = pivoting inside the diagonal tile only.
+    ``lu_variant``: "A1" (Alg. 2: GETRF of the tile) or "A2" (Sec. II-B: GEQRT of the
+    tile; Eliminate A_ik U^-1, Apply Q^T A_kj, the same Update; a QR decision continues
+    from that GEQRT).
     """
+    assert lu_variant in ("A1", "A2")
+    assert lu_variant == "A1" or (domain == 1 and norm_mode == 0)
     A = np.asarray(A)
     N = A.shape[0]
     assert A.shape == (N, N) and N >= 1 and nb >= 1
@@ -642,7 +664,15 @@ def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
             away_max = np.max(np.abs(away_src.astype(np.float64)), axis=0)
         else:
             away_max = np.zeros(r1 - r0)
-        if dd == 1:
+        qr_tau = None
+        if dd == 1 and lu_variant == "A2":
+            # -- factor (variant A2): GEQRT of a scratch copy of the diagonal tile
+            LU = Akk.copy()
+            qr_tau = geqrt(LU)
+            piv = np.arange(r1 - r0)
+            zd = np.flatnonzero(np.diag(LU) == 0.0)
+            zero_row = int(zd[0]) if len(zd) else -1
+        elif dd == 1:
             # -- factor: GETRF of a scratch copy of the diagonal tile (Alg. 1, "Factor")
             LU = Akk.copy()
             piv, zero_row = getrf(LU)
@@ -652,7 +682,7 @@ def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
             sd = StepDecision(d, math.inf if d == DEC_LU else -math.inf)
         else:
             sd = decide(criterion, alpha, LU, piv, zero_row, norms[1:], local_max,
-                        away_max, mumps_mode, norm_mode, seed, k)
+                        away_max, mumps_mode, norm_mode, seed, k, qr_tau)
         if sd.dec == DEC_LU and zero_row >= 0:
             raise Singular(k, r0 + zero_row)
         fact.dec[k] = sd.dec
@@ -664,7 +694,11 @@ def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
             if dd > 1:
                 apply_row_swaps(aug[r0:q1, r0:W], dpiv)
                 fact.domain_piv[k] = (dd, dpiv)
-            _lu_step(aug, k, n, nb, N, W, LU, piv)
+            if qr_tau is not None:
+                _lu_step_a2(aug, k, nb, N, W, LU, qr_tau)
+                fact.lu_tau[k] = qr_tau
+            else:
+                _lu_step(aug, k, n, nb, N, W, LU, piv)
             fact.piv[k] = piv
         else:
             ops = elimination_ops(k, n, tree, group)
@@ -683,6 +717,19 @@ def _lu_step(aug, k, n, nb, N, W, LU, piv):
         swptrsm(aug[r0:r1, r1:W], LU, piv)                  # Apply: L^-1 P A_kj (and b_k)
     if r1 < N and r1 < W:
         gemm_update(aug[r1:N, r1:W], aug[r1:N, r0:r1], aug[r0:r1, r1:W])  # Update
+
+
+def _lu_step_a2(aug, k, nb, N, W, QR, tau):
+    """LU step, variant A2 (Sec. II-B): Factor by GEQRT (V below, U on and above the
+    diagonal), Eliminate A_ik U^-1, Apply Q^T A_kj (and b_k), Update as in A1."""
+    r0, r1 = tile_bounds(k, nb, N)
+    aug[r0:r1, r0:r1] = QR
+    if r1 < N:
+        trsm_right_upper(aug[r1:N, r0:r1], QR)
+    if r1 < W:
+        unmqr(QR, tau, aug[r0:r1, r1:W])
+    if r1 < N and r1 < W:
+        gemm_update(aug[r1:N, r1:W], aug[r1:N, r0:r1], aug[r0:r1, r1:W])
 
 
 def _qr_step(aug, k, nb, N, W, ops, taus):
@@ -742,7 +789,10 @@ def apply_transforms(fact, b):
             if k in fact.domain_piv:
                 dd, dpiv = fact.domain_piv[k]
                 apply_row_swaps(y[r0:tile_bounds(k + dd - 1, nb, N)[1]], dpiv)
-            swptrsm(y[r0:r1], LU, fact.piv[k])
+            if k in fact.lu_tau:
+                unmqr(LU, fact.lu_tau[k], y[r0:r1])
+            else:
+                swptrsm(y[r0:r1], LU, fact.piv[k])
             if r1 < N:
                 y[r1:N] -= aug[r1:N, r0:r1] @ y[r0:r1]
         else:
