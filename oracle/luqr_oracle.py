@@ -80,6 +80,9 @@ READINGS = {
                     "LU at least as often)",
     "lu_variant": "A1 (GETRF of the tile) by default; A2 factors the tile by GEQRT, a zero "
                   "diagonal entry of R playing the zero pivot's part",
+    "random_choice": "Sec. V-B's random choice: LU with probability alpha/100, u_k = SplitMix64 "
+                     "output k of the seed, top 53 bits times 2^-53, LU iff u_k < alpha/100; a "
+                     "zero pivot still selects QR",
     "tie": ">= in Eq. 2-4 selects LU",
     "zero_pivot": "an exact zero pivot in the diagonal GETRF selects QR (FORCE_LU raises Singular)",
     "alpha_zero": "alpha = 0 selects QR at every step, the last one included",

@@ -59,3 +59,13 @@ def test_domain_runs_solve_and_replay(crit, alpha):
     b2 = np.random.default_rng(8).standard_normal(N)
     x2 = O.replay_solve(f, b2)
     assert O.backward_error(A, x2, b2) <= 1e-13
+
+
+def test_domain_with_mumps_and_float32_emulation():
+    A = gauss(192, 9)
+    b = A @ np.ones(192)
+    x, f = O.solve(A, b, 32, O.CRIT_MUMPS, 2.1, domain=2)
+    assert O.backward_error(A, x, b) <= 1e-13
+    x32, f32 = O.solve(A, b, 32, O.CRIT_MAX, 3000.0, domain=2, dtype=np.float32)
+    assert O.backward_error(A, x32.astype(np.float64), b) <= 1e-4
+    assert f32.aug.dtype == np.float32
