@@ -319,6 +319,43 @@ int luqr_mlp_adam(float* dparams, const float* dgrad, float* dm, float* dv, int 
                   float beta1, float beta2, float eps, void* stream);
 int luqr_features(luqr_handle_t h, float* feat, uint8_t* predicted, int* n_out);
 
+/*
+ * Batched solver: many independent systems A_i x_i = b_i of uneven order N_i, each solved
+ * by the hybrid method (Alg. 1 with Eq. 2-4, the LU step of Alg. 2, the QR step of Alg. 3
+ * with the flat TS tree of Alg. 4(a), back substitution of the augmented right-hand side,
+ * Sec. II-D) inside ONE persistent launch: each CTA claims the next system from a queue
+ * ordered largest first, copies it into its own padded scratch slot and decides every
+ * step in-kernel.  Not in the paper (its experiments solve one system at a time).
+ *
+ * luqr_batched_create - sets up a batch; nothing runs yet.
+ *   dA        HOST array of `count` DEVICE pointers; dA[i] is column-major FP64 N[i] x N[i]
+ *             with leading dimension N[i]; read only, caller-owned, valid until destroy.
+ *   db        HOST array of `count` DEVICE pointers to FP64 vectors of length N[i]; every
+ *             run overwrites db[i] with x_i.  The batch keeps its own copy of the right-hand
+ *             sides taken at create time, so runs are repeatable.
+ *   N, nb     HOST arrays: order 1 <= N[i] <= 8192 and tile size nb[i] in {32, 64}.
+ *   criterion LUQR_MAX / SUM / MUMPS / FORCE_LU / FORCE_QR (not RANDOM); alpha >= 0.
+ *   opt       may be NULL; uses precision (FP64, or FP32 tiles with FP64 refinement inside
+ *             the kernel) and mumps_mode; norm_mode must be 0; the other fields are ignored.
+ *   tol, max_iter  FP32 mode: refine until eta <= tol, at most max_iter corrections.
+ *   out       receives the batch (device workspace: one slot per resident CTA plus the
+ *             per-system results), owned by the batch until luqr_batched_destroy.
+ * Synchronous (copies the metadata to the device).  Returns LUQR_ERR_INVALID for NULL
+ * arrays, count < 1, a size or tile size outside the limits, a bad criterion, alpha < 0 or
+ * NaN, tol < 0 or max_iter < 0, bad options; LUQR_ERR_NOMEM / LUQR_ERR_CUDA when the
+ * workspace cannot be set up (then *out is NULL).
+ *
+ * luqr_batched_run       - enqueues one solve of every system on `stream` (one launch).
+ * luqr_batched_run_graph - the same through a CUDA graph, captured on a private stream at
+ *                          the first call and replayed on `stream` afterwards.
+ *   Both return LUQR_ERR_INVALID for a NULL batch and LUQR_ERR_CUDA if the launch fails.
+ * luqr_batched_results - synchronises the device, then copies to HOST arrays (any may be
+ *   NULL): dec (count x nmax bytes, row i = system i's decisions LUQR_DEC_*, 255 for steps
+ *   past its last tile), status (count ints, LUQR_OK or LUQR_ERR_*), iters (refinement
+ *   corrections used), eta (normwise backward error per system), *nmax_out (the largest
+ *   tile count).  Returns LUQR_ERR_CUDA if the device reports an error.
+ * luqr_batched_destroy - synchronises the device and frees the batch (NULL: no-op).
+ */
 typedef struct luqr_batched* luqr_batched_t;
 int luqr_batched_create(const double* const* dA, double* const* db, const int* N, const int* nb,
                         int count, int criterion, double alpha, const luqr_options* opt,
