@@ -9,9 +9,12 @@ It is a deliberately slow, step-by-step restatement of the paper's method in
 float64 (or float32 for the emulation of the low-precision factorisation):
 
 * Alg. 1 (hybrid step loop), Eq. 1 (factor / apply / eliminate / update),
-* Alg. 2 (LU step, variant A1: GETRF, TRSM, SWPTRSM, GEMM),
+* Alg. 2 (LU step, variant A1: GETRF, TRSM, SWPTRSM, GEMM) and variant A2 of Sec. II-B
+  (GEQRT of the diagonal tile, TRSM with its U, ORMQR apply, GEMM); the diagonal-domain
+  Factor of Sec. II-B (pivoting across several tiles of the panel),
 * Alg. 3 + Alg. 4(a)/(b) (QR step with TS or TT elimination kernels),
-* Eq. 2 (Max), Eq. 3 (Sum) and Eq. 4 (MUMPS) robustness criteria (Sec. III),
+* Eq. 2 (Max), Eq. 3 (Sum) and Eq. 4 (MUMPS) robustness criteria (Sec. III), with the
+  exact inverse norm or the Hager-Higham estimate, and the random choice of Sec. V-B,
 * Sec. II-D "Solving systems of linear equations": the transformations are applied
   to the augmented matrix (A, b), followed by one N-by-N triangular solve, or
   replayed on a new right-hand side in a second pass,
