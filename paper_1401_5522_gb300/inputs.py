@@ -67,16 +67,20 @@ def _fwht_rows_(M):
 
 
 def _random_signs(N, g, device):
-    return (torch.randint(0, 2, (N,), generator=g, device=device).to(torch.float64) * 2.0 - 1.0)
+    return (torch.randint(0, 2, (N,), generator=g).to(torch.float64) * 2.0 - 1.0).to(device)
 
 
 def conditioned(N, kappa, seed, device="cpu"):
-    """A = U diag(s) V^T, s_i = kappa^(-i/(N-1)), U and V random orthogonal (float64)."""
-    g = _gen(seed, device)
-    i = torch.arange(N, dtype=torch.float64, device=device)
-    s = torch.pow(torch.tensor(float(kappa), dtype=torch.float64, device=device),
-                  -i / max(N - 1, 1))
+    """A = U diag(s) V^T, s_i = kappa^(-i/(N-1)), U and V random orthogonal (float64).
+
+    For N a power of two the random signs and the singular values are drawn on the host
+    and only the exact transforms (sign flips, additions, one scaling per level) run on
+    ``device``, so the matrix is bit-identical on the host and on a GPU."""
     if N >= 2 and (N & (N - 1)) == 0:
+        g = _gen(seed, "cpu")
+        i = torch.arange(N, dtype=torch.float64)
+        s = torch.pow(torch.tensor(float(kappa), dtype=torch.float64), -i / max(N - 1, 1))
+        s = s.to(device)
         # Row-major work array R holds A^T while the transforms are applied:
         # A = U S V^T  <=>  A^T = V S U^T.  Start from S (diagonal), then
         # A^T = V (S U^T): right-multiply by U^T = (H D1 H D2 H D3)^T = D3 H D2 H D1 H,
@@ -96,6 +100,10 @@ def conditioned(N, kappa, seed, device="cpu"):
         Rt.mul_(d[3].view(1, N)); _fwht_rows_(Rt)
         # Rt now holds (V S U^T)^T = U S V^T = A in row-major; return column-major view of A
         return Rt.t().contiguous().t()
+    g = _gen(seed, device)
+    i = torch.arange(N, dtype=torch.float64, device=device)
+    s = torch.pow(torch.tensor(float(kappa), dtype=torch.float64, device=device),
+                  -i / max(N - 1, 1))
     G1 = torch.randn((N, N), generator=g, device=device, dtype=torch.float64)
     G2 = torch.randn((N, N), generator=g, device=device, dtype=torch.float64)
     U = _haar(G1)
