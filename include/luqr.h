@@ -375,14 +375,16 @@ void luqr_batched_destroy(luqr_batched_t b);
  * LU with partial pivoting of a scratch copy of the diagonal tile, exact ||A_kk^-1||_1 and
  * the Max / Sum / MUMPS comparison) without allocating any device memory.  The paper has
  * no counterpart: this entry exists for callers that cannot call cudaMalloc, e.g. code
- * that records a CUDA graph under stream capture (allocation is not allowed there), code
- * confined to a pre-reserved memory budget, or latency-critical paths that must not wait
- * on the allocator.
+ * confined to a pre-reserved memory budget or to a pool that the host application owns,
+ * or latency-critical paths that must not wait on the allocator (which can synchronise
+ * the device).
  *   dpanel    device, column-major FP64 panel of `rows` x nb: the diagonal tile on top,
  *             then the (rows/nb - 1) sub-diagonal tiles; leading dimension ld >= rows.
  *   rows      a multiple of nb, at most LUQR_NOALLOC_MAX_TILES * nb (pad with zero tiles).
  *   nb        multiple of 32 with 32 <= nb <= LUQR_NOALLOC_MAX_NB.
- *   criterion, alpha, mumps_mode  as luqr_factor / luqr_options.
+ *   criterion LUQR_MAX, LUQR_SUM, LUQR_MUMPS, LUQR_FORCE_LU or LUQR_FORCE_QR; LUQR_RANDOM
+ *             is not accepted (its draw needs the step index of a whole factorization) and
+ *             returns LUQR_ERR_INVALID.  alpha >= 0 and mumps_mode (0 or 1) as luqr_factor.
  *   ddec      device uint8: receives LUQR_DEC_LU, LUQR_DEC_QR, or LUQR_DEC_ABORTED when the
  *             panel holds a NaN/Inf or FORCE_LU meets an exact zero pivot.
  *   dmargin   device double: log2(lhs/rhs) of the test (as luqr_decisions).
@@ -393,7 +395,8 @@ void luqr_batched_destroy(luqr_batched_t b);
  * the caller.  The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before any stream
  * capture begins.  Returns LUQR_ERR_INVALID for sizes beyond the limits above or bad
- * arguments, LUQR_ERR_CUDA if the set-up or a launch fails.
+ * arguments, LUQR_ERR_CUDA if the set-up or a launch fails, or if an earlier launch left
+ * a CUDA error pending (the call then runs nothing and leaves that error in place).
  */
 int luqr_panel_test_noalloc(const double* dpanel, int64_t ld, int64_t rows, int nb, int criterion,
                             double alpha, int mumps_mode, uint8_t* ddec, double* dmargin,

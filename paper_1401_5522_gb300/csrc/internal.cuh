@@ -4,6 +4,8 @@
 #include <stdint.h>
 #include <math.h>
 
+#include <mutex>
+
 namespace luqr {
 
 constexpr int IB = 32;              // inner block of the Householder kernels (T is IB x IB per block)
@@ -75,17 +77,29 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// Raises kernel K's dynamic shared-memory limit to `bytes` when a launch needs more
-// than the current limit (one record per kernel instantiation).  The request is the
-// launch's own size, so kernels that also use static shared memory stay within the
+// Raises kernel K's dynamic shared-memory limit to `bytes` when a launch needs more than
+// the limit already set on the current device.  cudaFuncSetAttribute acts on the current
+// device only, so the record is kept per device (up to ENSURE_SMEM_DEVICES; beyond that the
+// attribute is set on every launch), under a lock shared by the host threads.  The request
+// is the launch's own size, so kernels that also use static shared memory stay within the
 // per-block maximum.
+constexpr int ENSURE_SMEM_DEVICES = 64;
 template <auto K>
 inline void ensure_dyn_smem(size_t bytes) {
-  static size_t cur = 48 * 1024;
-  if (bytes > cur) {
-    cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    cur = bytes;
+  static std::mutex mu;
+  static size_t cur[ENSURE_SMEM_DEVICES] = {};   // 0: the 48 KB default
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= ENSURE_SMEM_DEVICES) {
+    if (bytes > 48 * 1024)
+      cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return;
   }
+  std::lock_guard<std::mutex> lk(mu);
+  const size_t have = cur[dev] ? cur[dev] : (size_t)48 * 1024;
+  if (bytes > have &&
+      cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+          cudaSuccess)
+    cur[dev] = bytes;
 }
 
 // ---------------------------------------------------------------- launch profiler

@@ -1,9 +1,8 @@
 // Allocation-free robustness test of one panel.
 //
-// Some callers cannot call cudaMalloc: code recording a CUDA graph with stream capture
-// (allocation calls are not allowed inside a global-mode capture), code running under a
-// strict device-memory budget or a pre-reserved memory pool, and real-time paths that
-// must not block on the allocator.  luqr_panel_test_noalloc gives them the factorization's
+// Some callers cannot call cudaMalloc: code running under a strict device-memory budget
+// or inside a pre-reserved memory pool owned by a host application, and real-time paths
+// that must not block on the allocator (cudaMalloc can synchronise the device).  luqr_panel_test_noalloc gives them the factorization's
 // per-step decision (panel statistics, scratch GETRF of the diagonal tile, exact inverse
 // norm and the Eq. 2-4 comparison) without any device allocation: its scratch lives in a
 // fixed file-scope device array sized for nb <= LUQR_NOALLOC_MAX_NB and panels of at most
@@ -64,6 +63,9 @@ extern "C" int luqr_panel_test_noalloc(const double* dpanel, int64_t ld, int64_t
                                        int criterion, double alpha, int mumps_mode,
                                        uint8_t* ddec, double* dmargin, void* stream) {
   using namespace luqr;
+  // An error left pending by an earlier, unrelated launch is not ours to report or clear:
+  // refuse to run on top of it.
+  if (cudaPeekAtLastError() != cudaSuccess) return LUQR_ERR_CUDA;
   if (!dpanel || !ddec || !dmargin) return LUQR_ERR_INVALID;
   if (nb < 32 || nb > NA_MAX_NB || (nb % 32) != 0) return LUQR_ERR_INVALID;
   if (rows < nb || (rows % nb) != 0 || rows / nb > NA_MAX_TILES || ld < rows) return LUQR_ERR_INVALID;

@@ -388,17 +388,31 @@ def panel_test_noalloc(panel, nb, criterion="max", alpha=100.0, mumps_mode=0, de
                        margin=None, stream=None):
     """Allocation-free robustness test of one panel (rows x nb, column-major float64 CUDA).
 
-    ``dec`` (uint8[1]) and ``margin`` (float64[1]) are caller-provided CUDA tensors that
-    receive the result; the call itself allocates no device memory."""
+    ``dec`` (uint8[1]) and ``margin`` (float64[1]) are caller-provided CUDA tensors on the
+    panel's device that receive the result; the call itself allocates no device memory."""
     import torch
-    if not (panel.is_cuda and panel.dtype == torch.float64 and panel.stride(0) == 1):
-        raise TypeError("panel must be a column-major float64 CUDA matrix")
-    rows = panel.shape[0]
-    ld = max(panel.stride(1), rows) if panel.dim() == 2 and panel.shape[1] > 1 else rows
+    if not (isinstance(panel, torch.Tensor) and panel.is_cuda and panel.dtype == torch.float64
+            and panel.dim() == 2 and panel.stride(0) == 1):
+        raise TypeError("panel must be a 2-D column-major float64 CUDA matrix")
+    rows, cols = panel.shape
+    if cols < nb:
+        raise ValueError(f"panel has {cols} columns, fewer than nb = {nb}")
+    if cols > 1 and panel.stride(1) < rows:
+        raise ValueError("panel's column stride is smaller than its row count")
+    ld = panel.stride(1) if cols > 1 else rows
+    if dec is None or margin is None:
+        raise TypeError("dec (uint8 CUDA[1]) and margin (float64 CUDA[1]) are required")
+    if not (dec.is_cuda and dec.dtype == torch.uint8 and margin.is_cuda and
+            margin.dtype == torch.float64):
+        raise TypeError("dec must be a uint8 and margin a float64 CUDA tensor")
+    if panel.device != dec.device or panel.device != margin.device:
+        raise ValueError("panel, dec and margin must live on the same device")
     crit = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
-    st = lib().luqr_panel_test_noalloc(ctypes.c_void_p(panel.data_ptr()), ld, rows, int(nb), crit,
-                                       float(alpha), int(mumps_mode), ctypes.c_void_p(dec.data_ptr()),
-                                       ctypes.c_void_p(margin.data_ptr()), _stream_ptr(stream))
+    with torch.cuda.device(panel.device):
+        st = lib().luqr_panel_test_noalloc(ctypes.c_void_p(panel.data_ptr()), ld, rows, int(nb),
+                                           crit, float(alpha), int(mumps_mode),
+                                           ctypes.c_void_p(dec.data_ptr()),
+                                           ctypes.c_void_p(margin.data_ptr()), _stream_ptr(stream))
     if st != OK:
         raise LuqrError(st, "luqr_panel_test_noalloc")
     return dec, margin
