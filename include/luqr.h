@@ -147,7 +147,8 @@ int luqr_solve(luqr_handle_t h, double* db, int nrhs, int64_t ldb, void* stream)
  *   max_iter  maximum number of corrections.
  *   iters     (host, nullable) corrections applied; eta (host, nullable) final error.
  * Synchronises the stream once per iteration.  Returns LUQR_ERR_NOT_CONVERGED when
- * tol was not reached (dx still holds the best iterate).
+ * tol was not reached; dx then holds the iterate with the smallest backward error and
+ * *eta that error.
  */
 int luqr_refine(luqr_handle_t h, const double* dA, int64_t lda, const double* db,
                 double* dx, double tol, int max_iter, int* iters, double* eta,
@@ -169,6 +170,16 @@ int luqr_refine(luqr_handle_t h, const double* dA, int64_t lda, const double* db
 int luqr_refine_gmres(luqr_handle_t h, const double* dA, int64_t lda, const double* db,
                       double* dx, double tol, int max_iter, int restart, int* iters, double* eta,
                       void* stream);
+
+/*
+ * luqr_accuracy - accuracy of the solution that the last luqr_refine / luqr_refine_gmres
+ * call returned (Sec. V-A), from the FP64 infinity norms that refinement computed on the
+ * GPU: eta = ||b - A x|| / (||A|| ||x|| + ||b||) (normwise backward error) and
+ * HPL3 = ||A x - b|| / (||A|| ||x|| eps N) with eps = 2^-53.  norms (HOST, nullable)
+ * receives {||A||, ||b - A x||, ||x||, ||b||}.  Any output may be NULL.  Host-only (no
+ * synchronisation).  LUQR_ERR_INVALID before the handle's first refinement.
+ */
+int luqr_accuracy(luqr_handle_t h, double* eta, double* hpl3, double* norms);
 
 /*
  * luqr_decisions - copies the per-step decisions (LUQR_DEC_*) and margins

@@ -84,6 +84,7 @@ struct luqr_handle {
   double* ref = nullptr;    // x, r, scalars, partial sums
   int ref_chunks = 0;
   double* gm = nullptr;     // GMRES: basis (N x (restart+1)), work vector, dot buffers
+  double acc[4] = {NAN, NAN, NAN, NAN};   // last refinement: ||A||, ||r||, ||x||, ||b|| (inf-norms)
   int gm_restart = 0;
   size_t elt = 8;
 };
@@ -563,7 +564,7 @@ int refine_gmres_impl(luqr_handle* h, const double* dA, int64_t lda, const doubl
   if (!h->ref || h->ref_chunks < nchunk) {
     if (h->ref) cudaFree(h->ref);
     h->ref = nullptr;
-    cudaError_t e = cudaMalloc(&h->ref, sizeof(double) * ((size_t)N * (nchunk + 1) + 8));
+    cudaError_t e = cudaMalloc(&h->ref, sizeof(double) * ((size_t)N * (nchunk + 2) + 8));
     if (e != cudaSuccess) return cuda_err(e);
     h->ref_chunks = nchunk;
   }
@@ -659,6 +660,7 @@ int refine_gmres_impl(luqr_handle* h, const double* dA, int64_t lda, const doubl
     if (cudaStreamSynchronize(s) != cudaSuccess) return LUQR_ERR_CUDA;
     e_it = host[1] / (host[0] * host[2] + host[3]);
     best = std::min(best, e_it);
+    std::memcpy(h->acc, host, sizeof(host));
     if (!(e_it > tol) || jend == 0) break;
   }
   if (iters) *iters = total;
@@ -864,13 +866,14 @@ int luqr_refine(luqr_handle_t h, const double* dA, int64_t lda, const double* db
   if (!h->ref || h->ref_chunks < nchunk) {
     if (h->ref) cudaFree(h->ref);
     h->ref = nullptr;
-    cudaError_t e = cudaMalloc(&h->ref, sizeof(double) * ((size_t)N * (nchunk + 1) + 8));
+    cudaError_t e = cudaMalloc(&h->ref, sizeof(double) * ((size_t)N * (nchunk + 2) + 8));
     if (e != cudaSuccess) return cuda_err(e);
     h->ref_chunks = nchunk;
   }
   double* r = h->ref;
   double* partial = r + N;
   double* scal = partial + (size_t)N * nchunk;   // [0] ||A||, [1] ||r||, [2] ||x||, [3] ||b||
+  double* xbest = scal + 8;                       // best iterate so far (N)
   int st = ensure_rhs(h, 1);
   if (st) return st;
   launch_row_abs_sum_max(dA, lda, N, partial, nchunk, scal + 0, s);
@@ -896,7 +899,11 @@ int luqr_refine(luqr_handle_t h, const double* dA, int64_t lda, const double* db
     cudaMemcpyAsync(host, scal, sizeof(host), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return LUQR_ERR_CUDA;
     const double e_it = host[1] / (host[0] * host[2] + host[3]);
-    best = std::min(best, e_it);
+    if (e_it < best) {
+      best = e_it;
+      cudaMemcpyAsync(xbest, dx, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+      std::memcpy(h->acc, host, sizeof(host));
+    }
     if (!(e_it > tol)) {
       if (iters) *iters = it + 1;
       if (eta) *eta = e_it;
@@ -904,6 +911,9 @@ int luqr_refine(luqr_handle_t h, const double* dA, int64_t lda, const double* db
       return code ? code : LUQR_OK;
     }
   }
+  // not converged: hand back the best iterate and its error
+  if (std::isfinite(best))
+    cudaMemcpyAsync(dx, xbest, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
   if (iters) *iters = it;
   if (eta) *eta = best;
   int code = read_status(h, nullptr);
@@ -919,6 +929,16 @@ int luqr_refine_gmres(luqr_handle_t h, const double* dA, int64_t lda, const doub
   if (h->prec == LUQR_PREC_FP64)
     return refine_gmres_impl<double>(h, dA, lda, db, dx, tol, max_iter, restart, iters, eta);
   return refine_gmres_impl<float>(h, dA, lda, db, dx, tol, max_iter, restart, iters, eta);
+}
+
+int luqr_accuracy(luqr_handle_t h, double* eta, double* hpl3, double* norms) {
+  if (!h) return LUQR_ERR_INVALID;
+  if (!std::isfinite(h->acc[0])) return LUQR_ERR_INVALID;   // no refinement has run
+  const double nA = h->acc[0], nr = h->acc[1], nx = h->acc[2], nb = h->acc[3];
+  if (eta) *eta = nr / (nA * nx + nb);
+  if (hpl3) *hpl3 = nr / (nA * nx * std::ldexp(1.0, -53) * (double)h->N);
+  if (norms) std::memcpy(norms, h->acc, sizeof(h->acc));
+  return LUQR_OK;
 }
 
 int luqr_features(luqr_handle_t h, float* feat, uint8_t* predicted, int* n_out) {

@@ -63,6 +63,7 @@ _SIGS = {
                                          ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_double), _P]),
     "luqr_decisions": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
+    "luqr_accuracy": (ctypes.c_int, [_P, _P, _P, _P]),
     "luqr_step_stats": (ctypes.c_int, [_P, _P, _P]),
     "luqr_factor_data": (ctypes.c_int, [_P, _P, _I64]),
     "luqr_sync": (ctypes.c_int, [_P]),
@@ -176,6 +177,18 @@ class Handle:
         if st != OK:
             raise LuqrError(st, "luqr_features")
         return feat, pred
+
+    def accuracy(self):
+        """(eta, HPL3, norms[4]) of the last refinement's solution (Sec. V-A), computed by the
+        library from its FP64 GPU norms {||A||, ||b - A x||, ||x||, ||b||}."""
+        eta = ctypes.c_double()
+        hpl3 = ctypes.c_double()
+        norms = np.zeros(4)
+        st = lib().luqr_accuracy(self._ptr(), ctypes.byref(eta), ctypes.byref(hpl3),
+                                 norms.ctypes.data_as(_P))
+        if st != OK:
+            raise LuqrError(st, "luqr_accuracy")
+        return eta.value, hpl3.value, norms
 
     def step_stats(self):
         lhs = np.zeros(self.n)

@@ -65,3 +65,34 @@ def test_step_features_hand_computed():
     f0 = M.step_features(0, 3, np.inf, 0, [3.0, 1.0], A, [1.0] * 4, [], [])
     assert f0[6] == 64.0 and f0[8] == 0.5 and f0[12] == 64.0 and f0[15] == 0.0
     assert abs(f0[7] - 16.0) < 1e-15        # mean of 0, 64, 0, 0
+
+
+def test_forward_of_a_hand_computed_sparse_network():
+    """A network with a few non-zero weights, evaluated by hand.  Row = output unit in W1
+    and W2, so a transposed W2 or a missing ReLU changes the logits below.
+      x = (1, 0, 4, 0.5, 0...):  h1_0 = relu(2*1 - 0.5 + 0.5) = 2,  h1_1 = relu(4 - 3) = 1,
+        h2_0 = relu(1.5*2 - 2*1 + 0.25) = 1.25,  h2_5 = relu(1*1) = 1,
+        logit = 3*1.25 - 0.5*1 + 0.1 = 3.35
+      x = (-1, 0, 1, 0, 0...):  h1_0 = relu(-2 + 0.5) = 0,  h1_1 = relu(1 - 3) = 0,
+        h2_0 = relu(0.25) = 0.25,  h2_5 = 0,  logit = 3*0.25 + 0.1 = 0.85"""
+    p = np.zeros(M.NPARAMS)
+    q = M.unpack(np.arange(M.NPARAMS, dtype=float))          # offsets of every entry
+    def at(name, *idx):
+        return int(q[name][idx] if idx else q[name])
+    p[at("W1", 0, 0)] = 2.0
+    p[at("W1", 0, 3)] = -1.0
+    p[at("b1", 0)] = 0.5
+    p[at("W1", 1, 2)] = 1.0
+    p[at("b1", 1)] = -3.0
+    p[at("W2", 0, 0)] = 1.5
+    p[at("W2", 0, 1)] = -2.0
+    p[at("b2", 0)] = 0.25
+    p[at("W2", 5, 1)] = 1.0
+    p[at("W3", 0)] = 3.0
+    p[at("W3", 5)] = -0.5
+    p[at("b3", 0)] = 0.1
+    X = np.zeros((2, M.F))
+    X[0, [0, 2, 3]] = [1.0, 4.0, 0.5]
+    X[1, [0, 2]] = [-1.0, 1.0]
+    z = M.forward(p, X)
+    assert abs(z[0] - 3.35) < 1e-14 and abs(z[1] - 0.85) < 1e-14, z
