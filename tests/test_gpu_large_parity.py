@@ -1,0 +1,140 @@
+"""GPU decision sequences at the benchmarked sizes against the oracle's.
+
+The oracle runs for N = 16384 and N = 32768 take minutes each on the host cores, so their
+decisions, margins and criterion values are stored in tests/golden/large_*.json, written
+by tests/golden/make_large.py (which calls only the oracle and the input recipes).  Each
+test rebuilds the input from the same seeded recipe on the host, checks it against the
+stored fingerprint, runs the GPU solver through the C interface with the same options in
+the launch configuration the benchmark uses, and compares:
+
+* decisions: identical at every step (FP64); FP32 runs against the float32 oracle:
+  identical at every step whose oracle margin is farther than the FP32 bar from a tie, and
+  no step may be that close (a near-tie would make the comparison meaningless, so it fails
+  loudly rather than passing silently);
+* margins log2(lhs/rhs): within TOL_MARGIN_64 (FP64; rounding-order differences of 64-128
+  steps amplified by kappa(A_kk)), TOL_MARGIN_INJECT after a run-time injection (which
+  raises the remaining system's condition by up to 2^27), TOL_MARGIN_32 in FP32;
+* FP64 runs with a right-hand side: the solution's normwise backward error <= 1e-13.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import luqr_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = os.path.join(HERE, "golden")
+TOL_MARGIN_64 = 1e-7
+TOL_MARGIN_INJECT = 1e-3
+TOL_MARGIN_32 = 5e-2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1401_5522_gb300 import build
+    build.build()
+
+
+def golden_names():
+    return sorted(f[len("large_"):-len(".json")] for f in os.listdir(GOLDEN)
+                  if f.startswith("large_") and f.endswith(".json"))
+
+
+def load(name):
+    with open(os.path.join(GOLDEN, f"large_{name}.json")) as f:
+        return json.load(f)
+
+
+_last = {}
+
+
+def host_input(g):
+    """The run's input matrix, rebuilt on the host (the last one is kept: runs on the same
+    matrix are collected next to each other)."""
+    key = json.dumps({k: g["config"].get(k) for k in ("N", "nb", "recipe", "seed", "kappa")})
+    if key not in _last:
+        _last.clear()
+        _last[key] = _build_input(g)
+    return _last[key]
+
+
+def _build_input(g):
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_large", os.path.join(GOLDEN, "make_large.py"))
+    ml = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(ml)
+    A = ml.make_input(g["config"])
+    fp = g["fingerprint"]
+    got = np.array([A[i, j] for i, j in fp["pos"]])
+    want = np.array([float.fromhex(v) for v in fp["val"]])
+    # the recipes draw from torch's seeded host generator; a host whose generator or libm
+    # differs beyond the last bit would build another matrix and void the comparison
+    assert np.allclose(got, want, rtol=4e-16, atol=0), "input recipe gave another matrix here"
+    assert abs(float(np.sum(A[:, :8])) - fp["sum8"]) <= 1e-9 * max(1.0, abs(fp["sum8"]))
+    return A
+
+
+def run_gpu(g, A, with_rhs):
+    from paper_1401_5522_gb300 import luqr
+    cfg = g["config"]
+    N = cfg["N"]
+    dA = torch.from_numpy(A).cuda()          # column-major view in, column-major copy
+    assert dA.stride(0) == 1
+    db = None
+    if with_rhs:
+        db = (dA @ torch.ones(N, 1, dtype=torch.float64, device="cuda")).reshape(-1).contiguous()
+        b = db.clone()
+    prec = "fp32" if cfg.get("dtype") == "float32" else "fp64"
+    h = luqr.factor(dA, cfg["nb"], cfg["criterion"], cfg["alpha"], b=db, tree=cfg["tree"],
+                    group=cfg.get("group", 4), precision=prec,
+                    mumps_mode=cfg.get("mumps_mode", 0), inject=cfg.get("inject") or None)
+    dec, mg = h.decisions()
+    lhs, rhs = h.step_stats()
+    st, _, _ = h.info()
+    h.close()
+    out = dict(dec=dec, margin=mg, lhs=lhs, rhs=rhs, status=st)
+    if with_rhs:
+        out["eta"] = O.backward_error(A, db.cpu().numpy(), b.cpu().numpy())
+    del dA
+    torch.cuda.empty_cache()
+    return out
+
+
+@pytest.mark.parametrize("name", golden_names())
+def test_decisions_match_the_oracle_at_full_size(name):
+    g = load(name)
+    cfg = g["config"]
+    fp32 = cfg.get("dtype") == "float32"
+    A = host_input(g)
+    r = run_gpu(g, A, with_rhs=not fp32)
+    assert r["status"] == 0, r["status"]
+    dec_o = np.array([int(c) for c in g["dec"]], dtype=np.uint8)
+    mg_o = np.array(g["margin"], dtype=np.float64)
+    fin = np.isfinite(mg_o)
+    assert np.array_equal(np.isfinite(r["margin"]), fin)
+    if fp32:
+        near = np.flatnonzero(fin & (np.abs(mg_o) <= TOL_MARGIN_32))
+        assert near.size == 0, f"near-ties at steps {near.tolist()}: {mg_o[near].tolist()}"
+        tol = TOL_MARGIN_32
+    else:
+        tol = TOL_MARGIN_INJECT if cfg.get("inject") else TOL_MARGIN_64
+    dmg = np.abs(r["margin"][fin] - mg_o[fin])
+    bad = np.flatnonzero(r["dec"] != dec_o)
+    print(f"\n{name}: {int(dec_o.sum())} LU of {len(dec_o)}; max |d margin| "
+          f"{dmg.max() if dmg.size else 0.0:.2e}; min |margin| "
+          f"{np.min(np.abs(mg_o[fin])) if fin.any() else float('inf'):.3g}"
+          + (f"; eta {r['eta']:.2e}" if "eta" in r else ""))
+    assert bad.size == 0, f"decisions differ at steps {bad.tolist()}"
+    assert dmg.size == 0 or dmg.max() <= tol, dmg.max()
+    if cfg["criterion"] in ("max", "sum"):
+        rhs_o = np.array(g["rhs"], dtype=np.float64)
+        ok = np.isfinite(rhs_o) & (rhs_o > 0)
+        rel = np.abs(r["rhs"][ok] - rhs_o[ok]) / rhs_o[ok]
+        assert rel.size == 0 or rel.max() <= (1e-4 if fp32 else 1e-8), rel.max()
+    if "eta" in r:
+        assert r["eta"] <= 1e-13, r["eta"]

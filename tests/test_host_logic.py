@@ -2,6 +2,7 @@
 standardisation into the MLP's first layer, the repeat-previous predictor, and the batched
 solver's size buckets."""
 import numpy as np
+import pytest
 
 from oracle import mlp_oracle as M
 from paper_1401_5522_gb300 import batched as Bt
@@ -51,3 +52,25 @@ def test_bench_defaults_follow_the_measurement_contract():
     assert (a.N, a.nb, a.kappa, a.criterion, a.alpha, a.tree) == (32768, 256, 1e5, "max", 100.0,
                                                                      "binary_tt")
     assert a.tol == 1e-13 and a.e2e_steps >= 1
+
+
+def test_bench_update_work_follows_the_trailing_matrix_model():
+    """Bytes of the bulk update = trailing rows k.. x bulk columns read + written once per
+    step; summed over a run they approach (2/3) s_C N^3 / nb, the per-solve algorithmic
+    bytes of the trailing update; flops approach Table I's update terms."""
+    import numpy as np
+    import bench
+    n, nb = 128, 256
+    N = n * nb
+    qr = np.zeros(n, dtype=np.uint8)
+    qr[-1] = 1
+    by, fl = bench.update_work(qr, n, nb, "binary_tt", 4)
+    m = np.arange(n - 1, -1, -1, dtype=float)           # m = n-1-k
+    cols = np.maximum(m - 1, 0) * nb
+    assert by == pytest.approx(float(np.sum(8.0 * (m + 1) * nb * cols)))
+    assert by == pytest.approx((2.0 / 3.0) * 4 * N ** 3 / nb, rel=0.03)
+    # all-QR update flops ~ 4/3 N^3 (UNMQR + TTMQR on every trailing tile) up to O(N^2 nb)
+    assert fl == pytest.approx((4.0 / 3.0) * N ** 3, rel=0.03)
+    lu = np.ones(n, dtype=np.uint8)
+    _, fl_lu = bench.update_work(lu, n, nb, "binary_tt", 4)
+    assert fl_lu == pytest.approx((2.0 / 3.0) * N ** 3, rel=0.03)
