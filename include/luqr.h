@@ -106,7 +106,13 @@ typedef struct luqr_options {
                               least as often).  luqr_factor only (the batched solver
                               returns LUQR_ERR_INVALID for 1). */
   uint64_t seed;           /* LUQR_RANDOM: SplitMix64 seed of the per-step draws */
-  int reserved[4];
+  int lu_variant;          /* LU step of Sec. II-B: 0 = A1 (GETRF of the diagonal tile with
+                              partial pivoting, default); 1 = A2 (GEQRT of the diagonal tile:
+                              ||A_kk^-1||_1 = ||R^-1 Q^T||_1, pivots |R_jj| for MUMPS, a zero
+                              on R's diagonal selects QR; an LU step applies Q^T to A_kj and b_k
+                              and R^-1 to A_ik).  A2 needs norm_mode = 0 and speculate = 0;
+                              luqr_factor only (the batched solver returns LUQR_ERR_INVALID). */
+  int reserved[3];
 } luqr_options;
 
 typedef struct luqr_handle* luqr_handle_t;

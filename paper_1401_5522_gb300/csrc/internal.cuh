@@ -248,6 +248,16 @@ template <typename T>
 void launch_qr_apply_vec(Mat<const T> F, int k, int nb, TileList tl, bool pair, bool tri,
                          const T* Tk, T* x, const uint8_t* dec, cudaStream_t s);
 
+// LU step variant A2 (k_a2.cu): identity pivots and R's first zero diagonal entry; the
+// gate that lets the QR-gated UNMQR run on A2 LU steps; columns of Q^T (mode 1, to X) or the
+// column sums of |R^-1 Q^T| (mode 0, to colsum) from GEQRT factors (leading dimension lds).
+template <typename T>
+void launch_a2_prep(const T* S, int nb, int* piv, int* status, cudaStream_t s);
+void launch_a2_gate(const uint8_t* dec, uint8_t* gate, int k, cudaStream_t s);
+template <typename T>
+void launch_qt_cols(const T* S, int64_t lds, int nb, const T* Tslot, int mode, double* colsum,
+                    T* X, const int* status, const uint8_t* gate, int k, cudaStream_t s);
+
 // Decision predictor and speculation helpers (k_mlp.cu).
 template <typename T>
 void launch_features_spec(const T* W, int64_t ldw, int k, int n, int nb, double alpha,

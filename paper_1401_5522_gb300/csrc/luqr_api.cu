@@ -23,6 +23,9 @@ struct luqr_handle {
   int64_t N = 0, Npad = 0, Wc = 0;
   int nb = 0, n = 0, prec = 0, criterion = 0, tree = 0, group = 4, mumps_mode = 0;
   int norm_mode = 0;   // 0 exact ||A_kk^-1||_1, 1 Hager-Higham estimate
+  int lu_variant = 0;  // 0 A1 (GETRF of A_kk), 1 A2 (GEQRT of A_kk)
+  uint8_t* gate_all = nullptr;  // n bytes of DEC_QR: runs QR-gated kernels unconditionally
+  uint8_t* a2gate = nullptr;    // A2: DEC_QR at steps whose decision is LU
   unsigned long long seed = 0;   // LUQR_RANDOM
   double alpha = 0.0;
   bool has_rhs = false;
@@ -320,7 +323,15 @@ void enqueue_lu_apply(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, c
       applied = true;
     }
   }
-  if (!applied) launch_swptrsm<T>(LU, nb, h->piv_all + (size_t)k * nb, C, r0, c0, c1, h->dec, k, s);
+  if (!applied) {
+    if (h->lu_variant == 1) {   // A2: Q^T of the tile's GEQRT (V below the diagonal, T slot)
+      const T* Tk = static_cast<const T*>(h->Tbuf) + (size_t)k * t_step_elems(h);
+      launch_unmqr<T>(Mat<const T>{W, ld}, k, nb, TileList{k, 1, 1, 0}, Tk, h->n, C, c0, c1,
+                      h->a2gate, s);
+    } else {
+      launch_swptrsm<T>(LU, nb, h->piv_all + (size_t)k * nb, C, r0, c0, c1, h->dec, k, s);
+    }
+  }
   Mat<const T> Ablk{W + r1 + r0 * ld, ld};
   Mat<const T> Brow{C.p + r0 + c0 * C.ld, C.ld};
   Mat<T> Cblk{C.p + r1 + c0 * C.ld, C.ld};
@@ -385,10 +396,22 @@ void enqueue_factor(luqr_handle* h) {
       enqueue_qr<T>(h, k, F, 0, 0, true, false, sp, true, shadow - r0 * ld, h->spec, false);
       cudaEventRecord(h->ev_spec[k], sp);
     }
-    launch_getrf<T>(W, ld, k, nb, S, h->piv_s, h->status, s);
-    if (need_inv) {
-      if (h->norm_mode == 1) launch_invnorm_est<T>(S, nb, h->piv_s, h->colsum, h->status, s);
-      else launch_invnorm<T>(S, nb, h->piv_s, h->colsum, h->status, s);
+    T* Tkk = static_cast<T*>(h->Tbuf) + (size_t)k * t_step_elems(h) +
+             (size_t)k * 2 * t_block_elems(h);   // T slot of tile (k, k), GEQRT kind
+    if (h->lu_variant == 1) {
+      // Factor (variant A2): GEQRT of a scratch copy of A_kk; its T goes to the tile's slot
+      launch_gated_copy<T>(W + r0 + r0 * ld, ld, S, nb, nb, nb, h->gate_all, k, DEC_QR,
+                           "k_a2_copy", s);
+      launch_geqrt<T>(Mat<T>{S, nb}, 0, nb, TileList{0, 1, 1, 0}, Tkk, n, h->gate_all, s);
+      launch_a2_prep<T>(S, nb, h->piv_s, h->status, s);
+      if (need_inv)
+        launch_qt_cols<T>(S, nb, nb, Tkk, 0, h->colsum, nullptr, h->status, h->gate_all, k, s);
+    } else {
+      launch_getrf<T>(W, ld, k, nb, S, h->piv_s, h->status, s);
+      if (need_inv) {
+        if (h->norm_mode == 1) launch_invnorm_est<T>(S, nb, h->piv_s, h->colsum, h->status, s);
+        else launch_invnorm<T>(S, nb, h->piv_s, h->colsum, h->status, s);
+      }
     }
     DecideArgs da{k,        n,         nb,       h->criterion, h->mumps_mode, h->alpha,
                   h->norms + (size_t)k * n, h->colsum, h->local, h->away,     h->forced,
@@ -396,6 +419,7 @@ void enqueue_factor(luqr_handle* h) {
     da.seed = h->seed;
     launch_decide<T>(da, S, s);
     if (spec) launch_spec_resolve(k, h->dec, h->spec, h->qrfac, h->cmt, s);
+    if (h->lu_variant == 1) launch_a2_gate(h->dec, h->a2gate, k, s);
     // ---- factor the panel: LU (Alg. 2: commit + TRSM) or QR (GEQRT + TS/TT chain)
     launch_lu_commit<T>(W, ld, k, nb, S, h->piv_s, h->piv_all + (size_t)k * nb, h->dec, s);
     Mat<const T> LU{W + r0 + r0 * ld, ld};
@@ -426,8 +450,13 @@ void enqueue_factor(luqr_handle* h) {
       if constexpr (std::is_same<T, float>::value) {
         if (tcqr) enqueue_qr_extras(h, k, sx);
         if (lu_x) {
-          launch_lu_inverse(reinterpret_cast<const float*>(W), ld, k, nb,
-                            h->piv_all + (size_t)k * nb, h->Linv[k & 1], h->dec, sx);
+          if (h->lu_variant == 1)   // A2: X = Q^T of the committed tile's GEQRT
+            launch_qt_cols<float>(reinterpret_cast<const float*>(W) + r0 + r0 * ld, ld, nb,
+                                  reinterpret_cast<const float*>(Tkk), 1, nullptr, h->Linv[k & 1],
+                                  h->status, h->a2gate, k, sx);
+          else
+            launch_lu_inverse(reinterpret_cast<const float*>(W), ld, k, nb,
+                              h->piv_all + (size_t)k * nb, h->Linv[k & 1], h->dec, sx);
           launch_tc_pack(h->Linv[k & 1], nb, 0, 0, TC_MASK_NONE, nb, nb, h->Xpk[k & 1], 0, 1,
                          h->dec, k, DEC_LU, sx);
         }
@@ -527,7 +556,7 @@ void free_handle(luqr_handle* h) {
                   h->Gbuf,   h->Tfull[0], h->Tfull[1], h->Vt[0], h->Vt[1], h->gm,
                   h->Apk[0], h->Apk[1],   h->Lpk[0],   h->Lpk[1], h->feat, h->spec,
                   h->Linv[0], h->Linv[1], h->Xpk[0],   h->Xpk[1],
-                  h->qrfac,  h->cmt,      h->shadow};
+                  h->qrfac,  h->cmt,      h->shadow, h->gate_all, h->a2gate};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -688,6 +717,8 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   if (o.fp32_kernels < 0 || o.fp32_kernels > 2) return LUQR_ERR_INVALID;
   if (o.mumps_mode < 0 || o.mumps_mode > 1 || o.n_inject < 0) return LUQR_ERR_INVALID;
   if (o.norm_mode < 0 || o.norm_mode > 1) return LUQR_ERR_INVALID;
+  if (o.lu_variant < 0 || o.lu_variant > 1) return LUQR_ERR_INVALID;
+  if (o.lu_variant == 1 && (o.norm_mode != 0 || o.speculate != 0)) return LUQR_ERR_INVALID;
   if (o.speculate < 0 || o.speculate > 2 || (o.speculate == 1 && !o.mlp_params))
     return LUQR_ERR_INVALID;
   luqr_handle* h = new (std::nothrow) luqr_handle();
@@ -706,6 +737,7 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   h->group = o.group;
   h->mumps_mode = o.mumps_mode;
   h->norm_mode = o.norm_mode;
+  h->lu_variant = o.lu_variant;
   h->seed = o.seed;
   h->stream = static_cast<cudaStream_t>(stream);
   h->injected.assign(h->n, 0);
@@ -735,6 +767,10 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   A((void**)&h->rhs, sizeof(double) * n);
   A((void**)&h->status, sizeof(int) * ST_WORDS);
   if (o.forced) A((void**)&h->forced, (size_t)n);
+  if (h->lu_variant == 1) {
+    A((void**)&h->gate_all, (size_t)n);
+    A((void**)&h->a2gate, (size_t)n);
+  }
   h->use_tc = (h->prec == LUQR_PREC_FP32) && (o.fp32_kernels != 1);
   h->use_tc_qr = (h->prec == LUQR_PREC_FP32) && (o.fp32_kernels != 1);
   h->pk_tile = tc_packed_bytes(nb, nb);
@@ -812,6 +848,8 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   cudaMemsetAsync(h->status, 0, sizeof(int) * ST_WORDS, s);
   cudaMemsetAsync(h->dec, DEC_ABORT, (size_t)n, s);
   cudaMemsetAsync(h->piv_all, 0, sizeof(int) * (size_t)n * nb, s);
+  if (h->gate_all) cudaMemsetAsync(h->gate_all, DEC_QR, (size_t)n, s);
+  if (h->a2gate) cudaMemsetAsync(h->a2gate, DEC_LU, (size_t)n, s);
   if (o.forced) cudaMemcpyAsync(h->forced, o.forced, (size_t)n, cudaMemcpyHostToDevice, s);
   if (h->prec == LUQR_PREC_FP64) {
     launch_pack<double>(dA, lda, db, N, h->Npad, h->Wc, wsT<double>(h), h->Npad, s);

@@ -45,7 +45,7 @@ class Options(ctypes.Structure):
                 ("fp32_kernels", ctypes.c_int), ("speculate", ctypes.c_int),
                 ("log_features", ctypes.c_int), ("mlp_params", ctypes.c_void_p),
                 ("norm_mode", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("reserved", ctypes.c_int * 4)]
+                ("lu_variant", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 _lib = None
@@ -283,13 +283,14 @@ NORM_MODE = {"exact": 0, "estimate": 1}
 def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
            precision="fp64", mumps_mode=0, forced=None, inject=None, stream=None,
            fp32_kernels="default", speculate="off", mlp_params=None, log_features=False,
-           norm_mode="exact", seed=0):
+           norm_mode="exact", seed=0, lu_variant="A1"):
     """luqr_factor on a column-major float64 CUDA matrix; b (if given) is overwritten by x.
 
     speculate: "off", "mlp" (mlp_params: float32 CUDA tensor of MLP_PARAMS values, kept
     alive by the caller until the factorization has run) or "repeat".
     norm_mode: "exact" ||A_kk^-1||_1 or "estimate" (Hager-Higham).
-    criterion "random": LU with probability alpha/100 per step (SplitMix64 draws from seed)."""
+    criterion "random": LU with probability alpha/100 per step (SplitMix64 draws from seed).
+    lu_variant: "A1" (GETRF of the diagonal tile) or "A2" (GEQRT of the diagonal tile)."""
     N = A.shape[0]
     lda = _check_matrix(A)
     crit = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
@@ -300,6 +301,7 @@ def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
     opt.mumps_mode = int(mumps_mode)
     opt.norm_mode = NORM_MODE[norm_mode] if isinstance(norm_mode, str) else int(norm_mode)
     opt.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    opt.lu_variant = {"A1": 0, "A2": 1}[lu_variant] if isinstance(lu_variant, str) else int(lu_variant)
     opt.fp32_kernels = {"default": 0, "cuda": 1, "tensor": 2}[fp32_kernels]
     opt.speculate = SPECULATE[speculate] if isinstance(speculate, str) else int(speculate)
     opt.log_features = 1 if log_features else 0

@@ -86,16 +86,22 @@ def run(name):
     from oracle import luqr_oracle_mt as M
     cfg = RUNS[name]
     A = make_input(cfg)
+    fp32 = cfg.get("dtype") == "float32"
+    b = None if fp32 else A @ np.ones(A.shape[0])
     t = time.time()
-    res = M.factor(A, None, cfg["nb"], CRIT[cfg["criterion"]], cfg["alpha"],
+    res = M.factor(A, b, cfg["nb"], CRIT[cfg["criterion"]], cfg["alpha"],
                    tree=TREE[cfg["tree"]], group=cfg.get("group", 4),
                    mumps_mode=cfg.get("mumps_mode", 0), inject=cfg.get("inject", ()),
-                   dtype=np.float32 if cfg.get("dtype") == "float32" else np.float64)
+                   dtype=np.float32 if fp32 else np.float64)
     dt = time.time() - t
+    eta = None
+    if b is not None:   # the oracle's own solution of A x = A 1 and its backward error
+        from oracle import luqr_oracle as O
+        eta = O.backward_error(A, M.back_substitution(res), b)
     out = {"name": name, "config": cfg, "fingerprint": fingerprint(A),
            "dec": "".join(str(int(d)) for d in res.dec),
            "margin": [float(v) for v in res.margin], "lhs": [float(v) for v in res.lhs],
-           "rhs": [float(v) for v in res.rhs],
+           "rhs": [float(v) for v in res.rhs], "eta": eta,
            "oracle": "oracle/luqr_oracle_mt.cpp", "threads": res.threads,
            "seconds": round(dt, 1), "host": platform.machine(),
            "writer": "tests/golden/make_large.py"}
