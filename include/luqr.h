@@ -112,7 +112,13 @@ typedef struct luqr_options {
                               on R's diagonal selects QR; an LU step applies Q^T to A_kj and b_k
                               and R^-1 to A_ik).  A2 needs norm_mode = 0 and speculate = 0;
                               luqr_factor only (the batched solver returns LUQR_ERR_INVALID). */
-  int reserved[3];
+  int timeout_ms;          /* budget of the bounded waits of the persistent second-pass kernel
+                              (a task waiting for the tasks it depends on), in milliseconds at
+                              the 2.07 GHz maximum SM clock; 0 = default (about 500 ms).  A wait
+                              that runs out records LUQR_ERR_TIMEOUT in the handle's status,
+                              stops the kernel and leaves the device usable.  The tensor-core
+                              update kernel bounds its own waits at about 500 ms. */
+  int reserved[2];
 } luqr_options;
 
 typedef struct luqr_handle* luqr_handle_t;
@@ -176,6 +182,18 @@ int luqr_refine(luqr_handle_t h, const double* dA, int64_t lda, const double* db
 int luqr_refine_gmres(luqr_handle_t h, const double* dA, int64_t lda, const double* db,
                       double* dx, double tol, int max_iter, int restart, int* iters, double* eta,
                       void* stream);
+
+/*
+ * luqr_debug_replay_skip - test hook for the failure path of the bounded device waits.  The
+ * single-vector second pass (luqr_solve with nrhs = 1, and every correction of
+ * luqr_refine) runs as one persistent launch of tasks that wait on each other's completion
+ * signals; this makes task number `task` (in the launch's program order) skip its signal, so
+ * that the next task on the same tile row waits until the handle's timeout_ms budget runs out
+ * and the call reports LUQR_ERR_TIMEOUT.  -1 restores normal operation.  LUQR_ERR_INVALID for
+ * a NULL handle, a task out of range, or a handle whose second pass takes the per-step
+ * launches (FP64 with nb = 512).  Not for production use.
+ */
+int luqr_debug_replay_skip(luqr_handle_t h, int task);
 
 /*
  * luqr_accuracy - accuracy of the solution that the last luqr_refine / luqr_refine_gmres

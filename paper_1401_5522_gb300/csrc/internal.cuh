@@ -241,12 +241,40 @@ void launch_multiaxpy(const double* V, int64_t ldv, int64_t N, int cnt, const do
 void launch_lu_inverse(const float* W, int64_t ldw, int k, int nb, const int* piv_k, float* X,
                        const uint8_t* dec, cudaStream_t s);
 
-// One right-hand side of the second pass (k_qr.cu).
+// Single-vector second pass in one persistent launch (k_replay.cu).  Task types; rows i
+// (and e for pairs) are written, row r (GEMV) is read; ni / ne / nr are the numbers of
+// earlier writes of those rows to wait for.
+constexpr int LUQR_TIMEOUT_CODE = -6;   // LUQR_ERR_TIMEOUT
+enum : int { RT_SCALE = 0, RT_SINGLE = 1, RT_PAIR_TS = 2, RT_PAIR_TT = 3, RT_LUAPPLY = 4,
+             RT_GEMV = 5, RT_TRSV = 6 };
+struct ReplayTask {
+  int type, k, i, e, r, ni, ne, nr;
+  int gate;              // 0 always; 1 only if dec[k] = QR; 2 only if dec[k] = LU (a task whose
+                         // branch was not taken still waits and signals, as a no-op)
+};
 template <typename T>
-bool qr_apply_vec_fits(int nb);   // its double-buffered V blocks fit in shared memory
+struct ReplayArgs {
+  const T* W;            // factored workspace (column-major, leading dimension ld)
+  int64_t ld;
+  const T* Tbuf;         // T blocks, t_step elements per step
+  size_t t_step;
+  const int* piv_all;    // n x nb pivots of the LU steps
+  const uint8_t* dec;    // decisions of the factorization
+  T* x;                  // Npad vector, transformed in place
+  const ReplayTask* tasks;
+  int ntasks, nb;
+  int* ctl;              // [0] next task, [1] abort flag (zero before the launch)
+  int* done;             // n completed-write counters (zero before the launch)
+  int* status;
+  long long budget;      // clock64 cycles a wait may last
+  int skip_signal;       // test hook: this task does not signal its completion (-1: none)
+};
 template <typename T>
-void launch_qr_apply_vec(Mat<const T> F, int k, int nb, TileList tl, bool pair, bool tri,
-                         const T* Tk, T* x, const uint8_t* dec, cudaStream_t s);
+bool replay_fits(int nb);
+template <typename T>
+void launch_replay(const ReplayArgs<T>& a, int grid, cudaStream_t s);
+template <typename T>
+int replay_blocks_per_sm(int nb);
 
 // LU step variant A2 (k_a2.cu): identity pivots and R's first zero diagonal entry; the
 // gate that lets the QR-gated UNMQR run on A2 LU steps; columns of Q^T (mode 1, to X) or the

@@ -777,128 +777,6 @@ __global__ void __launch_bounds__(NT) k_pair_apply(Mat<const T> F, int k, int nb
 }
 
 // ---------------------------------------------------------------- one right-hand side
-// Second pass on a single vector: Q^T of one tile (GEQRT reflectors) or of one tile pair
-// (TS/TT reflectors) applied to x, inner block by inner block,
-//   w = V_b^T x,  w2 = T_b^T w,  x -= V_b w2,
-// with the V and T blocks staged in shared memory and the next block's copy in flight.
-__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// 16-byte global -> shared copy (both addresses 16-byte aligned)
-__device__ __forceinline__ void cp_async16_any(void* sdst, const void* gsrc) {
-  const unsigned saddr = (unsigned)__cvta_generic_to_shared(sdst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cpa_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-template <typename T>
-__global__ void __launch_bounds__(NT) k_qr_apply_vec(Mat<const T> F, int k, int nb, TileList tl,
-                                                     int pair, int tri, const T* __restrict__ Tk,
-                                                     T* __restrict__ x,
-                                                     const uint8_t* __restrict__ dec) {
-  if (dec[k] != DEC_QR) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  // V blocks column-major (column j of the block at j * nb), copied 16 bytes at a time;
-  // the reflector masks (unit diagonal, zeros above / below) are applied when reading.
-  T* Vb = reinterpret_cast<T*>(smem_raw);           // 2 x (IB x nb)
-  T* Tb = Vb + 2 * (size_t)IB * nb;                 // 2 x (IB x IB), column-major
-  T* xs = Tb + 2 * IB * IB;                         // nb: tile i
-  T* xe = xs + nb;                                  // nb: eliminator tile (pairs)
-  T* w = xe + nb;                                   // IB
-  T* w2 = w + IB;                                   // IB
-  constexpr int VEC = 16 / sizeof(T);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
-  const int i = tl.i0 + blockIdx.x * tl.istride;
-  const int e = i - tl.eoff;
-  const T* V = F.p + (int64_t)i * nb + (int64_t)k * nb * F.ld;
-  const T* Tslot = Tk + ((size_t)i * 2 + (pair ? 1 : 0)) * IB * nb;
-  T* xi = x + (int64_t)i * nb;
-  T* xg = x + (int64_t)e * nb;
-  auto lo = [&](int jb) { return pair ? 0 : jb; };
-  auto hi = [&](int jb) { return pair ? (tri ? jb + IB : nb) : nb; };
-  auto stage = [&](int jb, int buf) {
-    T* vs = Vb + (size_t)buf * IB * nb;
-    const int r0 = lo(jb), rows = hi(jb) - r0, cpc = rows / VEC;   // chunks per column
-    for (int idx = tid; idx < IB * cpc; idx += NT) {
-      const int j = idx / cpc, q = idx - j * cpc;
-      cp_async16_any(&vs[(size_t)j * nb + q * VEC], &V[r0 + q * VEC + (int64_t)(jb + j) * F.ld]);
-    }
-    T* ts = Tb + buf * IB * IB;
-    for (int idx = tid; idx < IB * IB / VEC; idx += NT)
-      cp_async16_any(&ts[idx * VEC], &Tslot[(size_t)jb * IB + idx * VEC]);
-    cpa_commit();
-  };
-  // value of reflector j of block jb at row r (r in [lo, hi))
-  auto vval = [&](const T* vs, int jb, int r, int j) -> T {
-    const int d = jb + j;
-    if (!pair) {
-      if (r < d) return (T)0;
-      if (r == d) return (T)1;
-    } else if (tri && r > d) {
-      return (T)0;
-    }
-    return vs[(size_t)j * nb + (r - lo(jb))];
-  };
-  for (int r = tid; r < nb; r += NT) {
-    xs[r] = xi[r];
-    if (pair) xe[r] = xg[r];
-  }
-  stage(0, 0);
-  for (int jb = 0, b = 0; jb < nb; jb += IB, b ^= 1) {
-    if (jb + IB < nb) stage(jb + IB, b ^ 1);
-    else cpa_commit();
-    cpa_wait1();
-    __syncthreads();
-    const T* vs = Vb + (size_t)b * IB * nb;
-    const T* ts = Tb + b * IB * IB;
-    const int r0 = lo(jb), r1 = hi(jb);
-    for (int j = warp; j < IB; j += nw) {
-      T acc = (T)0;
-      for (int r = r0 + lane; r < r1; r += 32) acc += vval(vs, jb, r, j) * xs[r];
-      acc = warp_sum<T>(acc);
-      if (lane == 0) w[j] = pair ? acc + xe[jb + j] : acc;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      T acc = (T)0;
-      for (int a = 0; a <= lane; ++a) acc += ts[(size_t)lane * IB + a] * w[a];
-      w2[lane] = acc;
-    }
-    __syncthreads();
-    for (int r = r0 + tid; r < r1; r += NT) {
-      T acc = (T)0;
-#pragma unroll 8
-      for (int j = 0; j < IB; ++j) acc += vval(vs, jb, r, j) * w2[j];
-      xs[r] -= acc;
-    }
-    if (pair && tid < IB) xe[jb + tid] -= w2[tid];
-    __syncthreads();
-  }
-  for (int r = tid; r < nb; r += NT) {
-    xi[r] = xs[r];
-    if (pair) xg[r] = xe[r];
-  }
-}
-
-template <typename T>
-static size_t qr_apply_vec_smem(int nb) {
-  return sizeof(T) * (2 * (size_t)IB * nb + 2 * IB * IB + 2 * (size_t)nb + 2 * IB);
-}
-
-template <typename T>
-bool qr_apply_vec_fits(int nb) {
-  return qr_apply_vec_smem<T>(nb) <= (size_t)SMEM_MAX;
-}
-
-template <typename T>
-void launch_qr_apply_vec(Mat<const T> F, int k, int nb, TileList tl, bool pair, bool tri,
-                         const T* Tk, T* x, const uint8_t* dec, cudaStream_t s) {
-  if (tl.count <= 0) return;
-  const size_t smem = qr_apply_vec_smem<T>(nb);
-  ensure_dyn_smem<k_qr_apply_vec<T>>(smem);
-  ProfScope ps_(pair ? (tri ? "k_ttmqr_vec" : "k_tsmqr_vec") : "k_unmqr_vec", s);
-  k_qr_apply_vec<T><<<tl.count, NT, smem, s>>>(F, k, nb, tl, pair ? 1 : 0, tri ? 1 : 0, Tk, x,
-                                               dec);
-}
-
 // ---------------------------------------------------------------- launchers
 // The slab width SW is the widest of {64, 32, 16, 8} whose shared-memory plan fits.
 enum PlanKind { PLAN_GEQRT, PLAN_UNMQR, PLAN_PAIR_QRT, PLAN_PAIR_APPLY };
@@ -997,9 +875,6 @@ void launch_pair_apply(Mat<const T> F, int k, int nb, TileList tl, bool tri, con
 }
 
 #define INST(T)                                                                                  \
-  template void launch_qr_apply_vec<T>(Mat<const T>, int, int, TileList, bool, bool, const T*,   \
-                                       T*, const uint8_t*, cudaStream_t);                        \
-  template bool qr_apply_vec_fits<T>(int);                                                       \
   template void launch_geqrt<T>(Mat<T>, int, int, TileList, T*, int, const uint8_t*,             \
                                 cudaStream_t);                                                   \
   template void launch_unmqr<T>(Mat<const T>, int, int, TileList, const T*, int, Mat<T>,         \

@@ -1,0 +1,355 @@
+// Second pass on one right-hand side in ONE persistent launch (Sec. II-D, "Solving systems":
+// every stored step replayed on a new b, then the N x N triangular solve).
+//
+// The host lists the replay as tasks in program order (rq_build in luqr_api.cu):
+//   RT_SCALE   x_k *= 2^-27                          (run-time injection at step k)
+//   RT_SINGLE  x_i <- Q_ik^T x_i                      (GEQRT reflectors of tile (i, k); also
+//                                                      the Q^T of an A2 LU step, tile (k, k))
+//   RT_PAIR_*  [x_e; x_i] <- Q^T [x_e; x_i]            (TS / TT reflectors of tile (i, k))
+//   RT_LUAPPLY x_k <- L^-1 P x_k                       (A1 LU step k)
+//   RT_GEMV    x_i -= A_ik x_k                          (LU step k, i > k; back substitution,
+//                                                      i < k, with the tiles of U)
+//   RT_TRSV    x_k <- U_kk^-1 x_k                       (back substitution)
+// Every task writes one or two tile rows of x and may read one more.  Per tile row r the
+// kernel counts completed writes (done[r]); a task waits until every write that precedes it
+// in program order has completed on each row it touches (the counts are precomputed).  Reads
+// need no count of their own: every later writer of a row depends, through the back
+// substitution, on all readers of that row.  CTAs claim tasks in program order from a
+// device counter and a task waits only on earlier tasks, which running CTAs have claimed, so
+// the launch always progresses, whatever number of CTAs is resident.  Waits are bounded by
+// a clock64 budget; when one runs out the kernel records LUQR_ERR_TIMEOUT in the status
+// word, raises an abort flag that stops every CTA, and returns.
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace luqr {
+
+
+// Shared memory of one task: two staged IB x nb V blocks, two IB x IB T blocks, two nb
+// segments of x, two IB work vectors.
+template <typename T>
+size_t replay_smem(int nb) {
+  return sizeof(T) * (2 * (size_t)IB * nb + 2 * IB * IB + 2 * (size_t)nb + 2 * IB);
+}
+
+__device__ __forceinline__ void rp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void rp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void rp_cp16(void* sdst, const void* gsrc) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ int rp_load_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Q^T of one tile (pair = 0: GEQRT reflectors, unit lower V) or one tile pair (pair = 1:
+// reflector j is [e_j; V(:, j)], V upper triangular for TT) applied to the vector segments
+// xs (row i) and xe (eliminator row), inner block by inner block:
+//   w = V_b^T x_i (+ x_e(block rows) for pairs),  w2 = T_b^T w,  x_i -= V_b w2,  x_e -= w2,
+// with the next block's V and T copies in flight.
+template <typename T>
+__device__ void rp_qr_vec(const T* __restrict__ V, int64_t ldv, const T* __restrict__ Tslot,
+                          int nb, bool pair, bool tri, T* Vb, T* Tb, T* xs, T* xe, T* w, T* w2) {
+  constexpr int VEC = 16 / sizeof(T);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
+  auto lo = [&](int jb) { return pair ? 0 : jb; };
+  auto hi = [&](int jb) { return pair ? (tri ? jb + IB : nb) : nb; };
+  auto stage = [&](int jb, int buf) {
+    T* vs = Vb + (size_t)buf * IB * nb;
+    const int r0 = lo(jb), rows = hi(jb) - r0, cpc = rows / VEC;
+    for (int idx = tid; idx < IB * cpc; idx += NT) {
+      const int j = idx / cpc, q = idx - j * cpc;
+      rp_cp16(&vs[(size_t)j * nb + q * VEC], &V[r0 + q * VEC + (int64_t)(jb + j) * ldv]);
+    }
+    T* ts = Tb + buf * IB * IB;
+    for (int idx = tid; idx < IB * IB / VEC; idx += NT)
+      rp_cp16(&ts[idx * VEC], &Tslot[(size_t)jb * IB + idx * VEC]);
+    rp_commit();
+  };
+  auto vval = [&](const T* vs, int jb, int r, int j) -> T {
+    const int d = jb + j;
+    if (!pair) {
+      if (r < d) return (T)0;
+      if (r == d) return (T)1;
+    } else if (tri && r > d) {
+      return (T)0;
+    }
+    return vs[(size_t)j * nb + (r - lo(jb))];
+  };
+  stage(0, 0);
+  for (int jb = 0, b = 0; jb < nb; jb += IB, b ^= 1) {
+    if (jb + IB < nb) stage(jb + IB, b ^ 1);
+    else rp_commit();
+    rp_wait1();
+    __syncthreads();
+    const T* vs = Vb + (size_t)b * IB * nb;
+    const T* ts = Tb + b * IB * IB;
+    const int r0 = lo(jb), r1 = hi(jb);
+    for (int j = warp; j < IB; j += nw) {
+      T acc = (T)0;
+      for (int r = r0 + lane; r < r1; r += 32) acc += vval(vs, jb, r, j) * xs[r];
+      acc = warp_sum<T>(acc);
+      if (lane == 0) w[j] = pair ? acc + xe[jb + j] : acc;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      T acc = (T)0;
+      for (int a = 0; a <= lane; ++a) acc += ts[(size_t)lane * IB + a] * w[a];
+      w2[lane] = acc;
+    }
+    __syncthreads();
+    for (int r = r0 + tid; r < r1; r += NT) {
+      T acc = (T)0;
+#pragma unroll 8
+      for (int j = 0; j < IB; ++j) acc += vval(vs, jb, r, j) * w2[j];
+      xs[r] -= acc;
+    }
+    if (pair && tid < IB) xe[jb + tid] -= w2[tid];
+    __syncthreads();
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// x <- L^-1 P x for the GETRF factors of the diagonal tile (unit lower L below the diagonal,
+// ld ldl): the exchanges in order, then 32-row blocks from the top: warp 0 solves the block
+// with shuffles, all threads update the rows below it.
+template <typename T>
+__device__ void rp_lu_apply(const T* __restrict__ L, int64_t ldl, const int* __restrict__ piv,
+                            int nb, T* xs) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0)
+    for (int r = 0; r < nb; ++r) {
+      const int p = piv[r];
+      if (p != r) { const T t = xs[r]; xs[r] = xs[p]; xs[p] = t; }
+    }
+  __syncthreads();
+  for (int b0 = 0; b0 < nb; b0 += 32) {
+    if (warp == 0) {
+      T l[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) l[c] = L[(b0 + lane) + (int64_t)(b0 + c) * ldl];
+      T x = xs[b0 + lane];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const T xc = __shfl_sync(0xffffffffu, x, c);
+        if (lane > c) x -= l[c] * xc;
+      }
+      xs[b0 + lane] = x;
+    }
+    __syncthreads();
+    for (int r = b0 + 32 + tid; r < nb; r += NT) {
+      T acc = (T)0;
+#pragma unroll 8
+      for (int c = 0; c < 32; ++c) acc += L[r + (int64_t)(b0 + c) * ldl] * xs[b0 + c];
+      xs[r] -= acc;
+    }
+    __syncthreads();
+  }
+}
+
+// x <- U^-1 x for the upper triangle of the diagonal tile (ld ldu), 32-row blocks from the
+// bottom.  Returns the first row with an exact zero diagonal entry, or -1.
+template <typename T>
+__device__ int rp_trsv(const T* __restrict__ U, int64_t ldu, int nb, T* xs, int* s_bad) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) *s_bad = -1;
+  __syncthreads();
+  for (int bb = nb / 32 - 1; bb >= 0; --bb) {
+    const int b0 = bb * 32;
+    if (warp == 0) {
+      T u[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r) u[r] = U[(b0 + lane) + (int64_t)(b0 + r) * ldu];
+      T x = xs[b0 + lane];
+      int bad = -1;
+#pragma unroll
+      for (int r = 31; r >= 0; --r) {
+        const T d = __shfl_sync(0xffffffffu, u[r], r);
+        if (d == (T)0) { bad = b0 + r; break; }
+        if (lane == r) x = x / d;
+        const T xr = __shfl_sync(0xffffffffu, x, r);
+        if (lane < r) x -= u[r] * xr;
+      }
+      xs[b0 + lane] = x;
+      if (lane == 0 && bad >= 0) *s_bad = bad;
+    }
+    __syncthreads();
+    if (*s_bad >= 0) return *s_bad;
+    for (int i = tid; i < b0; i += NT) {
+      T acc = (T)0;
+#pragma unroll 8
+      for (int q = 0; q < 32; ++q) acc += U[i + (int64_t)(b0 + q) * ldu] * xs[b0 + q];
+      xs[i] -= acc;
+    }
+    __syncthreads();
+  }
+  return -1;
+}
+
+// xs (row i) -= A xk for the nb x nb tile A (ld lda): thread r owns rows r, r + NT, ...
+template <typename T>
+__device__ void rp_gemv(const T* __restrict__ A, int64_t lda, int nb, const T* xk, T* xs) {
+  for (int r = threadIdx.x; r < nb; r += NT) {
+    T acc0 = (T)0, acc1 = (T)0;
+    int c = 0;
+    for (; c + 1 < nb; c += 2) {
+      acc0 += A[r + (int64_t)c * lda] * xk[c];
+      acc1 += A[r + (int64_t)(c + 1) * lda] * xk[c + 1];
+    }
+    if (c < nb) acc0 += A[r + (int64_t)c * lda] * xk[c];
+    xs[r] -= acc0 + acc1;
+  }
+}
+
+// Waits (thread 0) until *cnt >= need; false when the abort flag is raised or the clock64
+// budget runs out (then the timeout is recorded and the abort flag raised).
+__device__ bool rp_wait(const int* cnt, int need, long long budget, int* abort_flag, int* status,
+                        int k) {
+  if (rp_load_acquire(cnt) >= need) return true;
+  const long long t0 = clock64();
+  unsigned ns = 32;
+  while (rp_load_acquire(cnt) < need) {
+    if (*(volatile int*)abort_flag) return false;
+    if (clock64() - t0 > budget) {
+      if (atomicCAS(&status[ST_CODE], 0, LUQR_TIMEOUT_CODE) == 0) {
+        status[ST_STEP] = k;
+        status[ST_ROW] = -1;
+      }
+      atomicExch(abort_flag, 1);
+      return false;
+    }
+    __nanosleep(ns);
+    if (ns < 2048) ns *= 2;
+  }
+  return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_replay(ReplayArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nb = a.nb;
+  T* Vb = reinterpret_cast<T*>(smem_raw);           // 2 x (IB x nb)
+  T* Tb = Vb + 2 * (size_t)IB * nb;                 // 2 x (IB x IB)
+  T* xs = Tb + 2 * IB * IB;                         // nb: row i
+  T* xe = xs + nb;                                  // nb: eliminator row / read row
+  T* w = xe + nb;                                   // IB
+  T* w2 = w + IB;                                   // IB
+  __shared__ int s_task, s_go, s_bad;
+  const int tid = threadIdx.x;
+  int* next = a.ctl;
+  int* abort_flag = a.ctl + 1;
+  for (;;) {
+    if (tid == 0) s_task = *(volatile int*)abort_flag ? -1 : atomicAdd(next, 1);
+    __syncthreads();
+    const int t = s_task;
+    if (t < 0 || t >= a.ntasks) break;
+    const ReplayTask q = a.tasks[t];
+    if (tid == 0) {
+      bool ok = rp_wait(a.done + q.i, q.ni, a.budget, abort_flag, a.status, q.k);
+      if (ok && q.e >= 0) ok = rp_wait(a.done + q.e, q.ne, a.budget, abort_flag, a.status, q.k);
+      if (ok && q.r >= 0) ok = rp_wait(a.done + q.r, q.nr, a.budget, abort_flag, a.status, q.k);
+      s_go = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_go) break;
+    T* xi = a.x + (int64_t)q.i * nb;
+    const uint8_t dk = a.dec[q.k];
+    const bool run = q.gate == 0 || (q.gate == 1 && dk == DEC_QR) || (q.gate == 2 && dk == DEC_LU);
+    if (!run) {   // the branch not taken: keep the counts in program order, move no data
+      if (tid == 0 && t != a.skip_signal) {
+        __threadfence();
+        atomicAdd(a.done + q.i, 1);
+        if (q.e >= 0) atomicAdd(a.done + q.e, 1);
+      }
+      continue;
+    }
+    for (int r = tid; r < nb; r += NT) xs[r] = __ldcg(&xi[r]);
+    if (q.e >= 0)
+      for (int r = tid; r < nb; r += NT) xe[r] = __ldcg(&a.x[(int64_t)q.e * nb + r]);
+    if (q.r >= 0)
+      for (int r = tid; r < nb; r += NT) xe[r] = __ldcg(&a.x[(int64_t)q.r * nb + r]);
+    __syncthreads();
+    const T* tile = a.W + (int64_t)q.i * nb + (int64_t)q.k * nb * a.ld;
+    const T* Tstep = a.Tbuf + (size_t)q.k * a.t_step;
+    bool write_e = false;
+    switch (q.type) {
+      case RT_SCALE:
+        for (int r = tid; r < nb; r += NT) xs[r] *= (T)0x1.0p-27;
+        break;
+      case RT_SINGLE:
+        rp_qr_vec<T>(tile, a.ld, Tstep + ((size_t)q.i * 2 + 0) * IB * nb, nb, false, false, Vb, Tb,
+                     xs, xe, w, w2);
+        break;
+      case RT_PAIR_TS:
+      case RT_PAIR_TT:
+        rp_qr_vec<T>(tile, a.ld, Tstep + ((size_t)q.i * 2 + 1) * IB * nb, nb, true,
+                     q.type == RT_PAIR_TT, Vb, Tb, xs, xe, w, w2);
+        write_e = true;
+        break;
+      case RT_LUAPPLY:
+        rp_lu_apply<T>(tile, a.ld, a.piv_all + (size_t)q.k * nb, nb, xs);
+        break;
+      case RT_GEMV:
+        rp_gemv<T>(tile, a.ld, nb, xe, xs);
+        break;
+      case RT_TRSV: {
+        const int bad = rp_trsv<T>(tile, a.ld, nb, xs, &s_bad);
+        if (bad >= 0) {
+          if (tid == 0 && atomicCAS(&a.status[ST_CODE], 0, -4) == 0) {
+            a.status[ST_STEP] = q.k;
+            a.status[ST_ROW] = q.k * nb + bad;
+          }
+        }
+        break;
+      }
+      default:
+        break;
+    }
+    __syncthreads();
+    for (int r = tid; r < nb; r += NT) __stcg(&xi[r], xs[r]);
+    if (write_e)
+      for (int r = tid; r < nb; r += NT) __stcg(&a.x[(int64_t)q.e * nb + r], xe[r]);
+    __syncthreads();
+    if (tid == 0 && t != a.skip_signal) {   // skip_signal: test hook, normally -1
+      __threadfence();
+      atomicAdd(a.done + q.i, 1);
+      if (q.e >= 0) atomicAdd(a.done + q.e, 1);
+    }
+  }
+}
+
+template <typename T>
+bool replay_fits(int nb) {
+  return replay_smem<T>(nb) <= (size_t)SMEM_MAX && (nb % 32) == 0;
+}
+
+template <typename T>
+void launch_replay(const ReplayArgs<T>& a, int grid, cudaStream_t s) {
+  const size_t smem = replay_smem<T>(a.nb);
+  ensure_dyn_smem<k_replay<T>>(smem);
+  ProfScope ps_("k_replay", s);
+  k_replay<T><<<grid, NT, smem, s>>>(a);
+}
+
+template <typename T>
+int replay_blocks_per_sm(int nb) {
+  const size_t smem = replay_smem<T>(nb);
+  ensure_dyn_smem<k_replay<T>>(smem);
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_replay<T>, NT, smem) != cudaSuccess)
+    return 1;
+  return b > 0 ? b : 1;
+}
+
+template bool replay_fits<float>(int);
+template bool replay_fits<double>(int);
+template void launch_replay<float>(const ReplayArgs<float>&, int, cudaStream_t);
+template void launch_replay<double>(const ReplayArgs<double>&, int, cudaStream_t);
+template int replay_blocks_per_sm<float>(int);
+template int replay_blocks_per_sm<double>(int);
+
+}  // namespace luqr

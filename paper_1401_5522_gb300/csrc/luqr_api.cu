@@ -87,6 +87,14 @@ struct luqr_handle {
   double* ref = nullptr;    // x, r, scalars, partial sums
   int ref_chunks = 0;
   double* gm = nullptr;     // GMRES: basis (N x (restart+1)), work vector, dot buffers
+  // single-vector second pass in one persistent launch: the task list (both branches of
+  // every step, gated on the device decision), its device copy and counters
+  std::vector<ReplayTask> rq_host;
+  ReplayTask* rq = nullptr;
+  int* rq_ctl = nullptr;        // [0] next task, [1] abort flag, [2 .. 2+n) per-row counts
+  int rq_grid = 0;
+  int rq_skip = -1;             // test hook: task whose completion is never signalled
+  long long wait_cycles = 1000000000LL;   // budget of a bounded device wait (about 0.5 s)
   double acc[4] = {NAN, NAN, NAN, NAN};   // last refinement: ||A||, ||r||, ||x||, ||b|| (inf-norms)
   int gm_restart = 0;
   size_t elt = 8;
@@ -229,6 +237,44 @@ void for_each_tile_list(const luqr_handle* h, int k, FS&& single, FP&& pair) {
   }
 }
 
+// Task list of the single-vector second pass (k_replay.cu), in program order: per step k the
+// injection scaling, the QR branch (tile lists of the tree, gated on dec[k] = QR) and the LU
+// branch (A1: L^-1 P on row k, A2: the tile's Q^T; then x_i -= A_ik x_k; gated on LU), then
+// the back substitution from the last tile row up.  Each task carries, per row it writes
+// or reads, the number of earlier writes of that row.
+void rq_build(luqr_handle* h) {
+  const int n = h->n;
+  std::vector<int> wc(n, 0);
+  std::vector<ReplayTask>& out = h->rq_host;
+  out.clear();
+  auto push = [&](int type, int k, int i, int e, int r, int gate) {
+    ReplayTask t{type, k, i, e, r, wc[i], e >= 0 ? wc[e] : 0, r >= 0 ? wc[r] : 0, gate};
+    out.push_back(t);
+    ++wc[i];
+    if (e >= 0) ++wc[e];
+  };
+  for (int k = 0; k < n; ++k) {
+    if (h->injected[k]) push(RT_SCALE, k, k, -1, -1, 0);
+    for_each_tile_list(
+        h, k,
+        [&](TileList tl) {
+          for (int t = 0; t < tl.count; ++t) push(RT_SINGLE, k, tl.i0 + t * tl.istride, -1, -1, 1);
+        },
+        [&](TileList tl, bool tri) {
+          for (int t = 0; t < tl.count; ++t) {
+            const int i = tl.i0 + t * tl.istride;
+            push(tri ? RT_PAIR_TT : RT_PAIR_TS, k, i, i - tl.eoff, -1, 1);
+          }
+        });
+    push(h->lu_variant == 1 ? RT_SINGLE : RT_LUAPPLY, k, k, -1, -1, 2);
+    for (int i = k + 1; i < n; ++i) push(RT_GEMV, k, i, -1, k, 2);
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    push(RT_TRSV, k, k, -1, -1, 0);
+    for (int i = 0; i < k; ++i) push(RT_GEMV, k, i, -1, k, 0);
+  }
+}
+
 // Enqueues the QR step of panel k along the handle's tree.  do_factor factors the panel
 // tiles, do_apply applies the step's transformations to columns [c0, c1) of C.
 // The factorization works on column k of fbase (default: the workspace; the shadow copy
@@ -263,7 +309,6 @@ void enqueue_qr(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, bool do
       if constexpr (is_f32) {
         if (tc) { tc_apply_single(h, k, tl, C, c0, c1, s); return; }
       }
-      if (c1 - c0 == 1 && qr_apply_vec_fits<T>(nb)) { launch_qr_apply_vec<T>(Fc, k, nb, tl, false, false, Tk, C.p + c0 * C.ld, dec, s); return; }
       launch_unmqr<T>(Fc, k, nb, tl, Tk, n, C, c0, c1, dec, s);
     }
   };
@@ -279,7 +324,6 @@ void enqueue_qr(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, bool do
       if constexpr (is_f32) {
         if (tc) { tc_apply_pair(h, k, tl, tri, C, c0, c1, s); return; }
       }
-      if (c1 - c0 == 1 && qr_apply_vec_fits<T>(nb)) { launch_qr_apply_vec<T>(Fc, k, nb, tl, true, tri, Tk, C.p + c0 * C.ld, dec, s); return; }
       launch_pair_apply<T>(Fc, k, nb, tl, tri, Tk, n, C, c0, c1, dec, s);
     }
   };
@@ -504,6 +548,18 @@ void enqueue_backsolve(luqr_handle* h, Mat<T> X, int nrhs) {
 // Second pass: replay every step on X (Npad x nrhs, precision T), then back-substitute.
 template <typename T>
 void enqueue_replay(luqr_handle* h, Mat<T> X, int nrhs) {
+  if (nrhs == 1 && h->rq != nullptr && h->elt == sizeof(T)) {
+    cudaMemsetAsync(h->rq_ctl, 0, sizeof(int) * (2 + (size_t)h->n), h->stream);
+    ReplayArgs<T> a{};
+    a.W = wsT<T>(h); a.ld = h->Npad;
+    a.Tbuf = static_cast<const T*>(h->Tbuf); a.t_step = t_step_elems(h);
+    a.piv_all = h->piv_all; a.dec = h->dec; a.x = X.p;
+    a.tasks = h->rq; a.ntasks = (int)h->rq_host.size(); a.nb = h->nb;
+    a.ctl = h->rq_ctl; a.done = h->rq_ctl + 2; a.status = h->status;
+    a.budget = h->wait_cycles; a.skip_signal = h->rq_skip;
+    launch_replay<T>(a, h->rq_grid, h->stream);
+    return;
+  }
   for (int k = 0; k < h->n; ++k) {
     const int64_t r0 = (int64_t)k * h->nb;
     if (h->injected[k]) launch_scale_rows<T>(X.p, X.ld, r0, h->nb, 0, nrhs, std::ldexp(1.0, -27), h->stream);
@@ -556,7 +612,8 @@ void free_handle(luqr_handle* h) {
                   h->Gbuf,   h->Tfull[0], h->Tfull[1], h->Vt[0], h->Vt[1], h->gm,
                   h->Apk[0], h->Apk[1],   h->Lpk[0],   h->Lpk[1], h->feat, h->spec,
                   h->Linv[0], h->Linv[1], h->Xpk[0],   h->Xpk[1],
-                  h->qrfac,  h->cmt,      h->shadow, h->gate_all, h->a2gate};
+                  h->qrfac,  h->cmt,      h->shadow, h->gate_all, h->a2gate, h->rq,
+                  h->rq_ctl};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -718,6 +775,7 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   if (o.mumps_mode < 0 || o.mumps_mode > 1 || o.n_inject < 0) return LUQR_ERR_INVALID;
   if (o.norm_mode < 0 || o.norm_mode > 1) return LUQR_ERR_INVALID;
   if (o.lu_variant < 0 || o.lu_variant > 1) return LUQR_ERR_INVALID;
+  if (o.timeout_ms < 0) return LUQR_ERR_INVALID;
   if (o.lu_variant == 1 && (o.norm_mode != 0 || o.speculate != 0)) return LUQR_ERR_INVALID;
   if (o.speculate < 0 || o.speculate > 2 || (o.speculate == 1 && !o.mlp_params))
     return LUQR_ERR_INVALID;
@@ -838,6 +896,23 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
       e = cudaEventCreateWithFlags(&h->ev_stats[q], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_spec[q], cudaEventDisableTiming);
     }
+  }
+  if (o.timeout_ms > 0) h->wait_cycles = (long long)o.timeout_ms * 2070000LL;  // cycles at 2.07 GHz
+  // single-vector second pass in one launch when its shared-memory plan fits
+  const bool rq_ok = h->prec == LUQR_PREC_FP64 ? replay_fits<double>(nb) : replay_fits<float>(nb);
+  if (e == cudaSuccess && rq_ok) {
+    rq_build(h);
+    A((void**)&h->rq, sizeof(ReplayTask) * h->rq_host.size());
+    A((void**)&h->rq_ctl, sizeof(int) * (2 + (size_t)n));
+    int sms = 0, dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int bps = h->prec == LUQR_PREC_FP64 ? replay_blocks_per_sm<double>(nb)
+                                              : replay_blocks_per_sm<float>(nb);
+    h->rq_grid = (int)std::min<size_t>(h->rq_host.size(), (size_t)std::max(1, sms) * bps);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h->rq, h->rq_host.data(), sizeof(ReplayTask) * h->rq_host.size(),
+                     cudaMemcpyHostToDevice);
   }
   if (e != cudaSuccess) {
     free_handle(h);
@@ -967,6 +1042,13 @@ int luqr_refine_gmres(luqr_handle_t h, const double* dA, int64_t lda, const doub
   if (h->prec == LUQR_PREC_FP64)
     return refine_gmres_impl<double>(h, dA, lda, db, dx, tol, max_iter, restart, iters, eta);
   return refine_gmres_impl<float>(h, dA, lda, db, dx, tol, max_iter, restart, iters, eta);
+}
+
+int luqr_debug_replay_skip(luqr_handle_t h, int task) {
+  if (!h || task < -1) return LUQR_ERR_INVALID;
+  if (h->rq == nullptr || task >= (int)h->rq_host.size()) return LUQR_ERR_INVALID;
+  h->rq_skip = task;
+  return LUQR_OK;
 }
 
 int luqr_accuracy(luqr_handle_t h, double* eta, double* hpl3, double* norms) {

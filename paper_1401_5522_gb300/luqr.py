@@ -45,7 +45,8 @@ class Options(ctypes.Structure):
                 ("fp32_kernels", ctypes.c_int), ("speculate", ctypes.c_int),
                 ("log_features", ctypes.c_int), ("mlp_params", ctypes.c_void_p),
                 ("norm_mode", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("lu_variant", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("lu_variant", ctypes.c_int), ("timeout_ms", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 _lib = None
@@ -64,6 +65,7 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_double), _P]),
     "luqr_decisions": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
     "luqr_accuracy": (ctypes.c_int, [_P, _P, _P, _P]),
+    "luqr_debug_replay_skip": (ctypes.c_int, [_P, ctypes.c_int]),
     "luqr_step_stats": (ctypes.c_int, [_P, _P, _P]),
     "luqr_factor_data": (ctypes.c_int, [_P, _P, _I64]),
     "luqr_sync": (ctypes.c_int, [_P]),
@@ -283,7 +285,7 @@ NORM_MODE = {"exact": 0, "estimate": 1}
 def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
            precision="fp64", mumps_mode=0, forced=None, inject=None, stream=None,
            fp32_kernels="default", speculate="off", mlp_params=None, log_features=False,
-           norm_mode="exact", seed=0, lu_variant="A1"):
+           norm_mode="exact", seed=0, lu_variant="A1", timeout_ms=0):
     """luqr_factor on a column-major float64 CUDA matrix; b (if given) is overwritten by x.
 
     speculate: "off", "mlp" (mlp_params: float32 CUDA tensor of MLP_PARAMS values, kept
@@ -301,6 +303,7 @@ def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
     opt.mumps_mode = int(mumps_mode)
     opt.norm_mode = NORM_MODE[norm_mode] if isinstance(norm_mode, str) else int(norm_mode)
     opt.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    opt.timeout_ms = int(timeout_ms)
     opt.lu_variant = {"A1": 0, "A2": 1}[lu_variant] if isinstance(lu_variant, str) else int(lu_variant)
     opt.fp32_kernels = {"default": 0, "cuda": 1, "tensor": 2}[fp32_kernels]
     opt.speculate = SPECULATE[speculate] if isinstance(speculate, str) else int(speculate)

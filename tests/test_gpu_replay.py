@@ -1,0 +1,111 @@
+"""The single-vector second pass (Sec. II-D) in one persistent launch, and the failure path of
+its bounded waits.
+
+* luqr_solve on one right-hand side (the persistent task kernel) against the oracle's replay
+  of the same factorization (FP64: 1e-9 of max |x|, as the other second-pass tests) and
+  against the per-step launches the library uses for several right-hand sides (the first
+  column of a two-column solve): mixed LU/QR decisions, the three trees, a run-time
+  injection, both LU variants; FP32 against the float32 oracle at the FP32 level.
+* A bounded wait that runs out: a test hook makes one task skip its completion signal; with
+  a 2 ms budget the next task on that tile row gives up, the call reports
+  LUQR_ERR_TIMEOUT, and the device stays usable (a following normal solve on a new handle
+  is correct).  Nothing faults: the wait is a polling loop with a clock budget.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import luqr_oracle as O
+from paper_1401_5522_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TREE = {"flat_ts": O.TREE_FLAT_TS, "binary_tt": O.TREE_BINARY_TT, "grouped": O.TREE_GROUPED}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1401_5522_gb300 import build
+    build.build()
+
+
+def colmajor(M):
+    return torch.from_numpy(np.asfortranarray(M)).cuda()
+
+
+@pytest.mark.parametrize("tree", ["flat_ts", "binary_tt", "grouped"])
+@pytest.mark.parametrize("variant,inject", [("A1", ()), ("A1", (2,)), ("A2", ())])
+def test_single_vector_replay_matches_oracle_and_multi_rhs_path(tree, variant, inject):
+    from paper_1401_5522_gb300 import luqr
+    N, nb = 600, 64
+    A = inputs.gaussian(N, 11).numpy()
+    f = O.factor(A, None, nb, O.CRIT_MAX, 3000.0, tree=TREE[tree], group=3, inject=inject,
+                 lu_variant=variant)
+    assert 0 < int(f.dec.sum()) < len(f.dec)
+    b = inputs.gaussian(N, 12).numpy()[:, 0].copy()
+    y_o = O.replay_solve(f, b).ravel()
+    dA = colmajor(A)
+    h = luqr.factor(dA, nb, "max", 3000.0, tree=tree, group=3, inject=inject or None,
+                    lu_variant=variant)
+    dec, _ = h.decisions()
+    assert np.array_equal(dec, f.dec)
+    x1 = torch.from_numpy(b.copy()).cuda()
+    h.solve(x1)                                            # one column: persistent kernel
+    B2 = torch.from_numpy(np.asfortranarray(np.stack([b, 2.0 * b], axis=1))).cuda()
+    h.solve(B2)                                            # two columns: per-step launches
+    st = h.sync()
+    h.close()
+    assert st == 0
+    x1 = x1.cpu().numpy()
+    tol = (1e-5 if inject else 1e-9) * np.max(np.abs(y_o))
+    assert np.max(np.abs(x1 - y_o)) <= tol
+    assert np.max(np.abs(x1 - B2[:, 0].cpu().numpy())) <= (1e-5 if inject else 1e-10) * np.max(np.abs(y_o))
+
+
+def test_single_vector_replay_fp32():
+    from paper_1401_5522_gb300 import luqr
+    N, nb = 1024, 128
+    A = inputs.gaussian(N, 13).numpy()
+    f = O.factor(A, None, nb, O.CRIT_MAX, 3000.0, tree=O.TREE_BINARY_TT, dtype=np.float32)
+    b = A @ np.ones(N)
+    y_o = O.replay_solve(f, b).ravel()
+    dA = colmajor(A)
+    h = luqr.factor(dA, nb, "max", 3000.0, tree="binary_tt", precision="fp32")
+    x = torch.from_numpy(b.copy()).cuda()
+    h.solve(x)
+    assert h.sync() == 0
+    h.close()
+    assert np.max(np.abs(x.cpu().numpy() - y_o)) <= 1e-3 * np.max(np.abs(y_o))
+
+
+def test_bounded_wait_runs_out_and_device_stays_usable():
+    from paper_1401_5522_gb300 import luqr
+    N, nb = 512, 64
+    A = inputs.gaussian(N, 14).numpy()
+    b = A @ np.ones(N)
+    dA = colmajor(A)
+    h = luqr.factor(dA, nb, "max", 3000.0, tree="binary_tt", timeout_ms=2)
+    assert h.sync() == 0
+    L = luqr.lib()
+    assert L.luqr_debug_replay_skip(h._ptr(), 10 ** 7) == luqr.ERR_INVALID
+    assert L.luqr_debug_replay_skip(h._ptr(), 0) == luqr.OK      # task 0: first op on row 0
+    x = torch.from_numpy(b.copy()).cuda()
+    h.solve(x)
+    st = h.sync()
+    status, step, _ = h.info()
+    h.close()
+    assert st == luqr.ERR_TIMEOUT and status == luqr.ERR_TIMEOUT, (st, status)
+    assert 0 <= step < N // nb
+    # the context is intact: a new factorization and solve on the same device are correct
+    torch.cuda.synchronize()
+    db = torch.from_numpy(b.copy()).cuda()
+    h2 = luqr.factor(dA, nb, "max", 3000.0, b=db, tree="binary_tt")
+    assert h2.sync() == 0
+    x2 = torch.from_numpy(b.copy()).cuda()
+    h2.solve(x2)
+    assert h2.sync() == 0
+    h2.close()
+    assert O.backward_error(A, db.cpu().numpy(), b) <= 1e-13
+    assert O.backward_error(A, x2.cpu().numpy(), b) <= 1e-13
