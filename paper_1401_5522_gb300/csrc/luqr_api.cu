@@ -94,6 +94,7 @@ struct luqr_handle {
   int* rq_ctl = nullptr;        // [0] next task, [1] abort flag, [2 .. 2+n) per-row counts
   int rq_grid = 0;
   int rq_skip = -1;             // test hook: task whose completion is never signalled
+  bool rq_by_dec = false;       // the list holds only the branches taken (decisions known)
   long long wait_cycles = 1000000000LL;   // budget of a bounded device wait (about 0.5 s)
   double acc[4] = {NAN, NAN, NAN, NAN};   // last refinement: ||A||, ||r||, ||x||, ||b|| (inf-norms)
   int gm_restart = 0;
@@ -242,7 +243,10 @@ void for_each_tile_list(const luqr_handle* h, int k, FS&& single, FP&& pair) {
 // branch (A1: L^-1 P on row k, A2: the tile's Q^T; then x_i -= A_ik x_k; gated on LU), then
 // the back substitution from the last tile row up.  Each task carries, per row it writes
 // or reads, the number of earlier writes of that row.
-void rq_build(luqr_handle* h) {
+// dec (HOST, nullable): the factorization's decisions; when given, only the branch taken
+// at each step is listed (no gated no-op tasks, which would hold CTAs until their step's
+// tree completes).
+void rq_build(luqr_handle* h, const uint8_t* dec = nullptr) {
   const int n = h->n;
   std::vector<int> wc(n, 0);
   std::vector<ReplayTask>& out = h->rq_host;
@@ -255,19 +259,25 @@ void rq_build(luqr_handle* h) {
   };
   for (int k = 0; k < n; ++k) {
     if (h->injected[k]) push(RT_SCALE, k, k, -1, -1, 0);
+    const bool want_qr = dec == nullptr || dec[k] == DEC_QR;
+    const bool want_lu = dec == nullptr || dec[k] == DEC_LU;
+    const int gq = dec ? 0 : 1, gl = dec ? 0 : 2;
+    if (want_qr)
     for_each_tile_list(
         h, k,
         [&](TileList tl) {
-          for (int t = 0; t < tl.count; ++t) push(RT_SINGLE, k, tl.i0 + t * tl.istride, -1, -1, 1);
+          for (int t = 0; t < tl.count; ++t) push(RT_SINGLE, k, tl.i0 + t * tl.istride, -1, -1, gq);
         },
         [&](TileList tl, bool tri) {
           for (int t = 0; t < tl.count; ++t) {
             const int i = tl.i0 + t * tl.istride;
-            push(tri ? RT_PAIR_TT : RT_PAIR_TS, k, i, i - tl.eoff, -1, 1);
+            push(tri ? RT_PAIR_TT : RT_PAIR_TS, k, i, i - tl.eoff, -1, gq);
           }
         });
-    push(h->lu_variant == 1 ? RT_SINGLE : RT_LUAPPLY, k, k, -1, -1, 2);
-    for (int i = k + 1; i < n; ++i) push(RT_GEMV, k, i, -1, k, 2);
+    if (want_lu) {
+      push(h->lu_variant == 1 ? RT_SINGLE : RT_LUAPPLY, k, k, -1, -1, gl);
+      for (int i = k + 1; i < n; ++i) push(RT_GEMV, k, i, -1, k, gl);
+    }
   }
   for (int k = n - 1; k >= 0; --k) {
     push(RT_TRSV, k, k, -1, -1, 0);
@@ -567,6 +577,26 @@ void enqueue_replay(luqr_handle* h, Mat<T> X, int nrhs) {
     enqueue_qr<T>(h, k, X, 0, nrhs, false, true, h->stream);
   }
   enqueue_backsolve<T>(h, X, nrhs);
+}
+
+// Rebuilds the second-pass task list from the decisions once they are known on the host
+// (synchronises the handle's stream; called by the refinement drivers, which synchronise
+// anyway).  The list only shrinks, so the device allocation is reused.
+int rq_specialise(luqr_handle* h) {
+  if (h->rq == nullptr || h->rq_by_dec) return LUQR_OK;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LUQR_ERR_CUDA;
+  std::vector<uint8_t> dec(h->n);
+  if (cudaMemcpy(dec.data(), h->dec, (size_t)h->n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return LUQR_ERR_CUDA;
+  for (int k = 0; k < h->n; ++k)
+    if (dec[k] != DEC_QR && dec[k] != DEC_LU) return LUQR_OK;   // aborted run: keep the gates
+  rq_build(h, dec.data());
+  if (cudaMemcpy(h->rq, h->rq_host.data(), sizeof(ReplayTask) * h->rq_host.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return LUQR_ERR_CUDA;
+  h->rq_by_dec = true;
+  if (h->rq_skip >= (int)h->rq_host.size()) h->rq_skip = -1;
+  return LUQR_OK;
 }
 
 int ensure_rhs(luqr_handle* h, int nrhs) {
@@ -973,6 +1003,7 @@ int luqr_refine(luqr_handle_t h, const double* dA, int64_t lda, const double* db
                 double tol, int max_iter, int* iters, double* eta, void* stream) {
   if (!h || !dA || !db || !dx || lda < h->N || max_iter < 0 || !(tol >= 0.0)) return LUQR_ERR_INVALID;
   h->stream = static_cast<cudaStream_t>(stream);
+  if (int e0 = rq_specialise(h)) return e0;
   cudaStream_t s = h->stream;
   const int64_t N = h->N;
   const int nchunk = (int)((N + 511) / 512);
@@ -1039,6 +1070,7 @@ int luqr_refine_gmres(luqr_handle_t h, const double* dA, int64_t lda, const doub
       !(tol >= 0.0))
     return LUQR_ERR_INVALID;
   h->stream = static_cast<cudaStream_t>(stream);
+  if (int e0 = rq_specialise(h)) return e0;
   if (h->prec == LUQR_PREC_FP64)
     return refine_gmres_impl<double>(h, dA, lda, db, dx, tol, max_iter, restart, iters, eta);
   return refine_gmres_impl<float>(h, dA, lda, db, dx, tol, max_iter, restart, iters, eta);
@@ -1118,7 +1150,12 @@ int luqr_factor_data(luqr_handle_t h, double* host, int64_t ld) {
 
 int luqr_sync(luqr_handle_t h) {
   if (!h) return LUQR_ERR_INVALID;
-  return read_status(h, nullptr);
+  const int code = read_status(h, nullptr);
+  if (code == LUQR_OK) {
+    const int e0 = rq_specialise(h);
+    if (e0) return e0;
+  }
+  return code;
 }
 
 int luqr_info(luqr_handle_t h, int* status, int* step, int* row) {

@@ -59,9 +59,11 @@ def test_single_vector_replay_matches_oracle_and_multi_rhs_path(tree, variant, i
     h.close()
     assert st == 0
     x1 = x1.cpu().numpy()
-    tol = (1e-5 if inject else 1e-9) * np.max(np.abs(y_o))
+    # after an injection the remaining system's condition grows by up to 2^27, and rounding-
+    # order differences with it (kappa(A) ~ 1e4 here: 2^27 x 1e-16 x 1e4 ~ 1e-4)
+    tol = (1e-3 if inject else 1e-9) * np.max(np.abs(y_o))
     assert np.max(np.abs(x1 - y_o)) <= tol
-    assert np.max(np.abs(x1 - B2[:, 0].cpu().numpy())) <= (1e-5 if inject else 1e-10) * np.max(np.abs(y_o))
+    assert np.max(np.abs(x1 - B2[:, 0].cpu().numpy())) <= (1e-3 if inject else 1e-10) * np.max(np.abs(y_o))
 
 
 def test_single_vector_replay_fp32():
@@ -75,9 +77,16 @@ def test_single_vector_replay_fp32():
     h = luqr.factor(dA, nb, "max", 3000.0, tree="binary_tt", precision="fp32")
     x = torch.from_numpy(b.copy()).cuda()
     h.solve(x)
+    B2 = torch.from_numpy(np.asfortranarray(np.stack([b, b], axis=1))).cuda()
+    h.solve(B2)
     assert h.sync() == 0
     h.close()
-    assert np.max(np.abs(x.cpu().numpy() - y_o)) <= 1e-3 * np.max(np.abs(y_o))
+    x = x.cpu().numpy()
+    # FP32 factors: the two GPU paths differ in summation order only (u_32 ~ 6e-8 times the
+    # growth of the replay); against the float32 oracle the solution carries u_32 kappa(A)
+    # (~1e5 for this N = 1024 Gaussian matrix)
+    assert np.max(np.abs(x - B2[:, 0].cpu().numpy())) <= 1e-4 * np.max(np.abs(y_o))
+    assert np.max(np.abs(x - y_o)) <= 5e-2 * np.max(np.abs(y_o))
 
 
 def test_bounded_wait_runs_out_and_device_stays_usable():
