@@ -118,7 +118,14 @@ typedef struct luqr_options {
                               that runs out records LUQR_ERR_TIMEOUT in the handle's status,
                               stops the kernel and leaves the device usable.  The tensor-core
                               update kernel bounds its own waits at about 500 ms. */
-  int reserved[2];
+  int domain;              /* diagonal-domain pivoting (Sec. II-B, the variant of the paper's
+                              experiments): 0 or 1 = partial pivoting inside the diagonal tile
+                              (default); d > 1 = the Factor step pivots over tiles k .. k+d-1 of
+                              the panel (a tall GETRF), the criterion reads the pivoted panel,
+                              and an LU step applies the exchanges to columns k.. of those rows
+                              and to b before the tile LU step.  Needs speculate = 0 and
+                              lu_variant = 0; luqr_factor only. */
+  int reserved[1];
 } luqr_options;
 
 typedef struct luqr_handle* luqr_handle_t;

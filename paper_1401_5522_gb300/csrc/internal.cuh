@@ -276,6 +276,19 @@ void launch_replay(const ReplayArgs<T>& a, int grid, cudaStream_t s);
 template <typename T>
 int replay_blocks_per_sm(int nb);
 
+// Diagonal-domain pivoting (k_domain.cu): tall GETRF of the rows x nb domain of panel k
+// (exchanges to dpiv, identity to piv_s, zero pivot to the status word), the pivoted copy of
+// panel k the criterion reads, and the exchanges on columns [c0, c1) of an LU step.
+template <typename T>
+void launch_getrf_tall(const T* W, int64_t ld, int k, int nb, int rows, T* St, int* dpiv,
+                       int* piv_s, int* status, cudaStream_t s);
+template <typename T>
+void launch_domain_panel(const T* W, int64_t ld, int k, int nb, int rows, int64_t Npad,
+                         const int* dpiv, T* P, int64_t ldp, cudaStream_t s);
+template <typename T>
+void launch_domain_swap(T* M, int64_t ld, int k, int nb, int rows, int64_t c0, int64_t c1,
+                        const int* dpiv, const uint8_t* dec, cudaStream_t s);
+
 // LU step variant A2 (k_a2.cu): identity pivots and R's first zero diagonal entry; the
 // gate that lets the QR-gated UNMQR run on A2 LU steps; columns of Q^T (mode 1, to X) or the
 // column sums of |R^-1 Q^T| (mode 0, to colsum) from GEQRT factors (leading dimension lds).

@@ -874,7 +874,7 @@ extern "C" int luqr_batched_create(const double* const* dA, double* const* db, c
   if (opt) o = *opt;
   if (o.precision < 0 || o.precision > 1 || o.mumps_mode < 0 || o.mumps_mode > 1) return LUQR_ERR_INVALID;
   if (o.norm_mode != 0) return LUQR_ERR_INVALID;   // the batched criterion uses the exact norm
-  if (o.lu_variant != 0) return LUQR_ERR_INVALID;  // the batched solver runs variant A1
+  if (o.lu_variant != 0 || o.domain > 1) return LUQR_ERR_INVALID;  // batched: A1, tile pivoting
   int nmax = 0;
   int64_t npmax = 0;
   for (int i = 0; i < count; ++i) {

@@ -24,6 +24,9 @@ struct luqr_handle {
   int nb = 0, n = 0, prec = 0, criterion = 0, tree = 0, group = 4, mumps_mode = 0;
   int norm_mode = 0;   // 0 exact ||A_kk^-1||_1, 1 Hager-Higham estimate
   int lu_variant = 0;  // 0 A1 (GETRF of A_kk), 1 A2 (GEQRT of A_kk)
+  int domain = 1;      // tiles of the diagonal pivot domain (1: the diagonal tile)
+  void* St = nullptr;  // domain * nb x nb scratch of the tall GETRF
+  int* dpiv_all = nullptr;  // n x nb row exchanges of the domain (0-based in the domain)
   uint8_t* gate_all = nullptr;  // n bytes of DEC_QR: runs QR-gated kernels unconditionally
   uint8_t* a2gate = nullptr;    // A2: DEC_QR at steps whose decision is LU
   unsigned long long seed = 0;   // LUQR_RANDOM
@@ -435,8 +438,23 @@ void enqueue_factor(luqr_handle* h) {
       if (k > 0) cudaStreamWaitEvent(s, h->ev_rest[k - 1], 0);
       launch_scale_rows<T>(W, ld, r0, nb, r0, h->Wc, std::ldexp(1.0, -27), s);
     }
-    launch_panel_stats<T>(W, ld, k, n, nb, h->norms + (size_t)k * n, h->local, h->away, h->status,
-                          s);
+    const int dd = std::min(h->domain, n - k);   // tiles of this step's pivot domain
+    int* dpiv_k = h->dpiv_all ? h->dpiv_all + (size_t)k * nb : nullptr;
+    if (dd > 1) {
+      // Factor over the diagonal domain: the exchanges reach every column >= k, so the
+      // previous bulk update must be complete; the criterion reads the pivoted panel copy
+      if (k > 0) cudaStreamWaitEvent(s, h->ev_rest[k - 1], 0);
+      launch_getrf_tall<T>(W, ld, k, nb, dd * nb, static_cast<T*>(h->St), dpiv_k, h->piv_s,
+                           h->status, s);
+      launch_domain_panel<T>(W, ld, k, nb, dd * nb, h->Npad, dpiv_k, shadow, ld, s);
+      launch_panel_stats<T>(shadow - (int64_t)k * nb * ld, ld, k, n, nb, h->norms + (size_t)k * n,
+                            h->local, h->away, h->status, s);
+      launch_gated_copy<T>(static_cast<T*>(h->St), dd * nb, S, nb, nb, nb, h->gate_all, k, DEC_QR,
+                           "k_domain_top", s);
+    } else {
+      launch_panel_stats<T>(W, ld, k, n, nb, h->norms + (size_t)k * n, h->local, h->away,
+                            h->status, s);
+    }
     if (h->feat || spec)
       launch_features_spec<T>(W, ld, k, n, nb, h->alpha, h->criterion, h->norms + (size_t)k * n,
                               h->local, h->away, h->dec, h->margin, h->feat, h->speculate, h->mlp,
@@ -461,7 +479,7 @@ void enqueue_factor(luqr_handle* h) {
       if (need_inv)
         launch_qt_cols<T>(S, nb, nb, Tkk, 0, h->colsum, nullptr, h->status, h->gate_all, k, s);
     } else {
-      launch_getrf<T>(W, ld, k, nb, S, h->piv_s, h->status, s);
+      if (dd <= 1) launch_getrf<T>(W, ld, k, nb, S, h->piv_s, h->status, s);
       if (need_inv) {
         if (h->norm_mode == 1) launch_invnorm_est<T>(S, nb, h->piv_s, h->colsum, h->status, s);
         else launch_invnorm<T>(S, nb, h->piv_s, h->colsum, h->status, s);
@@ -474,6 +492,8 @@ void enqueue_factor(luqr_handle* h) {
     launch_decide<T>(da, S, s);
     if (spec) launch_spec_resolve(k, h->dec, h->spec, h->qrfac, h->cmt, s);
     if (h->lu_variant == 1) launch_a2_gate(h->dec, h->a2gate, k, s);
+    if (dd > 1)   // an LU step applies the domain's exchanges to columns k.. and b first
+      launch_domain_swap<T>(W, ld, k, nb, dd * nb, r0, h->Wc, dpiv_k, h->dec, s);
     // ---- factor the panel: LU (Alg. 2: commit + TRSM) or QR (GEQRT + TS/TT chain)
     launch_lu_commit<T>(W, ld, k, nb, S, h->piv_s, h->piv_all + (size_t)k * nb, h->dec, s);
     Mat<const T> LU{W + r0 + r0 * ld, ld};
@@ -573,6 +593,10 @@ void enqueue_replay(luqr_handle* h, Mat<T> X, int nrhs) {
   for (int k = 0; k < h->n; ++k) {
     const int64_t r0 = (int64_t)k * h->nb;
     if (h->injected[k]) launch_scale_rows<T>(X.p, X.ld, r0, h->nb, 0, nrhs, std::ldexp(1.0, -27), h->stream);
+    const int dd = std::min(h->domain, h->n - k);
+    if (dd > 1)
+      launch_domain_swap<T>(X.p, X.ld, k, h->nb, dd * h->nb, 0, nrhs,
+                            h->dpiv_all + (size_t)k * h->nb, h->dec, h->stream);
     enqueue_lu_apply<T>(h, k, X, 0, nrhs, h->stream);
     enqueue_qr<T>(h, k, X, 0, nrhs, false, true, h->stream);
   }
@@ -643,7 +667,7 @@ void free_handle(luqr_handle* h) {
                   h->Apk[0], h->Apk[1],   h->Lpk[0],   h->Lpk[1], h->feat, h->spec,
                   h->Linv[0], h->Linv[1], h->Xpk[0],   h->Xpk[1],
                   h->qrfac,  h->cmt,      h->shadow, h->gate_all, h->a2gate, h->rq,
-                  h->rq_ctl};
+                  h->rq_ctl, h->St, h->dpiv_all};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -806,6 +830,8 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   if (o.norm_mode < 0 || o.norm_mode > 1) return LUQR_ERR_INVALID;
   if (o.lu_variant < 0 || o.lu_variant > 1) return LUQR_ERR_INVALID;
   if (o.timeout_ms < 0) return LUQR_ERR_INVALID;
+  if (o.domain < 0) return LUQR_ERR_INVALID;
+  if (o.domain > 1 && (o.speculate != 0 || o.lu_variant != 0)) return LUQR_ERR_INVALID;
   if (o.lu_variant == 1 && (o.norm_mode != 0 || o.speculate != 0)) return LUQR_ERR_INVALID;
   if (o.speculate < 0 || o.speculate > 2 || (o.speculate == 1 && !o.mlp_params))
     return LUQR_ERR_INVALID;
@@ -826,6 +852,7 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   h->mumps_mode = o.mumps_mode;
   h->norm_mode = o.norm_mode;
   h->lu_variant = o.lu_variant;
+  h->domain = o.domain > 1 ? std::min(o.domain, h->n) : 1;
   h->seed = o.seed;
   h->stream = static_cast<cudaStream_t>(stream);
   h->injected.assign(h->n, 0);
@@ -855,10 +882,13 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   A((void**)&h->rhs, sizeof(double) * n);
   A((void**)&h->status, sizeof(int) * ST_WORDS);
   if (o.forced) A((void**)&h->forced, (size_t)n);
-  if (h->lu_variant == 1) {
-    A((void**)&h->gate_all, (size_t)n);
-    A((void**)&h->a2gate, (size_t)n);
+  if (h->domain > 1) {
+    A(&h->St, (size_t)h->domain * nb * nb * h->elt);
+    A((void**)&h->dpiv_all, sizeof(int) * (size_t)n * nb);
+    A(&h->shadow, (size_t)h->Npad * nb * h->elt);
   }
+  if (h->lu_variant == 1 || h->domain > 1) A((void**)&h->gate_all, (size_t)n);
+  if (h->lu_variant == 1) A((void**)&h->a2gate, (size_t)n);
   h->use_tc = (h->prec == LUQR_PREC_FP32) && (o.fp32_kernels != 1);
   h->use_tc_qr = (h->prec == LUQR_PREC_FP32) && (o.fp32_kernels != 1);
   h->pk_tile = tc_packed_bytes(nb, nb);
@@ -930,7 +960,7 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   if (o.timeout_ms > 0) h->wait_cycles = (long long)o.timeout_ms * 2070000LL;  // cycles at 2.07 GHz
   // single-vector second pass in one launch when its shared-memory plan fits
   const bool rq_ok = h->prec == LUQR_PREC_FP64 ? replay_fits<double>(nb) : replay_fits<float>(nb);
-  if (e == cudaSuccess && rq_ok) {
+  if (e == cudaSuccess && rq_ok && h->domain == 1) {
     rq_build(h);
     A((void**)&h->rq, sizeof(ReplayTask) * h->rq_host.size());
     A((void**)&h->rq_ctl, sizeof(int) * (2 + (size_t)n));

@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
                 ("log_features", ctypes.c_int), ("mlp_params", ctypes.c_void_p),
                 ("norm_mode", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("lu_variant", ctypes.c_int), ("timeout_ms", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("domain", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 _lib = None
@@ -285,14 +285,15 @@ NORM_MODE = {"exact": 0, "estimate": 1}
 def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
            precision="fp64", mumps_mode=0, forced=None, inject=None, stream=None,
            fp32_kernels="default", speculate="off", mlp_params=None, log_features=False,
-           norm_mode="exact", seed=0, lu_variant="A1", timeout_ms=0):
+           norm_mode="exact", seed=0, lu_variant="A1", timeout_ms=0, domain=1):
     """luqr_factor on a column-major float64 CUDA matrix; b (if given) is overwritten by x.
 
     speculate: "off", "mlp" (mlp_params: float32 CUDA tensor of MLP_PARAMS values, kept
     alive by the caller until the factorization has run) or "repeat".
     norm_mode: "exact" ||A_kk^-1||_1 or "estimate" (Hager-Higham).
     criterion "random": LU with probability alpha/100 per step (SplitMix64 draws from seed).
-    lu_variant: "A1" (GETRF of the diagonal tile) or "A2" (GEQRT of the diagonal tile)."""
+    lu_variant: "A1" (GETRF of the diagonal tile) or "A2" (GEQRT of the diagonal tile).
+    domain: tiles of the diagonal pivot domain (1: pivoting inside the diagonal tile)."""
     N = A.shape[0]
     lda = _check_matrix(A)
     crit = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
@@ -304,6 +305,7 @@ def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
     opt.norm_mode = NORM_MODE[norm_mode] if isinstance(norm_mode, str) else int(norm_mode)
     opt.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     opt.timeout_ms = int(timeout_ms)
+    opt.domain = int(domain)
     opt.lu_variant = {"A1": 0, "A2": 1}[lu_variant] if isinstance(lu_variant, str) else int(lu_variant)
     opt.fp32_kernels = {"default": 0, "cuda": 1, "tensor": 2}[fp32_kernels]
     opt.speculate = SPECULATE[speculate] if isinstance(speculate, str) else int(speculate)
