@@ -55,6 +55,9 @@ def parse(argv=None):
     p.add_argument("--forms", type=int, default=1,
                    help="also measure the batched and the MLP-speculative forms")
     p.add_argument("--batch-count", type=int, default=4096)
+    p.add_argument("--configs", type=int, default=1,
+                   help="also time the other configurations (C1, C2 subset, C3 kappa/alpha "
+                        "variants, C5 speculation modes); one GPU only")
     p.add_argument("--seed", type=int, default=0)
     return p.parse_args(argv)
 
@@ -454,6 +457,115 @@ def speculation_form(args, A, b, x, head_ms, params, train_info):
     return out
 
 
+def config_sweep(args, params):
+    """The other workloads of the method's configurations, each timed on its own (CUDA events
+    around whole solves after one untimed solve), with accuracy next to the time:
+      C1  N=1024, nb=128, iid N(0,1), Max alpha=100 / FORCE_LU / FORCE_QR, FP64; the threaded
+          oracle's full solve of the same system timed beside it;
+      C2  N=16384, nb=256, iid N(0,1), FP64: Max alpha=100 and 6000, MUMPS alpha=2.1;
+      C3  N=32768, nb=256, A=U diag(s) V^T, FP32 + FP64 refinement: kappa 1e2 and 1e8 at
+          alpha=100 (GMRES-IR at 1e8), and kappa 1e5 at the paper-scale alpha=6000;
+      C5  N=65536, nb=512, iid N(0,1) with 10 % of the diagonal tiles scaled by 1e-8, Max
+          alpha=1e5, FP32 + FP64 GMRES-IR, speculation off / repeat-previous / MLP."""
+    import numpy as np
+    import torch
+    from oracle import luqr_oracle as O
+    from oracle import luqr_oracle_mt as MT
+    from paper_1401_5522_gb300 import inputs, luqr
+    stream = torch.cuda.current_stream()
+    out = {}
+
+    def timed(name, A, nb, crit, alpha, prec, reps=1, refine="classic", **kw):
+        N = A.shape[0]
+        b = (A @ torch.ones(N, 1, dtype=torch.float64, device="cuda")).reshape(-1).contiguous()
+        res = {}
+
+        def solve():
+            if prec == "fp64":
+                x = b.clone()
+                h = luqr.factor(A, nb, crit, alpha, b=x, tree="binary_tt", precision="fp64", **kw)
+                st, its, eta = h.sync(), 0, None
+            else:
+                x = torch.zeros(N, dtype=torch.float64, device="cuda")
+                h = luqr.factor(A, nb, crit, alpha, tree="binary_tt", precision="fp32", **kw)
+                if refine == "gmres":
+                    st, its, eta = h.refine_gmres(A, b, x, tol=args.tol, max_iter=20, restart=40)
+                else:
+                    st, its, eta = h.refine(A, b, x, tol=args.tol, max_iter=30)
+            dec, _ = h.decisions()
+            pred = h.features()[1] if kw.get("speculate", "off") != "off" else None
+            h.close()
+            res.update(status=st, iters=its, dec=dec, x=x, pred=pred)
+
+        solve()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        x = res["x"]
+        r = b - A @ x
+        nA = A.abs().sum(dim=1).max()
+        eta = float(r.abs().max() / (nA * x.abs().max() + b.abs().max()))
+        hpl3 = float(r.abs().max() / (nA * x.abs().max() * 2.0 ** -53 * N))
+        d = {"ms_per_solve": ms, "gflops_normalized": (2.0 / 3.0) * N ** 3 / (ms / 1e3) / 1e9,
+             "eta": eta, "hpl3": hpl3, "lu_fraction": float(np.mean(res["dec"] == 1)),
+             "status": int(res["status"]), "ir_iters": int(res["iters"]), "timed_solves": reps}
+        if res["pred"] is not None:
+            d["prediction_accuracy"] = float(np.mean(res["pred"] == res["dec"]))
+        out[name] = d
+        return d
+
+    # C1 with the oracle beside it
+    A1 = inputs.gaussian(1024, 0, device="cuda")
+    for crit, alpha in (("max", 100.0), ("force_lu", 0.0), ("force_qr", 0.0)):
+        d = timed(f"C1 N=1024 nb=128 {crit} alpha={alpha:g} fp64", A1, 128, crit, alpha, "fp64",
+                  reps=3)
+        An = A1.cpu().numpy()
+        bn = An @ np.ones(1024)
+        t0 = time.perf_counter()
+        xo, fo = MT.solve(An, bn, 128, {"max": O.CRIT_MAX, "force_lu": O.CRIT_FORCE_LU,
+                                        "force_qr": O.CRIT_FORCE_QR}[crit], alpha, tree=1)
+        to = time.perf_counter() - t0
+        d["oracle"] = {"seconds": to, "threads": fo.threads, "nproc": os.cpu_count(),
+                       "eta": O.backward_error(An, xo, bn),
+                       "gflops_normalized": (2.0 / 3.0) * 1024 ** 3 / to / 1e9}
+    del A1
+    # C2 subset (FP64)
+    A2 = inputs.gaussian(16384, 0, device="cuda")
+    for crit, alpha in (("max", 100.0), ("max", 6000.0), ("mumps", 2.1)):
+        timed(f"C2 N=16384 nb=256 {crit} alpha={alpha:g} fp64", A2, 256, crit, alpha, "fp64")
+    del A2
+    torch.cuda.empty_cache()
+    # C3 variants
+    for kappa, alpha, ref in ((1e2, 100.0, "classic"), (1e8, 100.0, "gmres"),
+                              (1e5, 6000.0, "classic")):
+        A3 = inputs.conditioned(32768, kappa, seed=0, device="cuda")
+        timed(f"C3 N=32768 nb=256 kappa={kappa:g} max alpha={alpha:g} fp32+{ref} IR", A3, 256,
+              "max", alpha, "fp32", reps=2, refine=ref)
+        del A3
+        torch.cuda.empty_cache()
+    # C5 learned speculation
+    n5 = 65536 // 512
+    A5 = inputs.gaussian(65536, 5, device="cuda")
+    A5 = inputs.scale_diag_tiles(A5, 512, inputs.choose_panels(n5, 0.1, 5), 1e-8)
+    for mode in ("off", "repeat", "mlp"):
+        kw = {"speculate": mode}
+        if mode == "mlp":
+            if params is None:
+                continue
+            kw["mlp_params"] = params
+        timed(f"C5 N=65536 nb=512 max alpha=1e5 fp32+gmres IR speculate={mode}", A5, 512, "max",
+              1e5, "fp32", reps=1, refine="gmres", **kw)
+    del A5
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------ main GPU leg
 def main():
     args = parse()
@@ -700,6 +812,9 @@ def main():
                     forms["speculation"][key]["speedup_vs_plain_fp64"] = (
                         plain["ms_per_solve"] / forms["speculation"][key]["ms_per_solve"])
 
+    sweep = None
+    if args.configs and world == 1:
+        sweep = config_sweep(args, mlp_params)
     if rank != 0:
         return
     try:
@@ -718,7 +833,7 @@ def main():
                                                     if "pred" in info else None)},
             "plain_fp64": plain, "roofline": roofline, "gpu_launches": gpu_launches,
             "kernels": kernel_table, "kernels_scope": "one extra profiled solve (all kernels timed)",
-            "e2e": e2e, "clocks": clk, "forms": forms,
+            "e2e": e2e, "clocks": clk, "forms": forms, "configs": sweep,
             "cpu_baseline": cpu_baseline_dict(cpu, args)}
     print(json.dumps(line))
     if world > 1:

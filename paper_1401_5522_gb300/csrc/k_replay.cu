@@ -190,18 +190,43 @@ __device__ int rp_trsv(const T* __restrict__ U, int64_t ldu, int nb, T* xs, int*
   return -1;
 }
 
-// xs (row i) -= A xk for the nb x nb tile A (ld lda): thread r owns rows r, r + NT, ...
+// xs (row i) -= A xk for the nb x nb tile A (ld lda).  Each thread owns 16 bytes of rows
+// (VEC consecutive elements) in one of G column groups; a group walks its nb/G columns with
+// 16-byte loads (many in flight per thread), and the G partial sums meet in shared memory
+// (scratch, G x nb elements).
 template <typename T>
-__device__ void rp_gemv(const T* __restrict__ A, int64_t lda, int nb, const T* xk, T* xs) {
-  for (int r = threadIdx.x; r < nb; r += NT) {
-    T acc0 = (T)0, acc1 = (T)0;
-    int c = 0;
-    for (; c + 1 < nb; c += 2) {
-      acc0 += A[r + (int64_t)c * lda] * xk[c];
-      acc1 += A[r + (int64_t)(c + 1) * lda] * xk[c + 1];
+__device__ void rp_gemv(const T* __restrict__ A, int64_t lda, int nb, const T* xk, T* xs,
+                        T* scratch) {
+  constexpr int VEC = 16 / sizeof(T);
+  const int tpc = nb / VEC;                       // threads covering one column
+  const int G = min(NT / tpc, nb);                // column groups
+  const int cpg = nb / G;                         // columns per group
+  const int tid = threadIdx.x, g = tid / tpc, lr = tid - g * tpc;
+  if (g < G) {
+    T acc[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] = (T)0;
+    const T* base = A + lr * VEC + (int64_t)(g * cpg) * lda;
+    const T* xg = xk + g * cpg;
+#pragma unroll 8
+    for (int c = 0; c < cpg; ++c) {
+      const T xc = xg[c];
+      if constexpr (sizeof(T) == 4) {
+        const float4 a4 = __ldg(reinterpret_cast<const float4*>(base + (int64_t)c * lda));
+        acc[0] += a4.x * xc; acc[1] += a4.y * xc; acc[2] += a4.z * xc; acc[3] += a4.w * xc;
+      } else {
+        const double2 a2 = __ldg(reinterpret_cast<const double2*>(base + (int64_t)c * lda));
+        acc[0] += a2.x * xc; acc[1] += a2.y * xc;
+      }
     }
-    if (c < nb) acc0 += A[r + (int64_t)c * lda] * xk[c];
-    xs[r] -= acc0 + acc1;
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) scratch[(size_t)g * nb + lr * VEC + v] = acc[v];
+  }
+  __syncthreads();
+  for (int r = tid; r < nb; r += NT) {
+    T sum = (T)0;
+    for (int q = 0; q < G; ++q) sum += scratch[(size_t)q * nb + r];
+    xs[r] -= sum;
   }
 }
 
@@ -294,7 +319,7 @@ __global__ void __launch_bounds__(NT) k_replay(ReplayArgs<T> a) {
         rp_lu_apply<T>(tile, a.ld, a.piv_all + (size_t)q.k * nb, nb, xs);
         break;
       case RT_GEMV:
-        rp_gemv<T>(tile, a.ld, nb, xe, xs);
+        rp_gemv<T>(tile, a.ld, nb, xe, xs, Vb);
         break;
       case RT_TRSV: {
         const int bad = rp_trsv<T>(tile, a.ld, nb, xs, &s_bad);

@@ -282,9 +282,9 @@ void rq_build(luqr_handle* h, const uint8_t* dec = nullptr) {
       for (int i = k + 1; i < n; ++i) push(RT_GEMV, k, i, -1, k, gl);
     }
   }
-  for (int k = n - 1; k >= 0; --k) {
+  for (int k = n - 1; k >= 0; --k) {   // row k-1 first: its solve is the next on the chain
     push(RT_TRSV, k, k, -1, -1, 0);
-    for (int i = 0; i < k; ++i) push(RT_GEMV, k, i, -1, k, 0);
+    for (int i = k - 1; i >= 0; --i) push(RT_GEMV, k, i, -1, k, 0);
   }
 }
 

@@ -82,10 +82,9 @@ def test_single_vector_replay_fp32():
     assert h.sync() == 0
     h.close()
     x = x.cpu().numpy()
-    # FP32 factors: the two GPU paths differ in summation order only (u_32 ~ 6e-8 times the
-    # growth of the replay); against the float32 oracle the solution carries u_32 kappa(A)
-    # (~1e5 for this N = 1024 Gaussian matrix)
-    assert np.max(np.abs(x - B2[:, 0].cpu().numpy())) <= 1e-4 * np.max(np.abs(y_o))
+    # FP32 factors: both GPU paths and the float32 oracle differ in summation order only,
+    # and each solution carries u_32 kappa(A) (6e-8 x ~1e5 for this N = 1024 Gaussian matrix)
+    assert np.max(np.abs(x - B2[:, 0].cpu().numpy())) <= 1e-2 * np.max(np.abs(y_o))
     assert np.max(np.abs(x - y_o)) <= 5e-2 * np.max(np.abs(y_o))
 
 
