@@ -286,6 +286,27 @@ void rq_build(luqr_handle* h, const uint8_t* dec = nullptr) {
     push(RT_TRSV, k, k, -1, -1, 0);
     for (int i = k - 1; i >= 0; --i) push(RT_GEMV, k, i, -1, k, 0);
   }
+  // Claim order: by depth in the dependency graph (1 + the deepest earlier writer of any row
+  // the task touches), stable.  A task's dependencies are shallower, so the order stays a
+  // topological one (per row, writes keep their program order and the counts stay valid),
+  // and CTAs take tasks roughly when they become ready instead of holding a CTA on a task
+  // whose step's tree has barely started.
+  std::vector<int> depth(out.size()), lastw(n, 0);
+  for (size_t t = 0; t < out.size(); ++t) {
+    const ReplayTask& q = out[t];
+    int d = lastw[q.i];
+    if (q.e >= 0) d = std::max(d, lastw[q.e]);
+    if (q.r >= 0) d = std::max(d, lastw[q.r]);
+    depth[t] = d + 1;
+    lastw[q.i] = depth[t];
+    if (q.e >= 0) lastw[q.e] = depth[t];
+  }
+  std::vector<int> order(out.size());
+  for (size_t t = 0; t < order.size(); ++t) order[t] = (int)t;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return depth[x] < depth[y]; });
+  std::vector<ReplayTask> sorted(out.size());
+  for (size_t t = 0; t < order.size(); ++t) sorted[t] = out[order[t]];
+  out.swap(sorted);
 }
 
 // Enqueues the QR step of panel k along the handle's tree.  do_factor factors the panel
