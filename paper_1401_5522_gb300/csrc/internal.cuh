@@ -196,9 +196,6 @@ struct TcArgs {
   // packed A known to be triangular (exact zeros): 1 lower (A[m][q] = 0 for q > m), 2 upper
   // (A[m][q] = 0 for q < m); the persistent kernel skips the products of zero blocks
   int a_tri;
-  // set by the launcher: the C (or C1) operand of the epilogue is 16-byte aligned in every
-  // 32-row group, so the persistent kernel prefetches it with bulk copies
-  int epi_bulk;
 };
 void launch_tc(const TcArgs& a, int batch, const char* name, cudaStream_t s);
 // Packed-A form: pack A once (launch_tc_pack), then launch_tc2 with a.Apk/a.sApk set.

@@ -622,9 +622,7 @@ constexpr int T4_ABYTES = 2 * 2 * P_ABLK;                   // two M halves x (h
 constexpr int T4_BBYTES = 2 * T4_BN * P_BK * 4;             // hi + lo
 constexpr int T4_STAGE = T4_ABYTES + T4_BBYTES;             // 48 KB
 constexpr int T4_RAWB = T4_BN * P_BK * 4;                   // 8 KB
-constexpr int T4_EPIB = 32 * 32 * 4;                        // 32 rows x 32 columns of C
-constexpr int T4_EPI = 4 * 2 * T4_EPIB;                     // per epilogue warp, two buffers
-constexpr int T4_SMEM = T4_STG * T4_STAGE + T4_RAW * T4_RAWB + T4_EPI + 512;
+constexpr int T4_SMEM = T4_STG * T4_STAGE + T4_RAW * T4_RAWB + 512;
 
 __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles, int ntiles,
                                                      int total) {
@@ -632,16 +630,14 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
   if (a.status != nullptr && a.status[ST_CODE] != 0) return;
   extern __shared__ __align__(1024) unsigned char smem_p4[];
   unsigned char* rawbase = smem_p4 + T4_STG * T4_STAGE;
-  unsigned char* epibase = rawbase + T4_RAW * T4_RAWB;
-  uint64_t* raw_full = reinterpret_cast<uint64_t*>(epibase + T4_EPI);
+  uint64_t* raw_full = reinterpret_cast<uint64_t*>(rawbase + T4_RAW * T4_RAWB);
   uint64_t* raw_empty = raw_full + T4_RAW;
   uint64_t* a_full = raw_empty + T4_RAW;
   uint64_t* b_full = a_full + T4_STG;
   uint64_t* st_empty = b_full + T4_STG;
   uint64_t* acc_full = st_empty + T4_STG;
   uint64_t* acc_empty = acc_full + 2;
-  uint64_t* epi_full = acc_empty + 2;                  // 4 epilogue warps x 2 buffers
-  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(epi_full + 8);
+  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   volatile int* fail = reinterpret_cast<volatile int*>(taddr_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nK = a.K / P_BK;
@@ -676,7 +672,6 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
       mbar_init(&acc_full[q], 1);
       mbar_init(&acc_empty[q], 4);
     }
-    for (int q = 0; q < 8; ++q) mbar_init(&epi_full[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_fence_before();
@@ -822,100 +817,31 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
       }
     }
   } else if (warp >= 8) {
-    // ---- epilogue (warp 8 + e owns TMEM lanes 32e..32e+31 of each half).  With epi_bulk
-    // the old values of a tile's C (C1 for W = C1 + A B) come in 32-row x 32-column segments
-    // by bulk copies into two per-warp buffers: the first two are requested before the
-    // accumulator is ready and each consumed buffer is refilled with the segment two ahead,
-    // so the epilogue's HBM reads overlap the main loop and each other.
+    // ---- epilogue (warp 8 + e owns TMEM lanes 32e..32e+31 of each half)
     const int e = warp - 8;
-    const bool bulk = a.epi_bulk != 0 && a.epi != TC_EPI_OUT;
-    unsigned char* ebuf = epibase + e * 2 * T4_EPIB;
-    uint64_t* efull = epi_full + e * 2;
-    int fills[2] = {0, 0}, cons[2] = {0, 0};
-    bool stop = false;
-    for (int it = 0; it < ntile_cta && !stop; ++it) {
+    for (int it = 0; it < ntile_cta; ++it) {
       int64_t t, m0, n0;
       tile_of(it, t, m0, n0);
       const int mh = (a.M - m0) > 128 ? 2 : 1;
       const int buf = it & 1;
+      bool ok = wwait(&acc_full[buf], (uint32_t)(it / 2) & 1, fail);
+      if (!__all_sync(0xffffffffu, ok ? 1 : 0)) break;
+      tc_fence_after();
       float* C = a.C + t * a.sC;
       const float* C1 = a.C1 ? a.C1 + t * a.sC1 : nullptr;
-      const float* src = (a.epi == TC_EPI_ADD_OUT) ? C1 : C;
-      const int64_t lds = (a.epi == TC_EPI_ADD_OUT) ? a.ldc1 : a.ldc;
-      const int nsc = (int)std::min<int64_t>(4, (a.N - n0 + 31) / 32);   // column segments
-      const int nseg = mh * nsc;
-      // segment s: half s / nsc, columns (s % nsc) * 32 .. ; rows of this warp in range?
-      auto seg_rows = [&](int sidx) -> int64_t { return m0 + (sidx / nsc) * 128 + e * 32; };
-      auto seg_live = [&](int sidx) -> bool { return seg_rows(sidx) < a.M; };
-      auto issue = [&](int sidx) {
-        const int b = sidx & 1;
-        if (!seg_live(sidx)) return;
-        ++fills[b];
-        if (lane == 0) {
-          const int64_t row0 = seg_rows(sidx), gc0 = n0 + (sidx % nsc) * 32;
-          const int ncol = (int)std::min<int64_t>(32, a.N - gc0);
-          mbar_expect_tx(&efull[b], (uint32_t)(ncol * 32 * 4));
-          for (int c = 0; c < ncol; ++c)
-            bulk_g2s(ebuf + b * T4_EPIB + c * 128, src + row0 + (gc0 + c) * lds, 128, &efull[b]);
-        }
-      };
-      if (bulk) {
-        if (nseg > 0) issue(0);
-        if (nseg > 1) issue(1);
-      }
-      bool ok = wwait(&acc_full[buf], (uint32_t)(it / 2) & 1, fail);
-      if (!__all_sync(0xffffffffu, ok ? 1 : 0)) { stop = true; break; }
-      tc_fence_after();
-      if (!bulk) {
-        for (int h = 0; h < mh; ++h) {
-          const int64_t row = m0 + h * 128 + e * 32 + lane;
-          for (int cc = 0; cc < T4_BN; cc += 32) {
-            if (n0 + cc >= a.N) break;
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(e * 32) << 16) + (uint32_t)(buf * 256 + h * T4_BN + cc), v);
-            tc_epi32(a, C, C1, row, n0 + cc, v);
-          }
-        }
-      } else {
-        for (int sidx = 0; sidx < nseg; ++sidx) {
-          const int b = sidx & 1, h = sidx / nsc, cc = (sidx % nsc) * 32;
-          const bool live = seg_live(sidx);
-          if (live) {
-            const bool got = wwait(&efull[b], (uint32_t)cons[b] & 1, fail);
-            ++cons[b];
-            if (!__all_sync(0xffffffffu, got ? 1 : 0)) { stop = true; break; }
-          }
+      for (int h = 0; h < mh; ++h) {
+        const int64_t row = m0 + h * 128 + e * 32 + lane;
+        for (int cc = 0; cc < T4_BN; cc += 32) {
+          if (n0 + cc >= a.N) break;
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(e * 32) << 16) + (uint32_t)(buf * 256 + h * T4_BN + cc), v);
-          if (live) {
-            const int64_t row = seg_rows(sidx) + lane, gc0 = n0 + cc;
-            const int ncol = (int)std::min<int64_t>(32, a.N - gc0);
-            const float* old = reinterpret_cast<const float*>(ebuf + b * T4_EPIB) + lane;
-            float* Cr = C + row + gc0 * a.ldc;
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              if (i < ncol) {
-                const float o = old[i * 32];
-                Cr[(int64_t)i * a.ldc] = (a.epi == TC_EPI_SUB) ? o - v[i] : v[i] + o;
-              }
-            }
-          }
-          __syncwarp();
-          fence_async_smem();   // the buffer's generic reads precede its next bulk refill
-          if (sidx + 2 < nseg) issue(sidx + 2);
+          tc_epi32(a, C, C1, row, n0 + cc, v);
         }
-        if (stop) break;
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive1(&acc_empty[buf]);
     }
-    // copies requested but not consumed (a stop) are waited for before the CTA exits
-    for (int b = 0; b < 2; ++b)
-      while (cons[b] < fills[b]) {
-        wwait(&efull[b], (uint32_t)cons[b] & 1, fail, false);
-        ++cons[b];
-      }
   }
   tc_fence_before();
   __syncthreads();
@@ -970,17 +896,8 @@ void launch_tc2(const TcArgs& a, int batch, const char* name, cudaStream_t s) {
     // and operand kernels of the next steps keep SMs of their own (a grid over every SM held
     // them off for whole launches; short-lived CTAs cost the pipeline fill and drain of each)
     const int ctas = (int)std::min<int64_t>(total, std::max(1, sms - sms / 9));
-    // the epilogue's old values come by 128-byte bulk copies when every 32-row group of C
-    // (C1 for W = C1 + A B) starts on a 16-byte boundary
-    TcArgs a4 = a;
-    const float* esrc = a.epi == TC_EPI_ADD_OUT ? a.C1 : a.C;
-    const int64_t eld = a.epi == TC_EPI_ADD_OUT ? a.ldc1 : a.ldc;
-    const int64_t est = a.epi == TC_EPI_ADD_OUT ? a.sC1 : a.sC;
-    a4.epi_bulk = (a.epi != TC_EPI_OUT && esrc != nullptr &&
-                   (reinterpret_cast<uintptr_t>(esrc) % 16) == 0 && (eld % 4) == 0 &&
-                   (est % 4) == 0 && (a.M % 32) == 0) ? 1 : 0;
     ensure_dyn_smem<k_gemm_tc4>(T4_SMEM);
-    k_gemm_tc4<<<ctas, T4_THREADS, T4_SMEM, s>>>(a4, mtiles, ntiles, (int)total);
+    k_gemm_tc4<<<ctas, T4_THREADS, T4_SMEM, s>>>(a, mtiles, ntiles, (int)total);
   } else {
     ensure_dyn_smem<k_gemm_tc2>(P_SMEM);
     k_gemm_tc2<<<grid, TC_THREADS, P_SMEM, s>>>(a);
