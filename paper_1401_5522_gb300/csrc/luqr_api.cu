@@ -76,9 +76,6 @@ struct luqr_handle {
   uint8_t* qrfac = nullptr;     // QR chosen and not speculated: factor in place
   uint8_t* cmt = nullptr;       // QR chosen and speculated: commit the shadow copy
   void* shadow = nullptr;       // Npad x nb copy of the panel column (same leading dimension)
-  void* shadow2 = nullptr;      // Npad x nb copy of column k+1 for the speculative look-ahead
-  cudaStream_t specla_stream = nullptr;   // speculative look-ahead on shadow2
-  std::vector<cudaEvent_t> ev_specla;
   cudaStream_t spec_stream = nullptr;
   cudaStream_t panel_stream = nullptr;   // high priority; the caller's stream waits on it
   cudaStream_t la_stream = nullptr;      // look-ahead column, one tree level behind the panel
@@ -327,11 +324,9 @@ void enqueue_qr(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, bool do
                 const cudaEvent_t* rec = nullptr, const cudaEvent_t* wait = nullptr) {
   const int n = h->n, nb = h->nb;
   Mat<T> F{fbase ? fbase : wsT<T>(h), h->Npad};
-  // the apply phase reads V where the factor phase wrote it (the workspace, or the shadow
-  // copy of a speculated panel) and is gated like it (fdec: speculation / resolution gates)
-  Mat<const T> Fc{fbase ? fbase : wsT<T>(h), h->Npad};
+  Mat<const T> Fc{wsT<T>(h), h->Npad};
   T* Tk = static_cast<T*>(h->Tbuf) + (size_t)k * t_step_elems(h);
-  const uint8_t* dec = fdec ? fdec : h->dec;
+  const uint8_t* dec = h->dec;
   const uint8_t* fd = fdec ? fdec : h->dec;
   constexpr bool is_f32 = std::is_same<T, float>::value;
   tc = tc && is_f32 && h->use_tc_qr;
@@ -491,24 +486,8 @@ void enqueue_factor(luqr_handle* h) {
       cudaStreamWaitEvent(sp, h->ev_stats[k], 0);
       launch_gated_copy<T>(W + r0 + r0 * ld, ld, shadow + r0, ld, h->Npad - r0, nb, h->spec, k,
                            DEC_QR, "k_spec_copy", sp);
-      const bool la_spec = r1 < la_end;   // column k+1 exists
-      enqueue_qr<T>(h, k, F, 0, 0, true, false, sp, true, shadow - r0 * ld, h->spec, false,
-                    la_spec ? h->ev_lvl.data() : nullptr);
+      enqueue_qr<T>(h, k, F, 0, 0, true, false, sp, true, shadow - r0 * ld, h->spec, false);
       cudaEventRecord(h->ev_spec[k], sp);
-      if (la_spec) {
-        // speculative look-ahead: step k's predicted QR applied, level by level as the
-        // shadow chain produces it, to a copy of column k+1 (complete once step k-1's bulk
-        // update is), committed with the shadow panel when the criterion confirms QR
-        cudaStream_t ssl = h->specla_stream;
-        T* shadow2 = static_cast<T*>(h->shadow2);
-        cudaStreamWaitEvent(ssl, h->ev_stats[k], 0);
-        if (k > 0) cudaStreamWaitEvent(ssl, h->ev_rest[k - 1], 0);
-        launch_gated_copy<T>(W + r0 + r1 * ld, ld, shadow2 + r0, ld, h->Npad - r0, nb, h->spec, k,
-                             DEC_QR, "k_spec_copy_la", ssl);
-        enqueue_qr<T>(h, k, Mat<T>{shadow2 - r1 * ld, ld}, r1, la_end, false, true, ssl, false,
-                      shadow - r0 * ld, h->spec, true, nullptr, h->ev_lvl.data());
-        cudaEventRecord(h->ev_specla[k], ssl);
-      }
     }
     T* Tkk = static_cast<T*>(h->Tbuf) + (size_t)k * t_step_elems(h) +
              (size_t)k * 2 * t_block_elems(h);   // T slot of tile (k, k), GEQRT kind
@@ -553,11 +532,6 @@ void enqueue_factor(luqr_handle* h) {
       cudaStreamWaitEvent(s, h->ev_spec[k], 0);
       launch_gated_copy<T>(shadow + r0, ld, W + r0 + r0 * ld, ld, h->Npad - r0, nb, h->cmt, k,
                            DEC_QR, "k_spec_commit", s);
-      if (r1 < la_end) {
-        cudaStreamWaitEvent(s, h->ev_specla[k], 0);
-        launch_gated_copy<T>(static_cast<T*>(h->shadow2) + r0, ld, W + r0 + r1 * ld, ld,
-                             h->Npad - r0, nb, h->cmt, k, DEC_QR, "k_spec_commit_la", s);
-      }
     } else {
       enqueue_qr<T>(h, k, F, 0, 0, true, false, s, true, nullptr, nullptr, !tcqr,
                     piped ? h->ev_lvl.data() : nullptr);
@@ -598,10 +572,8 @@ void enqueue_factor(luqr_handle* h) {
       cudaStreamWaitEvent(sl, spec ? h->ev_fact[k] : h->ev_lvl[0], 0);
       if (k > 0) cudaStreamWaitEvent(sl, h->ev_rest[k - 1], 0);
       enqueue_lu_apply<T>(h, k, F, r1, la_end, sl, true);
-      // speculation: a confirmed prediction already updated column k+1 (committed copy);
-      // only a QR step that was not speculated is applied here
-      enqueue_qr<T>(h, k, F, r1, la_end, false, true, sl, false, nullptr, spec ? h->qrfac : nullptr,
-                    true, nullptr, piped ? h->ev_lvl.data() : nullptr);
+      enqueue_qr<T>(h, k, F, r1, la_end, false, true, sl, false, nullptr, nullptr, true, nullptr,
+                    piped ? h->ev_lvl.data() : nullptr);
       cudaEventRecord(h->ev_la[k], sl);
       cudaStreamWaitEvent(s, h->ev_la[k], 0);
     }
@@ -700,8 +672,6 @@ void free_handle(luqr_handle* h) {
   if (h->ev_start) cudaEventDestroy(h->ev_start);
   for (cudaEvent_t e : h->ev_stats) if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : h->ev_spec) if (e) cudaEventDestroy(e);
-  for (cudaEvent_t e : h->ev_specla) if (e) cudaEventDestroy(e);
-  if (h->specla_stream) cudaStreamDestroy(h->specla_stream);
   if (h->ev_end) cudaEventDestroy(h->ev_end);
   if (h->upd_stream) cudaStreamDestroy(h->upd_stream);
   if (h->spec_stream) cudaStreamDestroy(h->spec_stream);
@@ -718,7 +688,7 @@ void free_handle(luqr_handle* h) {
                   h->Apk[0], h->Apk[1],   h->Lpk[0],   h->Lpk[1], h->feat, h->spec,
                   h->Linv[0], h->Linv[1], h->Xpk[0],   h->Xpk[1],
                   h->qrfac,  h->cmt,      h->shadow, h->gate_all, h->a2gate, h->rq,
-                  h->rq_ctl, h->St, h->dpiv_all, h->shadow2};
+                  h->rq_ctl, h->St, h->dpiv_all};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -970,7 +940,6 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
     A((void**)&h->qrfac, (size_t)n);
     A((void**)&h->cmt, (size_t)n);
     A(&h->shadow, (size_t)h->Npad * nb * h->elt);
-    A(&h->shadow2, (size_t)h->Npad * nb * h->elt);
   }
   int prio_low = 0, prio_high = 0;
   if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
@@ -980,8 +949,6 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
     e = cudaStreamCreateWithPriority(&h->panel_stream, cudaStreamNonBlocking, prio_high);
   if (e == cudaSuccess && o.speculate)
     e = cudaStreamCreateWithPriority(&h->spec_stream, cudaStreamNonBlocking, prio_high);
-  if (e == cudaSuccess && o.speculate)
-    e = cudaStreamCreateWithPriority(&h->specla_stream, cudaStreamNonBlocking, prio_high);
   if (e == cudaSuccess)
     e = cudaStreamCreateWithPriority(&h->la_stream, cudaStreamNonBlocking, prio_high);
   if (e == cudaSuccess)
@@ -1006,11 +973,9 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   if (o.speculate) {
     h->ev_stats.assign(n, nullptr);
     h->ev_spec.assign(n, nullptr);
-    h->ev_specla.assign(n, nullptr);
     for (int q = 0; q < n && e == cudaSuccess; ++q) {
       e = cudaEventCreateWithFlags(&h->ev_stats[q], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_spec[q], cudaEventDisableTiming);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_specla[q], cudaEventDisableTiming);
     }
   }
   if (o.timeout_ms > 0) h->wait_cycles = (long long)o.timeout_ms * 2070000LL;  // cycles at 2.07 GHz
