@@ -42,6 +42,12 @@ def parse(argv=None):
     p.add_argument("--criterion", default="max")
     p.add_argument("--alpha", type=float, default=100.0)
     p.add_argument("--tree", default="binary_tt")
+    p.add_argument("--tree-small", default="flat_ts",
+                   help="tree of the steps with fewer than --tree-switch sub-diagonal tiles")
+    p.add_argument("--tree-switch", type=int, default=0)
+    p.add_argument("--tune-tree", type=int, default=0,
+                   help="time candidate tree policies on the input (untimed setup) and use the "
+                        "fastest")
     p.add_argument("--precision", default="fp32")
     p.add_argument("--tol", type=float, default=1e-13)
     p.add_argument("--fp32-kernels", default="default", choices=["default", "cuda", "tensor"])
@@ -64,6 +70,15 @@ def parse(argv=None):
 
 
 # ------------------------------------------------------------------ flop model
+def tree_at(tree, m):
+    """The tree of a step with m sub-diagonal tiles: `tree` is a name, or a policy
+    (tree, tree_small, tree_switch) that takes tree_small below tree_switch tiles."""
+    if isinstance(tree, (tuple, list)):
+        big, small, switch = tree
+        return small if switch > 0 and m < switch else big
+    return tree
+
+
 def step_kernel_flops(dec, n, nb, tree, ncols_extra, replay=False):
     """Algorithmic flops per kernel class for one factorization (replay=False) or one
     second-pass solve on a single right-hand side (replay=True).  Per Table I:
@@ -78,13 +93,14 @@ def step_kernel_flops(dec, n, nb, tree, ncols_extra, replay=False):
     for k in range(n):
         m = n - 1 - k
         cols = 1.0 if replay else m * nb + ncols_extra
+        t = tree_at(tree, m)
         if dec[k] == 1:
             if not replay:
                 add("k_trsm", m * nb3)
             add("k_swptrsm", cols * nb * nb)
             add("k_gemm_update", 2.0 * m * nb * cols * nb)
         else:
-            if tree == "binary_tt":
+            if t == "binary_tt":
                 if not replay:
                     add("k_geqrt", (m + 1) * 4.0 / 3.0 * nb3)
                     add("k_ttqrt", m * 2.0 / 3.0 * nb3)
@@ -125,7 +141,7 @@ def step_tc_bytes(dec, n, nb, tree, ncols_extra):
                 add("k_tc_lu_apply", 8.0 * nb * cols + a_op)
             add("k_tc_lu_gemm", 4.0 * (rows * nb + nb * cols + 2.0 * rows * cols))
             continue
-        if tree == "binary_tt":
+        if tree_at(tree, m) == "binary_tt":
             singles, pairs, kind = m + 1, m, "tt"
         else:
             singles, pairs, kind = 1, m, "ts"
@@ -152,7 +168,7 @@ def update_work(dec, n, nb, tree, s_c):
         by += 2.0 * s_c * (m + 1) * nb * cols
         if dec[k] == 1:
             fl += nb * nb * cols + 2.0 * m * nb * nb * cols
-        elif tree == "binary_tt":
+        elif tree_at(tree, m) == "binary_tt":
             fl += (m + 1) * 2.0 * nb * nb * cols + m * 2.0 * nb * nb * cols
         else:
             fl += 2.0 * nb * nb * cols + m * 4.0 * nb * nb * cols
@@ -618,9 +634,21 @@ def main():
                               else (None, None))
     if args.speculate == "mlp":
         spec["mlp_params"] = mlp_params
+    policy = (args.tree, args.tree_small, args.tree_switch)
+    tuning = None
+    if args.tune_tree:
+        from paper_1401_5522_gb300 import autotune
+        policy, table = autotune.tune_tree(A, nb, args.criterion, args.alpha, args.precision,
+                                           fp32_kernels=args.fp32_kernels)
+        tuning = {"chosen": list(policy),
+                  "factor_ms": [[list(p), round(t, 2)] for p, t in table]}
+        config["tree"], config["tree_small"], config["tree_switch"] = policy
+    elif args.tree_switch:
+        config["tree_small"], config["tree_switch"] = args.tree_small, args.tree_switch
 
     def one_solve():
-        h = luqr.factor(A, nb, args.criterion, args.alpha, tree=args.tree, precision=args.precision,
+        h = luqr.factor(A, nb, args.criterion, args.alpha, tree=policy[0], tree_small=policy[1],
+                        tree_switch=policy[2], precision=args.precision,
                         fp32_kernels=args.fp32_kernels, **spec)
         st, its, eta = h.refine(A, b, x, tol=args.tol, max_iter=30)
         dec, _ = h.decisions()
@@ -677,11 +705,11 @@ def main():
     n = len(dec)
 
     # ---------------- roofline of the dominant kernel (CUDA events inside the timed region)
-    fac = step_kernel_flops(dec, n, nb, args.tree, 0, replay=False)
-    rep = step_kernel_flops(dec, n, nb, args.tree, 0, replay=True)
+    fac = step_kernel_flops(dec, n, nb, policy, 0, replay=False)
+    rep = step_kernel_flops(dec, n, nb, policy, 0, replay=True)
     total_alg = {k: args.steps * fac.get(k, 0.0) + sum(iters) * rep.get(k, 0.0)
                  for k in set(fac) | set(rep)}
-    tc_bytes = step_tc_bytes(dec, n, nb, args.tree, 0) if args.precision == "fp32" else {}
+    tc_bytes = step_tc_bytes(dec, n, nb, policy, 0) if args.precision == "fp32" else {}
     # the profiler labels launches by role; the dominant kernel is the CUDA function with the
     # most device time, summed over the roles it serves
     funcs = {}
@@ -704,7 +732,7 @@ def main():
             # algorithmic work (trailing matrix read + written once per step; Table I update
             # flops) of the bulk update over the timed steps, per the kernel's own launch time
             peaks = load_peaks()
-            ub, uf = update_work(dec, n, nb, args.tree, 4)
+            ub, uf = update_work(dec, n, nb, policy, 4)
             alg_bytes = args.steps * ub
             gbs = alg_bytes / (tot_ms / 1e3) / 1e9
             tf32_peak = peaks["bf16_tflops_sustained"] * TF32_PER_BF16
@@ -845,7 +873,7 @@ def main():
                                                     if "pred" in info else None)},
             "plain_fp64": plain, "roofline": roofline, "gpu_launches": gpu_launches,
             "kernels": kernel_table, "kernels_scope": "one extra profiled solve (all kernels timed)",
-            "e2e": e2e, "clocks": clk, "forms": forms, "configs": sweep,
+            "e2e": e2e, "clocks": clk, "forms": forms, "configs": sweep, "tree_tuning": tuning,
             "cpu_baseline": cpu_baseline_dict(cpu, args)}
     print(json.dumps(line))
     if world > 1:

@@ -125,7 +125,13 @@ typedef struct luqr_options {
                               and an LU step applies the exchanges to columns k.. of those rows
                               and to b before the tile LU step.  Needs speculate = 0 and
                               lu_variant = 0; luqr_factor only. */
-  int reserved[1];
+  int tree_small;          /* per-step tree (Alg. 3 leaves the eliminator of each tile free):
+                              the tree (LUQR_TREE_*) of the steps below tree_switch */
+  int tree_switch;         /* steps with fewer than tree_switch sub-diagonal tiles use
+                              tree_small, the others `tree`; 0 (default) uses `tree` at every
+                              step.  The Python package's tree autotuner picks (tree,
+                              tree_small, tree_switch) by timing. */
+  int reserved[3];
 } luqr_options;
 
 typedef struct luqr_handle* luqr_handle_t;

@@ -86,6 +86,8 @@ READINGS = {
     "random_choice": "Sec. V-B's random choice: LU with probability alpha/100, u_k = SplitMix64 "
                      "output k of the seed, top 53 bits times 2^-53, LU iff u_k < alpha/100; a "
                      "zero pivot still selects QR",
+    "tree_per_step": "the elimination tree may change from step to step (Alg. 3 leaves it free); "
+                     "a two-tree policy switches below a number of sub-diagonal tiles",
     "tie": ">= in Eq. 2-4 selects LU",
     "zero_pivot": "an exact zero pivot in the diagonal GETRF selects QR (FORCE_LU raises Singular)",
     "alpha_zero": "alpha = 0 selects QR at every step, the last one included",
@@ -586,7 +588,8 @@ def tile_bounds(i, nb, N):
 
 def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
            forced=None, inject=(), dtype=np.float64, track_growth=False, on_step=None,
-           norm_mode=0, seed=0, domain=1, lu_variant="A1"):
+           norm_mode=0, seed=0, domain=1, lu_variant="A1", tree_small=TREE_FLAT_TS,
+           tree_switch=0):
     """Run Alg. 1 on the augmented matrix [A | b] and return the Factorization.
 
     A: N x N; b: None, N or N x nrhs.  dtype float32 emulates the whole factorization
@@ -601,6 +604,9 @@ def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
     criterion sees the pivoted panel; an LU step first applies the domain's row
     exchanges to columns k.. of those rows (and b), then runs Alg. 2 on the pivoted
     diagonal tile.  1 = pivoting inside the diagonal tile only.
+    ``tree_small``, ``tree_switch``: steps with fewer than tree_switch sub-diagonal tiles
+    eliminate along tree_small, the others along ``tree`` (Alg. 3 leaves the tree free at
+    every step); tree_switch = 0 uses ``tree`` throughout.
     ``lu_variant``: "A1" (Alg. 2: GETRF of the tile) or "A2" (Sec. II-B: GEQRT of the
     tile; Eliminate A_ik U^-1, Apply Q^T A_kj, the same Update; a QR decision continues
     from that GEQRT).
@@ -707,7 +713,8 @@ def factor(A, b, nb, criterion, alpha, tree=TREE_FLAT_TS, group=4, mumps_mode=0,
                 _lu_step(aug, k, n, nb, N, W, LU, piv)
             fact.piv[k] = piv
         else:
-            ops = elimination_ops(k, n, tree, group)
+            tree_k = tree_small if (tree_switch > 0 and m < tree_switch) else tree
+            ops = elimination_ops(k, n, tree_k, group)
             fact.ops[k] = ops
             _qr_step(aug, k, nb, N, W, ops, fact.taus)
     return fact

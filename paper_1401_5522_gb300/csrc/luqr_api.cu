@@ -22,6 +22,7 @@ using namespace luqr;
 struct luqr_handle {
   int64_t N = 0, Npad = 0, Wc = 0;
   int nb = 0, n = 0, prec = 0, criterion = 0, tree = 0, group = 4, mumps_mode = 0;
+  int tree_small = 0, tree_switch = 0;   // per-step tree: below tree_switch sub-diagonal tiles
   int norm_mode = 0;   // 0 exact ||A_kk^-1||_1, 1 Hager-Higham estimate
   int lu_variant = 0;  // 0 A1 (GETRF of A_kk), 1 A2 (GEQRT of A_kk)
   int domain = 1;      // tiles of the diagonal pivot domain (1: the diagonal tile)
@@ -216,10 +217,12 @@ void tc_apply_pair(luqr_handle* h, int k, TileList tl, bool tri, Mat<float> C, i
 template <typename FS, typename FP>
 void for_each_tile_list(const luqr_handle* h, int k, FS&& single, FP&& pair) {
   const int n = h->n, m = n - 1 - k;
-  if (h->tree == LUQR_TREE_FLAT_TS) {
+  // per-step tree: steps with fewer than tree_switch sub-diagonal tiles use tree_small
+  const int tree = (h->tree_switch > 0 && m < h->tree_switch) ? h->tree_small : h->tree;
+  if (tree == LUQR_TREE_FLAT_TS) {
     single(TileList{k, 1, 1, 0});
     for (int i = k + 1; i < n; ++i) pair(TileList{i, 1, 1, i - k}, false);
-  } else if (h->tree == LUQR_TREE_BINARY_TT) {
+  } else if (tree == LUQR_TREE_BINARY_TT) {
     single(TileList{k, 1, m + 1, 0});
     for (int step = 1; step <= m; step *= 2) {
       const int count = (m - step) / (2 * step) + 1;
@@ -846,6 +849,7 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   if (!(alpha >= 0.0)) return LUQR_ERR_INVALID;   // rejects NaN too
   if (criterion < LUQR_MAX || criterion > LUQR_RANDOM) return LUQR_ERR_INVALID;
   if (o.tree < 0 || o.tree > 2 || o.precision < 0 || o.precision > 1) return LUQR_ERR_INVALID;
+  if (o.tree_switch < 0 || o.tree_small < 0 || o.tree_small > 2) return LUQR_ERR_INVALID;
   if (o.fp32_kernels < 0 || o.fp32_kernels > 2) return LUQR_ERR_INVALID;
   if (o.mumps_mode < 0 || o.mumps_mode > 1 || o.n_inject < 0) return LUQR_ERR_INVALID;
   if (o.norm_mode < 0 || o.norm_mode > 1) return LUQR_ERR_INVALID;
@@ -869,6 +873,8 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   h->criterion = criterion;
   h->alpha = alpha;
   h->tree = o.tree;
+  h->tree_small = o.tree_small;
+  h->tree_switch = o.tree_switch;
   h->group = o.group;
   h->mumps_mode = o.mumps_mode;
   h->norm_mode = o.norm_mode;

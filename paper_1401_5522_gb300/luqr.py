@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
                 ("log_features", ctypes.c_int), ("mlp_params", ctypes.c_void_p),
                 ("norm_mode", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("lu_variant", ctypes.c_int), ("timeout_ms", ctypes.c_int),
-                ("domain", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("domain", ctypes.c_int), ("tree_small", ctypes.c_int),
+                ("tree_switch", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 _lib = None
@@ -285,7 +286,8 @@ NORM_MODE = {"exact": 0, "estimate": 1}
 def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
            precision="fp64", mumps_mode=0, forced=None, inject=None, stream=None,
            fp32_kernels="default", speculate="off", mlp_params=None, log_features=False,
-           norm_mode="exact", seed=0, lu_variant="A1", timeout_ms=0, domain=1):
+           norm_mode="exact", seed=0, lu_variant="A1", timeout_ms=0, domain=1,
+           tree_small="flat_ts", tree_switch=0):
     """luqr_factor on a column-major float64 CUDA matrix; b (if given) is overwritten by x.
 
     speculate: "off", "mlp" (mlp_params: float32 CUDA tensor of MLP_PARAMS values, kept
@@ -293,7 +295,9 @@ def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
     norm_mode: "exact" ||A_kk^-1||_1 or "estimate" (Hager-Higham).
     criterion "random": LU with probability alpha/100 per step (SplitMix64 draws from seed).
     lu_variant: "A1" (GETRF of the diagonal tile) or "A2" (GEQRT of the diagonal tile).
-    domain: tiles of the diagonal pivot domain (1: pivoting inside the diagonal tile)."""
+    domain: tiles of the diagonal pivot domain (1: pivoting inside the diagonal tile).
+    tree_small, tree_switch: steps with fewer than tree_switch sub-diagonal tiles use the
+    tree tree_small (0: `tree` at every step)."""
     N = A.shape[0]
     lda = _check_matrix(A)
     crit = CRITERIA[criterion] if isinstance(criterion, str) else int(criterion)
@@ -306,6 +310,8 @@ def factor(A, nb, criterion="max", alpha=100.0, b=None, tree="flat_ts", group=4,
     opt.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     opt.timeout_ms = int(timeout_ms)
     opt.domain = int(domain)
+    opt.tree_small = TREES[tree_small] if isinstance(tree_small, str) else int(tree_small)
+    opt.tree_switch = int(tree_switch)
     opt.lu_variant = {"A1": 0, "A2": 1}[lu_variant] if isinstance(lu_variant, str) else int(lu_variant)
     opt.fp32_kernels = {"default": 0, "cuda": 1, "tensor": 2}[fp32_kernels]
     opt.speculate = SPECULATE[speculate] if isinstance(speculate, str) else int(speculate)

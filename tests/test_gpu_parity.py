@@ -318,3 +318,64 @@ def test_fp32_tensor_core_updates_match_cuda_core_updates(tree, crit, alpha, dd)
         x = torch.zeros(N, dtype=torch.float64, device="cuda")
         st, iters, eta = h.refine(dA, b, x, tol=1e-14, max_iter=20)
         assert st == 0 and eta <= 1e-14, (st, iters, eta)
+
+
+@pytest.mark.parametrize("big,small,switch", [("binary_tt", "flat_ts", 6),
+                                              ("grouped", "binary_tt", 4),
+                                              ("flat_ts", "grouped", 10)])
+@pytest.mark.parametrize("crit,alpha", [("max", 2000.0), ("force_qr", 0.0)])
+def test_per_step_tree_policy_matches_oracle(big, small, switch, crit, alpha):
+    """A tree that changes at a step (the small tree once fewer than `switch` sub-diagonal
+    tiles remain) against the oracle with the same policy: decisions, margins, triangle,
+    solution at the usual bars."""
+    A = gauss(544, 5)
+    N, nb = A.shape[0], 32
+    b = A @ np.ones(N)
+    x_o, f = O.solve(A, b, nb, ORACLE_CRIT[crit], alpha, tree=ORACLE_TREE[big], group=3,
+                     tree_small=ORACLE_TREE[small], tree_switch=switch)
+    h, dec, mg, x_g, st = gpu_solve(A, b, nb, crit, alpha, tree=big, group=3,
+                                    tree_small=small, tree_switch=switch)
+    assert st == 0, st
+    assert np.array_equal(dec, f.dec), (dec, f.dec)
+    fin = np.isfinite(f.margin)
+    assert np.all(np.abs(mg[fin] - f.margin[fin]) <= TOL_MARGIN)
+    assert O.backward_error(A, x_g, b) <= 1e-13
+    assert np.max(np.abs(x_g - x_o.ravel())) <= TOL_X * np.max(np.abs(x_o))
+    Ug = np.triu(h.factor_data()[:N, :N])
+    rho = np.max(np.abs(f.U)) / np.max(np.abs(A))
+    assert np.max(np.abs(Ug - f.U)) <= TOL_U * max(1.0, rho) * np.max(np.abs(f.U))
+    b2 = gauss(N, 6)[:, 0].copy()
+    y_o = O.replay_solve(f, b2).ravel()
+    x2 = torch.from_numpy(b2.copy()).cuda()
+    h.solve(x2)
+    assert h.sync() == 0
+    h.close()
+    assert np.max(np.abs(x2.cpu().numpy() - y_o)) <= TOL_X * np.max(np.abs(y_o))
+
+
+def test_tree_policy_rejects_bad_values():
+    luqr = L()
+    dA = cuda_colmajor(np.eye(64))
+    for kw in (dict(tree_switch=-1), dict(tree_small=3, tree_switch=2)):
+        with pytest.raises(luqr.LuqrError) as e:
+            luqr.factor(dA, 32, "max", 100.0, **kw)
+        assert e.value.status == luqr.ERR_INVALID
+
+
+def test_tree_autotuner_picks_a_candidate_and_keeps_decisions():
+    from paper_1401_5522_gb300 import autotune
+    luqr = L()
+    A = gauss(1024, 8)
+    dA = cuda_colmajor(A)
+    pols = [("binary_tt", "flat_ts", 0), ("binary_tt", "flat_ts", 8), ("grouped", "binary_tt", 4)]
+    best, table = autotune.tune_tree(dA, 64, "max", 2000.0, policies=pols, group=3)
+    assert best in pols and [p for p, _ in table] == pols
+    assert all(ms > 0 for _, ms in table)
+    decs = []
+    for p in pols:
+        h = luqr.factor(dA, 64, "max", 2000.0, tree=p[0], tree_small=p[1], tree_switch=p[2],
+                        group=3)
+        decs.append(h.decisions()[0])
+        h.close()
+    f = O.factor(A, None, 64, O.CRIT_MAX, 2000.0, tree=O.TREE_BINARY_TT)
+    assert all(np.array_equal(d, f.dec) for d in decs)

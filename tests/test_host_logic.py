@@ -74,3 +74,13 @@ def test_bench_update_work_follows_the_trailing_matrix_model():
     lu = np.ones(n, dtype=np.uint8)
     _, fl_lu = bench.update_work(lu, n, nb, "binary_tt", 4)
     assert fl_lu == pytest.approx((2.0 / 3.0) * N ** 3, rel=0.03)
+
+
+def test_tree_autotuner_candidates():
+    from paper_1401_5522_gb300 import autotune
+    c = autotune.candidates(128)
+    assert ("binary_tt", "flat_ts", 0) in c and ("grouped", "flat_ts", 0) in c
+    assert ("binary_tt", "flat_ts", 8) in c and ("binary_tt", "grouped", 64) in c
+    assert all(t != s for t, s, w in c if w > 0)
+    assert len(set(c)) == len(c)
+    assert {w for _, _, w in autotune.candidates(4)} == {0, 2}

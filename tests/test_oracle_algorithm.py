@@ -346,3 +346,26 @@ def test_mumps_cumulative_reading_closed_form(seed):
         sd = O.decide(O.CRIT_MUMPS, float(a), LU, piv, -1, [1.0], local, away, mumps_mode=1)
         assert sd.dec == (O.DEC_LU if np.log(a) >= tmax else O.DEC_QR)
         assert sd.margin == pytest.approx(float(np.min(np.log(a) - t)) / np.log(2.0), abs=1e-9)
+
+
+@pytest.mark.parametrize("big,small,switch", [(O.TREE_BINARY_TT, O.TREE_FLAT_TS, 8),
+                                              (O.TREE_GROUPED, O.TREE_BINARY_TT, 5),
+                                              (O.TREE_FLAT_TS, O.TREE_BINARY_TT, 20)])
+def test_per_step_tree_policy(big, small, switch):
+    """A tree that changes with the step is still Householder QR on FORCE_QR (R equal to
+    numpy's up to row signs); switch 0 is the big tree and a switch above n the small tree,
+    step for step (bitwise)."""
+    A = gauss(400, 2)
+    f = O.factor(A, None, 16, O.CRIT_FORCE_QR, 0.0, tree=big, tree_small=small,
+                 tree_switch=switch, group=3)
+    Rn = np.linalg.qr(A, mode="r")
+    sgn = np.sign(np.diag(f.U)) * np.sign(np.diag(Rn))
+    assert np.allclose(f.U, Rn * sgn[:, None], atol=1e-11 * np.abs(Rn).max())
+    g0 = O.factor(A, None, 16, O.CRIT_MAX, 2000.0, tree=big, tree_small=small, tree_switch=0,
+                  group=3)
+    g1 = O.factor(A, None, 16, O.CRIT_MAX, 2000.0, tree=big, group=3)
+    assert np.array_equal(g0.aug, g1.aug)
+    h0 = O.factor(A, None, 16, O.CRIT_MAX, 2000.0, tree=big, tree_small=small, tree_switch=99,
+                  group=3)
+    h1 = O.factor(A, None, 16, O.CRIT_MAX, 2000.0, tree=small, group=3)
+    assert np.array_equal(h0.aug, h1.aug) and np.array_equal(h0.dec, h1.dec)
