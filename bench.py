@@ -187,10 +187,12 @@ KERNEL_OF_LABEL = {
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic byte (the
 # trailing matrix read + written once per step) of the tensor-core update kernel, summed
-# over every launch of one N=8192 nb=256 solve captured with ncu; traffic grows in
-# proportion to the algorithmic bytes (the same passes at every size), so the ratio scales
-# to the benchmarked size.  None until a capture of the current kernel exists.
-TRAFFIC_RATIO = {}
+# over the 535 launches of one N=8192 nb=256 FP32 solve (binary TT tree, 31 QR steps + 1 LU)
+# captured with ncu: 30.06 GB against 5.44 GB.  ncu flushes the caches before each launch,
+# so this is the cold-cache figure.  The ratio carries over to other sizes: each QR step
+# makes the same passes (W, C and the pair passes of each tree level), and the levels of a
+# binary tree touch (m+1)(1 + 1/2 + 1/4 ...) < 2(m+1) tile rows whatever the depth.
+TRAFFIC_RATIO = {"k_gemm_tc4": 30.055 / 5.4447}
 
 
 def traffic_per_launch(kernel, alg_bytes_per_launch):
