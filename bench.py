@@ -45,6 +45,7 @@ def parse(argv=None):
     p.add_argument("--tree-small", default="flat_ts",
                    help="tree of the steps with fewer than --tree-switch sub-diagonal tiles")
     p.add_argument("--tree-switch", type=int, default=0)
+    p.add_argument("--group", type=int, default=4, help="group size of the grouped tree")
     p.add_argument("--tune-tree", type=int, default=0,
                    help="time candidate tree policies on the input (untimed setup) and use the "
                         "fastest")
@@ -72,11 +73,29 @@ def parse(argv=None):
 # ------------------------------------------------------------------ flop model
 def tree_at(tree, m):
     """The tree of a step with m sub-diagonal tiles: `tree` is a name, or a policy
-    (tree, tree_small, tree_switch) that takes tree_small below tree_switch tiles."""
+    (tree, tree_small, tree_switch[, group]) that takes tree_small below tree_switch tiles."""
     if isinstance(tree, (tuple, list)):
-        big, small, switch = tree
+        big, small, switch = tree[:3]
         return small if switch > 0 and m < switch else big
     return tree
+
+
+def group_of(tree):
+    return tree[3] if isinstance(tree, (tuple, list)) and len(tree) > 3 else 4
+
+
+def tree_counts(tree, m):
+    """(GEQRT singles, TS pairs, TT pairs) of a QR step with m sub-diagonal tiles, as the
+    library's tile lists build them: flat TS 1 / m / 0; binary TT m+1 / 0 / m; grouped
+    (groups of g tiles, H = ceil((m+1)/g) heads) H / m+1-H / H-1."""
+    t = tree_at(tree, m)
+    if t == "flat_ts":
+        return 1, m, 0
+    if t == "binary_tt":
+        return m + 1, 0, m
+    g = group_of(tree)
+    H = (m + 1 + g - 1) // g
+    return H, m + 1 - H, H - 1
 
 
 def step_kernel_flops(dec, n, nb, tree, ncols_extra, replay=False):
@@ -93,34 +112,29 @@ def step_kernel_flops(dec, n, nb, tree, ncols_extra, replay=False):
     for k in range(n):
         m = n - 1 - k
         cols = 1.0 if replay else m * nb + ncols_extra
-        t = tree_at(tree, m)
         if dec[k] == 1:
             if not replay:
                 add("k_trsm", m * nb3)
             add("k_swptrsm", cols * nb * nb)
             add("k_gemm_update", 2.0 * m * nb * cols * nb)
         else:
-            if t == "binary_tt":
-                if not replay:
-                    add("k_geqrt", (m + 1) * 4.0 / 3.0 * nb3)
-                    add("k_ttqrt", m * 2.0 / 3.0 * nb3)
-                add("k_unmqr", (m + 1) * 2.0 * nb * nb * cols)
-                add("k_ttmqr", m * 2.0 * nb * nb * cols)
-            else:   # flat TS (grouped counted as flat for the model)
-                if not replay:
-                    add("k_geqrt", 4.0 / 3.0 * nb3)
-                    add("k_tsqrt", m * 2.0 * nb3)
-                add("k_unmqr", 2.0 * nb * nb * cols)
-                add("k_tsmqr", m * 4.0 * nb * nb * cols)
+            singles, ts, tt = tree_counts(tree, m)
+            if not replay:
+                add("k_geqrt", singles * 4.0 / 3.0 * nb3)
+                add("k_tsqrt", ts * 2.0 * nb3)
+                add("k_ttqrt", tt * 2.0 / 3.0 * nb3)
+            add("k_unmqr", singles * 2.0 * nb * nb * cols)
+            add("k_tsmqr", ts * 4.0 * nb * nb * cols)
+            add("k_ttmqr", tt * 2.0 * nb * nb * cols)
         if not replay:
             add("k_getrf", 2.0 / 3.0 * nb3)
-    return out
+    return {k: v for k, v in out.items() if v}
 
 
 def step_tc_bytes(dec, n, nb, tree, ncols_extra):
     """Algorithmic HBM bytes per tensor-core update kernel for one FP32 factorization:
     every launch reads its B operand and C (when accumulated), writes C, and reads its
-    nb x nb FP32 A operand once.  W = V^T C (UNMQR) / W = C1 + V2^T C2 (TT pair);
+    nb x nb FP32 A operand once.  W = V^T C (UNMQR) / W = C1 + V2^T C2 (TS/TT pair);
     C -= (V T^T) W; C1 -= T^T W; C2 -= (V2 T^T) W; LU: row k <- X row k (X = L^-1 P, in
     place) and C -= L U.  The tensor-core kernels update the bulk columns only: tile
     column k+1 goes through the look-ahead's CUDA-core kernels."""
@@ -141,15 +155,14 @@ def step_tc_bytes(dec, n, nb, tree, ncols_extra):
                 add("k_tc_lu_apply", 8.0 * nb * cols + a_op)
             add("k_tc_lu_gemm", 4.0 * (rows * nb + nb * cols + 2.0 * rows * cols))
             continue
-        if tree_at(tree, m) == "binary_tt":
-            singles, pairs, kind = m + 1, m, "tt"
-        else:
-            singles, pairs, kind = 1, m, "ts"
+        singles, ts, tt = tree_counts(tree, m)
         add("k_tc_unmqr_w", singles * (8.0 * nb * cols + a_op))
         add("k_tc_unmqr_c", singles * (12.0 * nb * cols + a_op))
-        add(f"k_tc_{kind}mqr_w", pairs * (12.0 * nb * cols + a_op))
-        add(f"k_tc_{kind}mqr_c1", pairs * (12.0 * nb * cols + a_op))
-        add(f"k_tc_{kind}mqr_c2", pairs * (12.0 * nb * cols + a_op))
+        for kind, pairs in (("ts", ts), ("tt", tt)):
+            if pairs:
+                add(f"k_tc_{kind}mqr_w", pairs * (12.0 * nb * cols + a_op))
+                add(f"k_tc_{kind}mqr_c1", pairs * (12.0 * nb * cols + a_op))
+                add(f"k_tc_{kind}mqr_c2", pairs * (12.0 * nb * cols + a_op))
     return out
 
 
@@ -168,10 +181,9 @@ def update_work(dec, n, nb, tree, s_c):
         by += 2.0 * s_c * (m + 1) * nb * cols
         if dec[k] == 1:
             fl += nb * nb * cols + 2.0 * m * nb * nb * cols
-        elif tree_at(tree, m) == "binary_tt":
-            fl += (m + 1) * 2.0 * nb * nb * cols + m * 2.0 * nb * nb * cols
         else:
-            fl += 2.0 * nb * nb * cols + m * 4.0 * nb * nb * cols
+            singles, ts, tt = tree_counts(tree, m)
+            fl += (2.0 * singles + 4.0 * ts + 2.0 * tt) * nb * nb * cols
     return by, fl
 
 
@@ -636,7 +648,7 @@ def main():
                               else (None, None))
     if args.speculate == "mlp":
         spec["mlp_params"] = mlp_params
-    policy = (args.tree, args.tree_small, args.tree_switch)
+    policy = (args.tree, args.tree_small, args.tree_switch, args.group)
     tuning = None
     if args.tune_tree:
         from paper_1401_5522_gb300 import autotune
@@ -644,13 +656,14 @@ def main():
                                            fp32_kernels=args.fp32_kernels)
         tuning = {"chosen": list(policy),
                   "factor_ms": [[list(p), round(t, 2)] for p, t in table]}
-        config["tree"], config["tree_small"], config["tree_switch"] = policy
-    elif args.tree_switch:
+        config["tree"], config["tree_small"], config["tree_switch"], config["group"] = policy
+    elif args.tree_switch or args.tree == "grouped":
         config["tree_small"], config["tree_switch"] = args.tree_small, args.tree_switch
+        config["group"] = args.group
 
     def one_solve():
         h = luqr.factor(A, nb, args.criterion, args.alpha, tree=policy[0], tree_small=policy[1],
-                        tree_switch=policy[2], precision=args.precision,
+                        tree_switch=policy[2], group=policy[3], precision=args.precision,
                         fp32_kernels=args.fp32_kernels, **spec)
         st, its, eta = h.refine(A, b, x, tol=args.tol, max_iter=30)
         dec, _ = h.decisions()

@@ -440,11 +440,12 @@ void qr_step(const Aug<R>& A, int k, const std::vector<Op>& ops, int threads) {
 // per step (DEC_NONE / NaN past the last step run).
 template <typename R>
 int factor(R* aug, int64_t ld, int64_t N, int64_t W, int nb, int criterion, double alpha, int tree,
-           int group, int mumps_mode, const uint8_t* forced, const int* inject, int n_inject,
+           int group, int tree_small, int tree_switch, int mumps_mode, const uint8_t* forced, const int* inject, int n_inject,
            uint64_t seed, int threads, int max_steps, uint8_t* dec, double* margin, double* lhs,
            double* rhs, int* where, int* steps_done) {
   if (!aug || N < 1 || nb < 1 || ld < N || W < N || criterion < CRIT_MAX ||
-      criterion > CRIT_RANDOM || !(alpha >= 0.0) || tree < 0 || tree > 2)
+      criterion > CRIT_RANDOM || !(alpha >= 0.0) || tree < 0 || tree > 2 || tree_small < 0 ||
+      tree_small > 2 || tree_switch < 0)
     return E_INVALID;
   const int n = (int)((N + nb - 1) / nb);
   Aug<R> A{aug, ld, N, W, nb, n};
@@ -513,7 +514,11 @@ int factor(R* aug, int64_t ld, int64_t N, int64_t W, int nb, int criterion, doub
     lhs[k] = sd.lhs;
     rhs[k] = sd.rhs;
     if (sd.dec == DEC_LU) lu_step(A, k, LU, piv.data(), threads);
-    else qr_step(A, k, elimination_ops(k, n, tree, group), threads);
+    else   // the tree of this step: tree_small below tree_switch sub-diagonal tiles
+      qr_step(A, k,
+              elimination_ops(k, n, (tree_switch > 0 && n - 1 - k < tree_switch) ? tree_small : tree,
+                              group),
+              threads);
     *steps_done = k + 1;
   }
   return OK;
@@ -548,21 +553,25 @@ int backsolve(const R* aug, int64_t ld, int64_t N, int64_t nrhs, double* x, int6
 extern "C" {
 
 int luqr_oracle_mt_factor_f64(double* aug, int64_t ld, int64_t N, int64_t W, int nb, int criterion,
-                              double alpha, int tree, int group, int mumps_mode,
+                              double alpha, int tree, int group, int tree_small,
+                              int tree_switch, int mumps_mode,
                               const uint8_t* forced, const int* inject, int n_inject, uint64_t seed,
                               int threads, int max_steps, uint8_t* dec, double* margin, double* lhs,
                               double* rhs, int* where, int* steps_done) {
-  return factor<double>(aug, ld, N, W, nb, criterion, alpha, tree, group, mumps_mode, forced,
+  return factor<double>(aug, ld, N, W, nb, criterion, alpha, tree, group, tree_small,
+                        tree_switch, mumps_mode, forced,
                         inject, n_inject, seed, threads, max_steps, dec, margin, lhs, rhs, where,
                         steps_done);
 }
 
 int luqr_oracle_mt_factor_f32(float* aug, int64_t ld, int64_t N, int64_t W, int nb, int criterion,
-                              double alpha, int tree, int group, int mumps_mode,
+                              double alpha, int tree, int group, int tree_small,
+                              int tree_switch, int mumps_mode,
                               const uint8_t* forced, const int* inject, int n_inject, uint64_t seed,
                               int threads, int max_steps, uint8_t* dec, double* margin, double* lhs,
                               double* rhs, int* where, int* steps_done) {
-  return factor<float>(aug, ld, N, W, nb, criterion, alpha, tree, group, mumps_mode, forced,
+  return factor<float>(aug, ld, N, W, nb, criterion, alpha, tree, group, tree_small,
+                        tree_switch, mumps_mode, forced,
                        inject, n_inject, seed, threads, max_steps, dec, margin, lhs, rhs, where,
                        steps_done);
 }

@@ -56,6 +56,7 @@ def lib():
         L = ctypes.CDLL(LIB)
         args = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                 ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                ctypes.c_int, ctypes.c_int,
                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                 ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                 ctypes.c_void_p, ctypes.c_void_p]
@@ -101,7 +102,7 @@ def _ptr(a):
 
 
 def factor(A, b, nb, criterion, alpha, tree=0, group=4, mumps_mode=0, forced=None, inject=(),
-           dtype=np.float64, seed=0, threads=None, steps=None):
+           dtype=np.float64, seed=0, threads=None, steps=None, tree_small=0, tree_switch=0):
     """Alg. 1 on [A | b]; same arguments and decisions as luqr_oracle.factor.
 
     ``steps``: run only the first ``steps`` panels (a prefix); ``threads``: worker threads
@@ -129,7 +130,7 @@ def factor(A, b, nb, criterion, alpha, tree=0, group=4, mumps_mode=0, forced=Non
     fn = lib().luqr_oracle_mt_factor_f64 if dtype == np.float64 else lib().luqr_oracle_mt_factor_f32
     assert dtype in (np.float64, np.float32)
     st = fn(_ptr(aug), N, N, N + nrhs, nb, int(criterion), float(alpha), int(tree), int(group),
-            int(mumps_mode), _ptr(fz), _ptr(inj) if len(inj) else None, len(inj), int(seed),
+            int(tree_small), int(tree_switch), int(mumps_mode), _ptr(fz), _ptr(inj) if len(inj) else None, len(inj), int(seed),
             th, -1 if steps is None else int(steps), _ptr(dec), _ptr(margin), _ptr(lhs), _ptr(rhs),
             _ptr(where), _ptr(done))
     if st == -5:

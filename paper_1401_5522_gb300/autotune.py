@@ -7,10 +7,12 @@ sub-diagonal tiles, `tree_small` below that.  Which policy is fastest depends on
 machine, the tile size and the number of tiles, so this module times candidate policies on
 the GPU and returns the fastest.
 
-Decisions do not depend on the tree: the QR factor R of a panel is unique up to the signs of
-its rows, every criterion reads norms, and so the trailing matrix each criterion sees differs
-between trees by rounding only.  The tuner can therefore time the caller's own criterion on
-a probe matrix drawn from the same recipe (or on the caller's matrix, which it copies).
+The tree changes more than the speed.  A QR step's R block is unique up to row signs, but the
+rows below it are the trailing matrix multiplied by an orthogonal factor that depends on the
+tree, and the per-tile norms the criteria read are not invariant under it: two policies can
+take different decisions on the same matrix (both correct runs of the method).  The tuner
+therefore times the caller's own criterion on the caller's matrix (or a probe drawn from the
+same recipe), and each policy has its own oracle run to be checked against.
 
 Marshalling and timing only: every factorization runs in libluqr.so.
 """
@@ -25,25 +27,27 @@ from . import luqr
 TREE_NAMES = ("flat_ts", "binary_tt", "grouped")
 
 
-def candidates(n_tiles, trees=("binary_tt", "grouped"), small=TREE_NAMES,
-               switches=None):
-    """Candidate (tree, tree_small, tree_switch) policies for a matrix of n_tiles tile rows:
-    every big tree alone, and every (big, small) pair with the switch at 1/16, 1/8, 1/4 and
-    1/2 of the tile count (at least 2 tiles)."""
+def candidates(n_tiles, trees=("binary_tt", "grouped"), small=("binary_tt", "grouped"),
+               switches=None, groups=(4, 8)):
+    """Candidate policies (tree, tree_small, tree_switch, group) for a matrix of n_tiles tile
+    rows: every big tree alone, and every (big, small) pair with the switch at 1/8, 1/4, 1/2
+    and 3/4 of the tile count (at least 2 tiles); the grouped tree with groups of each size
+    in `groups`."""
     if switches is None:
-        switches = sorted({max(2, n_tiles // d) for d in (16, 8, 4, 2)})
-    out = [(t, "flat_ts", 0) for t in trees]
-    for t, s, w in itertools.product(trees, small, switches):
-        if s != t:
-            out.append((t, s, int(w)))
+        switches = sorted({max(2, (n_tiles * f) // 8) for f in (1, 2, 4, 6)})
+    out = []
+    for t, s, w in [(t, "binary_tt", 0) for t in trees] + \
+            [(t, s, int(w)) for t, s, w in itertools.product(trees, small, switches) if s != t]:
+        uses_group = "grouped" in (t, s if w else t)
+        for g in (groups if uses_group else groups[:1]):
+            out.append((t, s, w, g))
     return out
 
 
-def time_policy(A, nb, criterion, alpha, policy, precision="fp64", group=4, reps=1,
-                **factor_kw):
+def time_policy(A, nb, criterion, alpha, policy, precision="fp64", reps=1, **factor_kw):
     """Median device time (ms) of `reps` factorizations of A under one policy (the solver
     reads A and factors a copy of its own, so every repetition sees the same matrix)."""
-    tree, small, switch = policy
+    tree, small, switch, group = policy
     stream = torch.cuda.current_stream()
     times = []
     for _ in range(reps):
@@ -64,17 +68,17 @@ def time_policy(A, nb, criterion, alpha, policy, precision="fp64", group=4, reps
     return times[len(times) // 2]
 
 
-def tune_tree(A, nb, criterion="max", alpha=100.0, precision="fp64", group=4, reps=1,
-              policies=None, warmup=1, **factor_kw):
+def tune_tree(A, nb, criterion="max", alpha=100.0, precision="fp64", reps=1, policies=None,
+              warmup=1, **factor_kw):
     """Time every candidate policy on A (a column-major float64 CUDA matrix) and return
     (best_policy, table), table a list of (policy, ms) in candidate order.  The tuned policy
-    is used as luqr.factor(..., tree=p[0], tree_small=p[1], tree_switch=p[2])."""
+    p is used as luqr.factor(..., tree=p[0], tree_small=p[1], tree_switch=p[2], group=p[3])."""
     luqr._check_matrix(A)
     n_tiles = (A.shape[0] + nb - 1) // nb
     pols = list(policies) if policies is not None else candidates(n_tiles)
     for _ in range(warmup):
-        time_policy(A, nb, criterion, alpha, pols[0], precision, group, 1, **factor_kw)
-    table = [(p, time_policy(A, nb, criterion, alpha, p, precision, group, reps, **factor_kw))
+        time_policy(A, nb, criterion, alpha, pols[0], precision, 1, **factor_kw)
+    table = [(p, time_policy(A, nb, criterion, alpha, p, precision, reps, **factor_kw))
              for p in pols]
     best = min(table, key=lambda pm: pm[1])[0]
     return best, table

@@ -46,30 +46,45 @@ __device__ __forceinline__ int rp_load_acquire(const int* p) {
   return v;
 }
 
+// Rows [lo, hi) of column j + jb of the reflector block jb: the nonzero part of V.
+__device__ __forceinline__ int rp_lo(bool pair, int jb) { return pair ? 0 : jb; }
+__device__ __forceinline__ int rp_hi(bool pair, bool tri, int jb, int nb) {
+  return pair ? (tri ? jb + IB : nb) : nb;
+}
+
+// Issues the cp.async copies of inner block jb (its IB columns of V and its IB x IB T block)
+// into buffer buf, as one commit group.
+template <typename T>
+__device__ void rp_stage(const T* __restrict__ V, int64_t ldv, const T* __restrict__ Tslot,
+                         int nb, bool pair, bool tri, int jb, int buf, T* Vb, T* Tb) {
+  constexpr int VEC = 16 / sizeof(T);
+  const int tid = threadIdx.x;
+  T* vs = Vb + (size_t)buf * IB * nb;
+  const int r0 = rp_lo(pair, jb), rows = rp_hi(pair, tri, jb, nb) - r0, cpc = rows / VEC;
+  for (int idx = tid; idx < IB * cpc; idx += NT) {
+    const int j = idx / cpc, q = idx - j * cpc;
+    rp_cp16(&vs[(size_t)j * nb + q * VEC], &V[r0 + q * VEC + (int64_t)(jb + j) * ldv]);
+  }
+  T* ts = Tb + buf * IB * IB;
+  for (int idx = tid; idx < IB * IB / VEC; idx += NT)
+    rp_cp16(&ts[idx * VEC], &Tslot[(size_t)jb * IB + idx * VEC]);
+  rp_commit();
+}
+
 // Q^T of one tile (pair = 0: GEQRT reflectors, unit lower V) or one tile pair (pair = 1:
 // reflector j is [e_j; V(:, j)], V upper triangular for TT) applied to the vector segments
 // xs (row i) and xe (eliminator row), inner block by inner block:
 //   w = V_b^T x_i (+ x_e(block rows) for pairs),  w2 = T_b^T w,  x_i -= V_b w2,  x_e -= w2,
-// with the next block's V and T copies in flight.
+// with the next block's V and T copies in flight.  staged0: block 0 was already staged into
+// buffer 0 (while the task waited for its inputs).
 template <typename T>
 __device__ void rp_qr_vec(const T* __restrict__ V, int64_t ldv, const T* __restrict__ Tslot,
-                          int nb, bool pair, bool tri, T* Vb, T* Tb, T* xs, T* xe, T* w, T* w2) {
-  constexpr int VEC = 16 / sizeof(T);
+                          int nb, bool pair, bool tri, T* Vb, T* Tb, T* xs, T* xe, T* w, T* w2,
+                          bool staged0) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
-  auto lo = [&](int jb) { return pair ? 0 : jb; };
-  auto hi = [&](int jb) { return pair ? (tri ? jb + IB : nb) : nb; };
-  auto stage = [&](int jb, int buf) {
-    T* vs = Vb + (size_t)buf * IB * nb;
-    const int r0 = lo(jb), rows = hi(jb) - r0, cpc = rows / VEC;
-    for (int idx = tid; idx < IB * cpc; idx += NT) {
-      const int j = idx / cpc, q = idx - j * cpc;
-      rp_cp16(&vs[(size_t)j * nb + q * VEC], &V[r0 + q * VEC + (int64_t)(jb + j) * ldv]);
-    }
-    T* ts = Tb + buf * IB * IB;
-    for (int idx = tid; idx < IB * IB / VEC; idx += NT)
-      rp_cp16(&ts[idx * VEC], &Tslot[(size_t)jb * IB + idx * VEC]);
-    rp_commit();
-  };
+  auto lo = [&](int jb) { return rp_lo(pair, jb); };
+  auto hi = [&](int jb) { return rp_hi(pair, tri, jb, nb); };
+  auto stage = [&](int jb, int buf) { rp_stage<T>(V, ldv, Tslot, nb, pair, tri, jb, buf, Vb, Tb); };
   auto vval = [&](const T* vs, int jb, int r, int j) -> T {
     const int d = jb + j;
     if (!pair) {
@@ -80,7 +95,7 @@ __device__ void rp_qr_vec(const T* __restrict__ V, int64_t ldv, const T* __restr
     }
     return vs[(size_t)j * nb + (r - lo(jb))];
   };
-  stage(0, 0);
+  if (!staged0) stage(0, 0);
   for (int jb = 0, b = 0; jb < nb; jb += IB, b ^= 1) {
     if (jb + IB < nb) stage(jb + IB, b ^ 1);
     else rp_commit();
@@ -230,6 +245,34 @@ __device__ void rp_gemv(const T* __restrict__ A, int64_t lda, int nb, const T* x
   }
 }
 
+// L2 prefetch of `elems` elements at p (16-byte aligned, a multiple of 16 bytes).
+template <typename T>
+__device__ __forceinline__ void rp_prefetch(const T* p, int elems) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p),
+               "r"((unsigned)(elems * (int)sizeof(T)))
+               : "memory");
+}
+
+// Prefetches into L2 the part of a task's tile (and T slot) that the task reads and that is
+// not already staged in shared memory: per column c, the rows the task touches (unit lower V
+// and L: c.., upper V and U: ..c, full tiles otherwise), rounded out to 16 bytes.  A QR
+// task's inner block 0 is staged separately.  Every address lies inside the tile and slot.
+template <typename T>
+__device__ void rp_prefetch_task(int type, const T* tile, int64_t ld, int nb, const T* Tslot) {
+  constexpr int VEC = 16 / (int)sizeof(T);
+  const bool qr = type == RT_SINGLE || type == RT_PAIR_TS || type == RT_PAIR_TT;
+  for (int c = threadIdx.x + (qr ? IB : 0); c < nb; c += NT) {
+    int lo = 0, hi = nb;
+    if (type == RT_SINGLE || type == RT_LUAPPLY) lo = c;
+    if (type == RT_PAIR_TT || type == RT_TRSV) hi = c + 1;
+    lo = lo / VEC * VEC;
+    hi = min(nb, (hi + VEC - 1) / VEC * VEC);
+    if (hi > lo) rp_prefetch<T>(tile + lo + (int64_t)c * ld, hi - lo);
+  }
+  if (Tslot != nullptr && (int)threadIdx.x < nb / IB - 1)
+    rp_prefetch<T>(Tslot + (size_t)(threadIdx.x + 1) * IB * IB, IB * IB);
+}
+
 // Waits (thread 0) until *cnt >= need; false when the abort flag is raised or the clock64
 // budget runs out (then the timeout is recorded and the abort flag raised).
 __device__ bool rp_wait(const int* cnt, int need, long long budget, int* abort_flag, int* status,
@@ -248,7 +291,7 @@ __device__ bool rp_wait(const int* cnt, int need, long long budget, int* abort_f
       return false;
     }
     __nanosleep(ns);
-    if (ns < 2048) ns *= 2;
+    if (ns < 256) ns *= 2;
   }
   return true;
 }
@@ -273,6 +316,19 @@ __global__ void __launch_bounds__(NT) k_replay(ReplayArgs<T> a) {
     const int t = s_task;
     if (t < 0 || t >= a.ntasks) break;
     const ReplayTask q = a.tasks[t];
+    const uint8_t dk = a.dec[q.k];
+    const bool run = q.gate == 0 || (q.gate == 1 && dk == DEC_QR) || (q.gate == 2 && dk == DEC_LU);
+    const T* tile = a.W + (int64_t)q.i * nb + (int64_t)q.k * nb * a.ld;
+    const T* Tstep = a.Tbuf + (size_t)q.k * a.t_step;
+    const bool qr = q.type == RT_SINGLE || q.type == RT_PAIR_TS || q.type == RT_PAIR_TT;
+    const bool pair = q.type == RT_PAIR_TS || q.type == RT_PAIR_TT;
+    const T* Tslot = qr ? Tstep + ((size_t)q.i * 2 + (pair ? 1 : 0)) * IB * nb : nullptr;
+    if (run && q.type != RT_SCALE) {
+      // the factor data do not depend on x: stage a QR task's first inner block and start
+      // the rest of its tile towards L2 while thread 0 waits for the task's inputs
+      if (qr) rp_stage<T>(tile, a.ld, Tslot, nb, pair, q.type == RT_PAIR_TT, 0, 0, Vb, Tb);
+      rp_prefetch_task<T>(q.type, tile, a.ld, nb, Tslot);
+    }
     if (tid == 0) {
       bool ok = rp_wait(a.done + q.i, q.ni, a.budget, abort_flag, a.status, q.k);
       if (ok && q.e >= 0) ok = rp_wait(a.done + q.e, q.ne, a.budget, abort_flag, a.status, q.k);
@@ -280,10 +336,11 @@ __global__ void __launch_bounds__(NT) k_replay(ReplayArgs<T> a) {
       s_go = ok ? 1 : 0;
     }
     __syncthreads();
-    if (!s_go) break;
+    if (!s_go) {
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      break;
+    }
     T* xi = a.x + (int64_t)q.i * nb;
-    const uint8_t dk = a.dec[q.k];
-    const bool run = q.gate == 0 || (q.gate == 1 && dk == DEC_QR) || (q.gate == 2 && dk == DEC_LU);
     if (!run) {   // the branch not taken: keep the counts in program order, move no data
       if (tid == 0 && t != a.skip_signal) {
         __threadfence();
@@ -298,21 +355,18 @@ __global__ void __launch_bounds__(NT) k_replay(ReplayArgs<T> a) {
     if (q.r >= 0)
       for (int r = tid; r < nb; r += NT) xe[r] = __ldcg(&a.x[(int64_t)q.r * nb + r]);
     __syncthreads();
-    const T* tile = a.W + (int64_t)q.i * nb + (int64_t)q.k * nb * a.ld;
-    const T* Tstep = a.Tbuf + (size_t)q.k * a.t_step;
     bool write_e = false;
     switch (q.type) {
       case RT_SCALE:
         for (int r = tid; r < nb; r += NT) xs[r] *= (T)0x1.0p-27;
         break;
       case RT_SINGLE:
-        rp_qr_vec<T>(tile, a.ld, Tstep + ((size_t)q.i * 2 + 0) * IB * nb, nb, false, false, Vb, Tb,
-                     xs, xe, w, w2);
+        rp_qr_vec<T>(tile, a.ld, Tslot, nb, false, false, Vb, Tb, xs, xe, w, w2, true);
         break;
       case RT_PAIR_TS:
       case RT_PAIR_TT:
-        rp_qr_vec<T>(tile, a.ld, Tstep + ((size_t)q.i * 2 + 1) * IB * nb, nb, true,
-                     q.type == RT_PAIR_TT, Vb, Tb, xs, xe, w, w2);
+        rp_qr_vec<T>(tile, a.ld, Tslot, nb, true, q.type == RT_PAIR_TT, Vb, Tb, xs, xe, w, w2,
+                     true);
         write_e = true;
         break;
       case RT_LUAPPLY:

@@ -91,6 +91,8 @@ def run(name):
     t = time.time()
     res = M.factor(A, b, cfg["nb"], CRIT[cfg["criterion"]], cfg["alpha"],
                    tree=TREE[cfg["tree"]], group=cfg.get("group", 4),
+                   tree_small=TREE[cfg.get("tree_small", "flat_ts")],
+                   tree_switch=cfg.get("tree_switch", 0),
                    mumps_mode=cfg.get("mumps_mode", 0), inject=cfg.get("inject", ()),
                    dtype=np.float32 if fp32 else np.float64)
     dt = time.time() - t

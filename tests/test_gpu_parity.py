@@ -362,20 +362,21 @@ def test_tree_policy_rejects_bad_values():
         assert e.value.status == luqr.ERR_INVALID
 
 
-def test_tree_autotuner_picks_a_candidate_and_keeps_decisions():
+def test_tree_autotuner_picks_a_candidate_and_matches_the_oracle():
     from paper_1401_5522_gb300 import autotune
     luqr = L()
     A = gauss(1024, 8)
     dA = cuda_colmajor(A)
-    pols = [("binary_tt", "flat_ts", 0), ("binary_tt", "flat_ts", 8), ("grouped", "binary_tt", 4)]
-    best, table = autotune.tune_tree(dA, 64, "max", 2000.0, policies=pols, group=3)
+    pols = [("binary_tt", "flat_ts", 0, 4), ("binary_tt", "flat_ts", 8, 4),
+            ("grouped", "binary_tt", 4, 3)]
+    best, table = autotune.tune_tree(dA, 64, "max", 2000.0, policies=pols)
     assert best in pols and [p for p, _ in table] == pols
     assert all(ms > 0 for _, ms in table)
-    decs = []
-    for p in pols:
+    for p in pols:   # each policy against the oracle run with the same policy
         h = luqr.factor(dA, 64, "max", 2000.0, tree=p[0], tree_small=p[1], tree_switch=p[2],
-                        group=3)
-        decs.append(h.decisions()[0])
+                        group=p[3])
+        dec = h.decisions()[0]
         h.close()
-    f = O.factor(A, None, 64, O.CRIT_MAX, 2000.0, tree=O.TREE_BINARY_TT)
-    assert all(np.array_equal(d, f.dec) for d in decs)
+        f = O.factor(A, None, 64, O.CRIT_MAX, 2000.0, tree=ORACLE_TREE[p[0]],
+                     tree_small=ORACLE_TREE[p[1]], tree_switch=p[2], group=p[3])
+        assert np.array_equal(dec, f.dec), (p, dec, f.dec)

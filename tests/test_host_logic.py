@@ -79,8 +79,23 @@ def test_bench_update_work_follows_the_trailing_matrix_model():
 def test_tree_autotuner_candidates():
     from paper_1401_5522_gb300 import autotune
     c = autotune.candidates(128)
-    assert ("binary_tt", "flat_ts", 0) in c and ("grouped", "flat_ts", 0) in c
-    assert ("binary_tt", "flat_ts", 8) in c and ("binary_tt", "grouped", 64) in c
-    assert all(t != s for t, s, w in c if w > 0)
+    assert ("binary_tt", "binary_tt", 0, 4) in c and ("grouped", "binary_tt", 0, 8) in c
+    assert ("grouped", "binary_tt", 64, 4) in c and ("binary_tt", "grouped", 96, 8) in c
+    assert all(t != s for t, s, w, g in c if w > 0)
+    assert all(g == 4 for t, s, w, g in c if "grouped" not in (t, s))
     assert len(set(c)) == len(c)
-    assert {w for _, _, w in autotune.candidates(4)} == {0, 2}
+    assert {w for _, _, w, _ in autotune.candidates(4)} == {0, 2, 3}
+
+
+def test_bench_tree_counts_cover_every_tile():
+    """(singles, TS, TT) of each tree: every sub-diagonal tile is killed exactly once and each
+    GEQRT single is a tile that is later an eliminator or tile k (singles - 1 = TT kills)."""
+    import bench
+    for m in range(0, 40):
+        for pol in ("flat_ts", "binary_tt", ("grouped", "grouped", 0, 3), ("grouped", "x", 0, 8)):
+            s, ts, tt = bench.tree_counts(pol, m)
+            assert ts + tt == m and s >= 1
+            if bench.tree_at(pol, m) != "flat_ts":
+                assert s - 1 == tt
+    assert bench.tree_at(("grouped", "binary_tt", 16, 4), 15) == "binary_tt"
+    assert bench.tree_at(("grouped", "binary_tt", 16, 4), 16) == "grouped"

@@ -152,3 +152,18 @@ def test_errors_match_the_numpy_oracle():
     assert e.value.step == 0 and e.value.row == 5
     f = M.factor(Z, None, 16, O.CRIT_MAX, math.inf)       # zero pivot selects QR
     assert f.dec[0] == O.DEC_QR
+
+
+@pytest.mark.parametrize("big,small,switch,group", [(2, 1, 8, 4), (1, 2, 5, 3), (2, 0, 20, 8)])
+def test_tree_policy_equals_numpy_oracle(big, small, switch, group):
+    """The per-step tree policy (small tree below `switch` sub-diagonal tiles) in the C++
+    restatement takes the numpy oracle's decisions, margins and final triangle."""
+    A = np.random.default_rng(5).standard_normal((640, 640))
+    f = O.factor(A, None, 32, O.CRIT_MAX, 2000.0, tree=big, tree_small=small, tree_switch=switch,
+                 group=group)
+    g = M.factor(A, None, 32, O.CRIT_MAX, 2000.0, tree=big, tree_small=small,
+                  tree_switch=switch, group=group, threads=4)
+    assert np.array_equal(f.dec, g.dec)
+    fin = np.isfinite(f.margin)
+    assert np.allclose(f.margin[fin], g.margin[fin], rtol=0, atol=1e-9)
+    assert np.allclose(np.triu(g.aug[:, :640]), f.U, rtol=0, atol=1e-10 * np.abs(f.U).max())
