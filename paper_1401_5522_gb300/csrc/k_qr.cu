@@ -38,16 +38,25 @@ __device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, const uint
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
-// d += a b with 3xTF32 (small terms first).
-__device__ __forceinline__ void mma3(float* d, const float* a, const float* b) {
-  uint32_t ah[4], al[4], bh[2], bl[2];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) split3(a[i], ah[i], al[i]);
-  split3(b[0], bh[0], bl[0]);
-  split3(b[1], bh[1], bl[1]);
+// d += a b with 3xTF32 on operands already split (small terms first).
+__device__ __forceinline__ void mma3s(float* d, const uint32_t* ah, const uint32_t* al,
+                                      const uint32_t* bh, const uint32_t* bl) {
   mma_tf32(d, al, bh);
   mma_tf32(d, ah, bl);
   mma_tf32(d, ah, bh);
+}
+// Splits an A fragment (4 values) once, so that it serves every n-tile of a k-step.
+__device__ __forceinline__ void split_a(const float* a, uint32_t* ah, uint32_t* al) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) split3(a[i], ah[i], al[i]);
+}
+// d += a b with 3xTF32, A pre-split.
+__device__ __forceinline__ void mma3a(float* d, const uint32_t* ah, const uint32_t* al,
+                                      const float* b) {
+  uint32_t bh[2], bl[2];
+  split3(b[0], bh[0], bl[0]);
+  split3(b[1], bh[1], bl[1]);
+  mma3s(d, ah, al, bh, bl);
 }
 
 // Stacked-operand helpers: rows 0..IB-1 come from the top block, rows IB.. from the bottom.
@@ -84,11 +93,13 @@ __device__ void apply_block_mma(const float* Vtop, const float* Vbot, int nbot, 
       a[1] = vstk(Vtop, Vbot, unit_top, k0 + t, m0 + g + 8);
       a[2] = vstk(Vtop, Vbot, unit_top, k0 + t + 4, m0 + g);
       a[3] = vstk(Vtop, Vbot, unit_top, k0 + t + 4, m0 + g + 8);
+      uint32_t ah[4], al[4];
+      split_a(a, ah, al);
 #pragma unroll
       for (int q = 0; q < NPW; ++q) {
         const int n0 = (nbase + q) * 8;
         float b[2] = {cstk(k0 + t, n0 + g), cstk(k0 + t + 4, n0 + g)};
-        mma3(acc[q], a, b);
+        mma3a(acc[q], ah, al, b);
       }
     }
 #pragma unroll
@@ -112,20 +123,26 @@ __device__ void apply_block_mma(const float* Vtop, const float* Vbot, int nbot, 
     for (int k0 = 0; k0 < IB; k0 += 8) {
       float a[4] = {Ts[(k0 + t) * TST + m0 + g], Ts[(k0 + t) * TST + m0 + g + 8],
                     Ts[(k0 + t + 4) * TST + m0 + g], Ts[(k0 + t + 4) * TST + m0 + g + 8]};
+      uint32_t ah[4], al[4];
+      split_a(a, ah, al);
 #pragma unroll
       for (int q = 0; q < NPW; ++q) {
         const int n0 = (nbase + q) * 8;
         float b[2] = {Ws[(k0 + t) * CST + n0 + g], Ws[(k0 + t + 4) * CST + n0 + g]};
-        mma3(acc[q], a, b);
+        mma3a(acc[q], ah, al, b);
       }
     }
+    // W2 is stored split: hi parts in W2s, lo parts in Ws (free once every warp has read W)
+    __syncthreads();
+    uint32_t* W2h = reinterpret_cast<uint32_t*>(W2s);
+    uint32_t* W2l = reinterpret_cast<uint32_t*>(Ws);
 #pragma unroll
     for (int q = 0; q < NPW; ++q) {
       const int n0 = (nbase + q) * 8;
-      W2s[(m0 + g) * CST + n0 + 2 * t] = acc[q][0];
-      W2s[(m0 + g) * CST + n0 + 2 * t + 1] = acc[q][1];
-      W2s[(m0 + g + 8) * CST + n0 + 2 * t] = acc[q][2];
-      W2s[(m0 + g + 8) * CST + n0 + 2 * t + 1] = acc[q][3];
+      const int o[4] = {(m0 + g) * CST + n0 + 2 * t, (m0 + g) * CST + n0 + 2 * t + 1,
+                        (m0 + g + 8) * CST + n0 + 2 * t, (m0 + g + 8) * CST + n0 + 2 * t + 1};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) split3(acc[q][e], W2h[o[e]], W2l[o[e]]);
     }
   }
   __syncthreads();
@@ -144,17 +161,22 @@ __device__ void apply_block_mma(const float* Vtop, const float* Vbot, int nbot, 
         acc[q][2] = rowA[(g + 8) * CST + n0 + 2 * t];
         acc[q][3] = rowA[(g + 8) * CST + n0 + 2 * t + 1];
       }
+      const uint32_t* W2h = reinterpret_cast<const uint32_t*>(W2s);
+      const uint32_t* W2l = reinterpret_cast<const uint32_t*>(Ws);
 #pragma unroll
       for (int k0 = 0; k0 < IB; k0 += 8) {
         float a[4] = {-vstk(Vtop, Vbot, unit_top, m0 + g, k0 + t),
                       -vstk(Vtop, Vbot, unit_top, m0 + g + 8, k0 + t),
                       -vstk(Vtop, Vbot, unit_top, m0 + g, k0 + t + 4),
                       -vstk(Vtop, Vbot, unit_top, m0 + g + 8, k0 + t + 4)};
+        uint32_t ah[4], al[4];
+        split_a(a, ah, al);
 #pragma unroll
         for (int q = 0; q < NTN; ++q) {
           const int n0 = q * 8;
-          float b[2] = {W2s[(k0 + t) * CST + n0 + g], W2s[(k0 + t + 4) * CST + n0 + g]};
-          mma3(acc[q], a, b);
+          const int o0 = (k0 + t) * CST + n0 + g, o1 = (k0 + t + 4) * CST + n0 + g;
+          const uint32_t bh[2] = {W2h[o0], W2h[o1]}, bl[2] = {W2l[o0], W2l[o1]};
+          mma3s(acc[q], ah, al, bh, bl);
         }
       }
 #pragma unroll
@@ -527,6 +549,25 @@ __device__ void panel_qr_any(T* Rs, T* Ps, int nrows, bool tri, int jb, T* tau_s
   else panel_qr_reg<T, SINGLE, 64>(Rs, Ps, nrows, tri, jb, tau_s, Ts, scratch);
 }
 
+// Row-fastest walk of an R x C index space by the CTA's NT threads, f(r, c) for every
+// r < R, c < C: the same elements as idx = tid, tid + NT, ... < R*C with r = idx % R and
+// c = idx / R, without a division per element (one at the start; afterwards idx + NT moves
+// r by NT % R and c by NT / R, with one carry).
+template <typename F>
+__device__ __forceinline__ void walk_rc(int R, int C, F&& f) {
+  int r = (int)threadIdx.x % R, c = (int)threadIdx.x / R;
+  const int dr = NT % R, dc = NT / R;
+  while (c < C) {
+    f(r, c);
+    r += dr;
+    c += dc;
+    if (r >= R) {
+      r -= R;
+      ++c;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- shared memory plans
 template <typename T, int SW>
 struct Plan {
@@ -568,17 +609,15 @@ __global__ void __launch_bounds__(NT) k_geqrt(Mat<T> F, int k, int nb, TileList 
   const int tid = threadIdx.x;
   for (int jb = 0; jb < nb; jb += IB) {
     const int nrows = nb - jb;
-    for (int idx = tid; idx < nrows * IB; idx += NT) {
-      const int r = idx % nrows, j = idx / nrows;
+    walk_rc(nrows, IB, [&](int r, int j) {
       cp_async(&Ps[r * VST + j], &tile[(jb + r) + (int64_t)(jb + j) * F.ld]);
-    }
+    });
     cp_async_wait_all();
     __syncthreads();
     panel_qr_any<T, true>(nullptr, Ps, nrows, false, jb, tau_s, Ts, Gs);
-    for (int idx = tid; idx < nrows * IB; idx += NT) {
-      const int r = idx % nrows, j = idx / nrows;
+    walk_rc(nrows, IB, [&](int r, int j) {
       tile[(jb + r) + (int64_t)(jb + j) * F.ld] = Ps[r * VST + j];
-    }
+    });
     for (int idx = tid; idx < IB * IB; idx += NT) {
       const int a = idx % IB, j = idx / IB;
       Tslot[a + (size_t)(jb + j) * IB] = Ts[a * TST + j];
@@ -586,17 +625,15 @@ __global__ void __launch_bounds__(NT) k_geqrt(Mat<T> F, int k, int nb, TileList 
     for (int cc = jb + IB; cc < nb; cc += SW) {
       const int w = min(SW, nb - cc);
       __syncthreads();
-      for (int idx = tid; idx < nrows * SW; idx += NT) {
-        const int r = idx % nrows, c = idx / nrows;
+      walk_rc(nrows, SW, [&](int r, int c) {
         if (c < w) cp_async(&Cs[r * CST + c], &tile[(jb + r) + (int64_t)(cc + c) * F.ld]);
-      }
+      });
       cp_async_wait_all();
       __syncthreads();
       apply_block<T, SW>(Ps, Ps + IB * VST, nrows - IB, Ts, Cs, Cs + IB * CST, w, Ws, W2s, true);
-      for (int idx = tid; idx < nrows * SW; idx += NT) {
-        const int r = idx % nrows, c = idx / nrows;
+      walk_rc(nrows, SW, [&](int r, int c) {
         if (c < w) tile[(jb + r) + (int64_t)(cc + c) * F.ld] = Cs[r * CST + c];
-      }
+      });
     }
     __syncthreads();
   }
@@ -622,16 +659,14 @@ __global__ void __launch_bounds__(NT) k_unmqr(Mat<const T> F, int k, int nb, Til
   const T* Tslot = Tk + ((size_t)i * 2 + 0) * IB * nb;
   const int tid = threadIdx.x;
   T* Cg = C.p + (int64_t)i * nb + cb * C.ld;
-  for (int idx = tid; idx < nb * SW; idx += NT) {
-    const int r = idx % nb, c = idx / nb;
+  walk_rc(nb, SW, [&](int r, int c) {
     if (c < w) cp_async(&Cs[r * CST + c], &Cg[r + (int64_t)c * C.ld]);
-  }
+  });
   for (int jb = 0; jb < nb; jb += IB) {
     const int nrows = nb - jb;
-    for (int idx = tid; idx < nrows * IB; idx += NT) {
-      const int r = idx % nrows, j = idx / nrows;
+    walk_rc(nrows, IB, [&](int r, int j) {
       cp_async(&Vs[r * VST + j], &V[(jb + r) + (int64_t)(jb + j) * F.ld]);
-    }
+    });
     for (int idx = tid; idx < IB * IB; idx += NT) {
       const int a = idx % IB, j = idx / IB;
       cp_async(&Ts[a * TST + j], &Tslot[a + (size_t)(jb + j) * IB]);
@@ -641,10 +676,9 @@ __global__ void __launch_bounds__(NT) k_unmqr(Mat<const T> F, int k, int nb, Til
     apply_block<T, SW>(Vs, Vs + IB * VST, nrows - IB, Ts, Cs + jb * CST, Cs + (jb + IB) * CST, w,
                        Ws, W2s, true);
   }
-  for (int idx = tid; idx < nb * SW; idx += NT) {
-    const int r = idx % nb, c = idx / nb;
+  walk_rc(nb, SW, [&](int r, int c) {
     if (c < w) Cg[r + (int64_t)c * C.ld] = Cs[r * CST + c];
-  }
+  });
 }
 
 // ---------------------------------------------------------------- TSQRT / TTQRT
@@ -678,11 +712,10 @@ __global__ void __launch_bounds__(NT) k_pair_qrt(Mat<T> F, int k, int nb, TileLi
       if (a <= j) cp_async(&Rs[a * VST + j], &R[(jb + a) + (int64_t)(jb + j) * F.ld]);
       else Rs[a * VST + j] = (T)0;
     }
-    for (int idx = tid; idx < rl * IB; idx += NT) {
-      const int r = idx % rl, j = idx / rl;
+    walk_rc(rl, IB, [&](int r, int j) {
       if (!tri || r <= jb + j) cp_async(&Ps[r * VST + j], &A[r + (int64_t)(jb + j) * F.ld]);
       else Ps[r * VST + j] = (T)0;
-    }
+    });
     cp_async_wait_all();
     __syncthreads();
     panel_qr_any<T, false>(Rs, Ps, rl, tri, jb, tau_s, Ts, Gs);
@@ -691,10 +724,9 @@ __global__ void __launch_bounds__(NT) k_pair_qrt(Mat<T> F, int k, int nb, TileLi
       if (a <= j) R[(jb + a) + (int64_t)(jb + j) * F.ld] = Rs[a * VST + j];
       Tslot[a + (size_t)(jb + j) * IB] = Ts[a * TST + j];
     }
-    for (int idx = tid; idx < rl * IB; idx += NT) {
-      const int r = idx % rl, j = idx / rl;
+    walk_rc(rl, IB, [&](int r, int j) {
       if (!tri || r <= jb + j) A[r + (int64_t)(jb + j) * F.ld] = Ps[r * VST + j];
-    }
+    });
     for (int cc = jb + IB; cc < nb; cc += SW) {
       const int w = min(SW, nb - cc);
       __syncthreads();
@@ -702,10 +734,9 @@ __global__ void __launch_bounds__(NT) k_pair_qrt(Mat<T> F, int k, int nb, TileLi
         const int a = idx % IB, c = idx / IB;
         if (c < w) cp_async(&Ct[a * CST + c], &R[(jb + a) + (int64_t)(cc + c) * F.ld]);
       }
-      for (int idx = tid; idx < rl * SW; idx += NT) {
-        const int r = idx % rl, c = idx / rl;
+      walk_rc(rl, SW, [&](int r, int c) {
         if (c < w) cp_async(&Cb[r * CST + c], &A[r + (int64_t)(cc + c) * F.ld]);
-      }
+      });
       cp_async_wait_all();
       __syncthreads();
       apply_block<T, SW>(nullptr, Ps, rl, Ts, Ct, Cb, w, Ws, W2s, false);
@@ -713,10 +744,9 @@ __global__ void __launch_bounds__(NT) k_pair_qrt(Mat<T> F, int k, int nb, TileLi
         const int a = idx % IB, c = idx / IB;
         if (c < w) R[(jb + a) + (int64_t)(cc + c) * F.ld] = Ct[a * CST + c];
       }
-      for (int idx = tid; idx < rl * SW; idx += NT) {
-        const int r = idx % rl, c = idx / rl;
+      walk_rc(rl, SW, [&](int r, int c) {
         if (c < w) A[r + (int64_t)(cc + c) * F.ld] = Cb[r * CST + c];
-      }
+      });
     }
     __syncthreads();
   }
@@ -745,20 +775,18 @@ __global__ void __launch_bounds__(NT) k_pair_apply(Mat<const T> F, int k, int nb
   T* C1g = C.p + (int64_t)e * nb + cb * C.ld;
   T* C2g = C.p + (int64_t)i * nb + cb * C.ld;
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < nb * SW; idx += NT) {
-    const int r = idx % nb, c = idx / nb;
+  walk_rc(nb, SW, [&](int r, int c) {
     if (c < w) {
       cp_async(&C1s[r * CST + c], &C1g[r + (int64_t)c * C.ld]);
       cp_async(&C2s[r * CST + c], &C2g[r + (int64_t)c * C.ld]);
     }
-  }
+  });
   for (int jb = 0; jb < nb; jb += IB) {
     const int rl = tri ? jb + IB : nb;
-    for (int idx = tid; idx < rl * IB; idx += NT) {
-      const int r = idx % rl, j = idx / rl;
+    walk_rc(rl, IB, [&](int r, int j) {
       if (!tri || r <= jb + j) cp_async(&Vs[r * VST + j], &V[r + (int64_t)(jb + j) * F.ld]);
       else Vs[r * VST + j] = (T)0;
-    }
+    });
     for (int idx = tid; idx < IB * IB; idx += NT) {
       const int a = idx % IB, j = idx / IB;
       cp_async(&Ts[a * TST + j], &Tslot[a + (size_t)(jb + j) * IB]);
@@ -767,13 +795,12 @@ __global__ void __launch_bounds__(NT) k_pair_apply(Mat<const T> F, int k, int nb
     __syncthreads();
     apply_block<T, SW>(nullptr, Vs, rl, Ts, C1s + jb * CST, C2s, w, Ws, W2s, false);
   }
-  for (int idx = tid; idx < nb * SW; idx += NT) {
-    const int r = idx % nb, c = idx / nb;
+  walk_rc(nb, SW, [&](int r, int c) {
     if (c < w) {
       C1g[r + (int64_t)c * C.ld] = C1s[r * CST + c];
       C2g[r + (int64_t)c * C.ld] = C2s[r * CST + c];
     }
-  }
+  });
 }
 
 // ---------------------------------------------------------------- one right-hand side

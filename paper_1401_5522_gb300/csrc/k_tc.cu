@@ -623,6 +623,7 @@ constexpr int T4_BBYTES = 2 * T4_BN * P_BK * 4;             // hi + lo
 constexpr int T4_STAGE = T4_ABYTES + T4_BBYTES;             // 48 KB
 constexpr int T4_RAWB = T4_BN * P_BK * 4;                   // 8 KB
 constexpr int T4_SMEM = T4_STG * T4_STAGE + T4_RAW * T4_RAWB + 512;
+static_assert(T4_SMEM <= SMEM_MAX, "persistent GEMM stages exceed the shared memory of a CTA");
 
 __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles, int ntiles,
                                                      int total) {
