@@ -41,10 +41,12 @@ def parse(argv=None):
     p.add_argument("--kappa", type=float, default=1e5)
     p.add_argument("--criterion", default="max")
     p.add_argument("--alpha", type=float, default=100.0)
-    p.add_argument("--tree", default="binary_tt")
-    p.add_argument("--tree-small", default="flat_ts",
+    # default tree policy: the fastest of the tuner's candidates on this GPU at N = 32768
+    # (bench.py --tune-tree 1 re-times them)
+    p.add_argument("--tree", default="grouped")
+    p.add_argument("--tree-small", default="binary_tt",
                    help="tree of the steps with fewer than --tree-switch sub-diagonal tiles")
-    p.add_argument("--tree-switch", type=int, default=0)
+    p.add_argument("--tree-switch", type=int, default=64)
     p.add_argument("--group", type=int, default=4, help="group size of the grouped tree")
     p.add_argument("--tune-tree", type=int, default=0,
                    help="time candidate tree policies on the input (untimed setup) and use the "
@@ -68,6 +70,21 @@ def parse(argv=None):
                         "variants, C5 speculation modes); one GPU only")
     p.add_argument("--seed", type=int, default=0)
     return p.parse_args(argv)
+
+
+def tree_kw(args):
+    """luqr.factor keywords of the tree policy."""
+    return dict(tree=args.tree, tree_small=args.tree_small, tree_switch=args.tree_switch,
+                group=args.group)
+
+
+def tree_desc(args):
+    def one(t):
+        return f"{t} tree" + (f" (groups of {args.group})" if t == "grouped" else "")
+    if args.tree_switch > 0:
+        return (f"{one(args.tree)} from {args.tree_switch} sub-diagonal tiles, "
+                f"{one(args.tree_small)} below")
+    return one(args.tree)
 
 
 # ------------------------------------------------------------------ flop model
@@ -301,10 +318,11 @@ def oracle_sample(A, args, steps=1):
     from oracle import luqr_oracle_mt as M
     N, nb = A.shape[0], args.nb
     crit = {"max": O.CRIT_MAX, "sum": O.CRIT_SUM, "mumps": O.CRIT_MUMPS}[args.criterion]
-    tree = {"flat_ts": 0, "binary_tt": 1, "grouped": 2}[args.tree]
+    trees = {"flat_ts": 0, "binary_tt": 1, "grouped": 2}
     M.build()
     t0 = time.perf_counter()
-    res = M.factor(A, None, nb, crit, args.alpha, tree=tree, steps=steps)
+    res = M.factor(A, None, nb, crit, args.alpha, tree=trees[args.tree], group=args.group,
+                   tree_small=trees[args.tree_small], tree_switch=args.tree_switch, steps=steps)
     t = time.perf_counter() - t0
     n = res.n
     dec = np.zeros(n, dtype=np.uint8)
@@ -441,7 +459,7 @@ def train_decision_mlp(args):
         A0 = inputs.gaussian(N0, 500 + seed, device="cuda")
         A0 = inputs.scale_diag_tiles(A0, nb0, inputs.choose_panels(N0 // nb0, 0.2, seed), 1e-8)
         runs.append(dict(A=A0, nb=nb0, criterion="max", alpha=(1e4, 3e4, 1e5)[seed % 3],
-                         precision="fp32", tree=args.tree))
+                         precision="fp32", **tree_kw(args)))
     t0 = time.time()
     X, y = S.collect(runs)
     params, losses = S.train(X, y, epochs=200, batch=128, lr=3e-3)
@@ -463,7 +481,7 @@ def speculation_form(args, A, b, x, head_ms, params, train_info):
         if mode == args.speculate:
             continue
         def solve():
-            h = luqr.factor(A, args.nb, args.criterion, args.alpha, tree=args.tree,
+            h = luqr.factor(A, args.nb, args.criterion, args.alpha, **tree_kw(args),
                             precision=args.precision, fp32_kernels=args.fp32_kernels,
                             speculate=mode, **extra)
             st, its, eta = h.refine(A, b, x, tol=args.tol, max_iter=30)
@@ -611,7 +629,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     config = {"workload": (f"hybrid LU-QR solve, N={args.N}, nb={args.nb}, A=U diag(s) V^T "
                            f"kappa={args.kappa:g}, b=A*1, {args.criterion} alpha={args.alpha:g}, "
-                           f"{args.tree} tree, {args.precision} factorization + FP64 refinement to "
+                           f"{tree_desc(args)}, {args.precision} factorization + FP64 refinement to "
                            f"eta<={args.tol:g}, {args.speculate} speculation"),
               "N": args.N, "nb": args.nb, "kappa": args.kappa, "criterion": args.criterion,
               "alpha": args.alpha, "tree": args.tree, "factor_precision": args.precision,
@@ -657,6 +675,9 @@ def main():
         tuning = {"chosen": list(policy),
                   "factor_ms": [[list(p), round(t, 2)] for p, t in table]}
         config["tree"], config["tree_small"], config["tree_switch"], config["group"] = policy
+        old_desc = tree_desc(args)
+        args.tree, args.tree_small, args.tree_switch, args.group = policy
+        config["workload"] = config["workload"].replace(old_desc, tree_desc(args))
     elif args.tree_switch or args.tree == "grouped":
         config["tree_small"], config["tree_switch"] = args.tree_small, args.tree_switch
         config["group"] = args.group
@@ -814,7 +835,7 @@ def main():
         for _ in range(args.e2e_steps):
             dA2.copy_(hA, non_blocking=True)
             db2.copy_(hb, non_blocking=True)
-            h = luqr.factor(dA2, nb, args.criterion, args.alpha, tree=args.tree,
+            h = luqr.factor(dA2, nb, args.criterion, args.alpha, **tree_kw(args),
                             precision=args.precision, fp32_kernels=args.fp32_kernels, **spec)
             h.refine(dA2, db2, dx2, tol=args.tol, max_iter=30)
             h.close()
@@ -832,7 +853,7 @@ def main():
     if args.fp64_baseline:
         small = inputs.conditioned(1024, args.kappa, seed=1, device="cuda")
         sb = (small @ torch.ones(1024, 1, dtype=torch.float64, device="cuda")).reshape(-1).contiguous()
-        luqr.factor(small, nb, args.criterion, args.alpha, b=sb, tree=args.tree,
+        luqr.factor(small, nb, args.criterion, args.alpha, b=sb, **tree_kw(args),
                     precision="fp64").close()                    # loads the FP64 kernels
         times = []
         for _ in range(args.fp64_baseline):
@@ -841,7 +862,7 @@ def main():
             g0 = torch.cuda.Event(enable_timing=True)
             g1 = torch.cuda.Event(enable_timing=True)
             g0.record(stream)
-            h = luqr.factor(A, nb, args.criterion, args.alpha, b=bb, tree=args.tree,
+            h = luqr.factor(A, nb, args.criterion, args.alpha, b=bb, **tree_kw(args),
                             precision="fp64")
             g1.record(stream)
             torch.cuda.synchronize()

@@ -245,8 +245,11 @@ void launch_lu_inverse(const float* W, int64_t ldw, int k, int nb, const int* pi
 // (and e for pairs) are written, row r (GEMV) is read; ni / ne / nr are the numbers of
 // earlier writes of those rows to wait for.
 constexpr int LUQR_TIMEOUT_CODE = -6;   // LUQR_ERR_TIMEOUT
+// RT_GEMV_TRSV: x_i -= A_{i,k} x_k (k = i + 1, the last update of row i in the back
+// substitution) and then x_i <- U_ii^-1 x_i, in one task (the chain of the back substitution
+// then takes one task per tile row instead of two).
 enum : int { RT_SCALE = 0, RT_SINGLE = 1, RT_PAIR_TS = 2, RT_PAIR_TT = 3, RT_LUAPPLY = 4,
-             RT_GEMV = 5, RT_TRSV = 6 };
+             RT_GEMV = 5, RT_TRSV = 6, RT_GEMV_TRSV = 7 };
 struct ReplayTask {
   int type, k, i, e, r, ni, ne, nr;
   int gate;              // 0 always; 1 only if dec[k] = QR; 2 only if dec[k] = LU (a task whose

@@ -10,6 +10,7 @@
 //   RT_GEMV    x_i -= A_ik x_k                          (LU step k, i > k; back substitution,
 //                                                      i < k, with the tiles of U)
 //   RT_TRSV    x_k <- U_kk^-1 x_k                       (back substitution)
+//   RT_GEMV_TRSV  x_i -= A_{i,i+1} x_{i+1}, then x_i <- U_ii^-1 x_i  (k = i + 1)
 // Every task writes one or two tile rows of x and may read one more.  Per tile row r the
 // kernel counts completed writes (done[r]); a task waits until every write that precedes it
 // in program order has completed on each row it touches (the counts are precomputed).  Reads
@@ -26,15 +27,27 @@
 namespace luqr {
 
 
-// Shared memory of one task: two staged IB x nb V blocks, two IB x IB T blocks, two nb
-// segments of x, two IB work vectors.
+// Shared memory of one task: a ring of nbuf staged IB x nb V blocks and IB x IB T blocks,
+// two nb segments of x, two IB work vectors.
 template <typename T>
-size_t replay_smem(int nb) {
-  return sizeof(T) * (2 * (size_t)IB * nb + 2 * IB * IB + 2 * (size_t)nb + 2 * IB);
+size_t replay_smem(int nb, int nbuf) {
+  return sizeof(T) * (nbuf * (size_t)IB * nb + nbuf * IB * IB + 2 * (size_t)nb + 2 * IB);
+}
+
+// Ring depth of the launch: the deepest of 6, 4, 3, 2 that fits one CTA's shared memory
+// (0: none fits).  FP32 tiles of 256 take 6 (about 218 KB), FP64 ones 3.
+template <typename T>
+int replay_nbuf(int nb) {
+  for (int q : {6, 4, 3, 2})
+    if (replay_smem<T>(nb, q) <= (size_t)SMEM_MAX) return q;
+  return 0;
 }
 
 __device__ __forceinline__ void rp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void rp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void rp_wait_groups() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 __device__ __forceinline__ void rp_cp16(void* sdst, const void* gsrc) {
   const unsigned saddr = (unsigned)__cvta_generic_to_shared(sdst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(gsrc) : "memory");
@@ -75,13 +88,14 @@ __device__ void rp_stage(const T* __restrict__ V, int64_t ldv, const T* __restri
 // reflector j is [e_j; V(:, j)], V upper triangular for TT) applied to the vector segments
 // xs (row i) and xe (eliminator row), inner block by inner block:
 //   w = V_b^T x_i (+ x_e(block rows) for pairs),  w2 = T_b^T w,  x_i -= V_b w2,  x_e -= w2,
-// with the next block's V and T copies in flight.  staged0: block 0 was already staged into
-// buffer 0 (while the task waited for its inputs).
-template <typename T>
+// with the copies of the next NBUF - 1 blocks in flight (a ring of NBUF buffers, one commit
+// group per block; block b lives in buffer b % NBUF).  Blocks 0 .. NBUF - 2 were staged
+// before the call (while the task waited for its inputs).
+template <typename T, int NBUF>
 __device__ void rp_qr_vec(const T* __restrict__ V, int64_t ldv, const T* __restrict__ Tslot,
-                          int nb, bool pair, bool tri, T* Vb, T* Tb, T* xs, T* xe, T* w, T* w2,
-                          bool staged0) {
+                          int nb, bool pair, bool tri, T* Vb, T* Tb, T* xs, T* xe, T* w, T* w2) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT / 32;
+  const int nblk = nb / IB;
   auto lo = [&](int jb) { return rp_lo(pair, jb); };
   auto hi = [&](int jb) { return rp_hi(pair, tri, jb, nb); };
   auto stage = [&](int jb, int buf) { rp_stage<T>(V, ldv, Tslot, nb, pair, tri, jb, buf, Vb, Tb); };
@@ -95,11 +109,12 @@ __device__ void rp_qr_vec(const T* __restrict__ V, int64_t ldv, const T* __restr
     }
     return vs[(size_t)j * nb + (r - lo(jb))];
   };
-  if (!staged0) stage(0, 0);
-  for (int jb = 0, b = 0; jb < nb; jb += IB, b ^= 1) {
-    if (jb + IB < nb) stage(jb + IB, b ^ 1);
+  for (int blk = 0; blk < nblk; ++blk) {
+    const int jb = blk * IB, b = blk % NBUF, nxt = blk + NBUF - 1;
+    // the buffer of block nxt held block blk - 1, consumed before the last barrier
+    if (nxt < nblk) stage(nxt * IB, nxt % NBUF);
     else rp_commit();
-    rp_wait1();
+    rp_wait_groups<NBUF - 1>();   // block blk has landed
     __syncthreads();
     const T* vs = Vb + (size_t)b * IB * nb;
     const T* ts = Tb + b * IB * IB;
@@ -255,13 +270,14 @@ __device__ __forceinline__ void rp_prefetch(const T* p, int elems) {
 
 // Prefetches into L2 the part of a task's tile (and T slot) that the task reads and that is
 // not already staged in shared memory: per column c, the rows the task touches (unit lower V
-// and L: c.., upper V and U: ..c, full tiles otherwise), rounded out to 16 bytes.  A QR
-// task's inner block 0 is staged separately.  Every address lies inside the tile and slot.
+// and L: c.., upper V and U: ..c, full tiles otherwise), rounded out to 16 bytes.  The first
+// staged_blocks inner blocks of a QR task are staged separately.  Every address lies inside
+// the tile and slot.
 template <typename T>
-__device__ void rp_prefetch_task(int type, const T* tile, int64_t ld, int nb, const T* Tslot) {
+__device__ void rp_prefetch_task(int type, const T* tile, int64_t ld, int nb, const T* Tslot,
+                                 int staged_blocks) {
   constexpr int VEC = 16 / (int)sizeof(T);
-  const bool qr = type == RT_SINGLE || type == RT_PAIR_TS || type == RT_PAIR_TT;
-  for (int c = threadIdx.x + (qr ? IB : 0); c < nb; c += NT) {
+  for (int c = threadIdx.x + staged_blocks * IB; c < nb; c += NT) {
     int lo = 0, hi = nb;
     if (type == RT_SINGLE || type == RT_LUAPPLY) lo = c;
     if (type == RT_PAIR_TT || type == RT_TRSV) hi = c + 1;
@@ -269,8 +285,8 @@ __device__ void rp_prefetch_task(int type, const T* tile, int64_t ld, int nb, co
     hi = min(nb, (hi + VEC - 1) / VEC * VEC);
     if (hi > lo) rp_prefetch<T>(tile + lo + (int64_t)c * ld, hi - lo);
   }
-  if (Tslot != nullptr && (int)threadIdx.x < nb / IB - 1)
-    rp_prefetch<T>(Tslot + (size_t)(threadIdx.x + 1) * IB * IB, IB * IB);
+  if (Tslot != nullptr && (int)threadIdx.x < nb / IB - staged_blocks)
+    rp_prefetch<T>(Tslot + (size_t)(threadIdx.x + staged_blocks) * IB * IB, IB * IB);
 }
 
 // Waits (thread 0) until *cnt >= need; false when the abort flag is raised or the clock64
@@ -296,13 +312,13 @@ __device__ bool rp_wait(const int* cnt, int need, long long budget, int* abort_f
   return true;
 }
 
-template <typename T>
+template <typename T, int NBUF>
 __global__ void __launch_bounds__(NT) k_replay(ReplayArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nb = a.nb;
-  T* Vb = reinterpret_cast<T*>(smem_raw);           // 2 x (IB x nb)
-  T* Tb = Vb + 2 * (size_t)IB * nb;                 // 2 x (IB x IB)
-  T* xs = Tb + 2 * IB * IB;                         // nb: row i
+  T* Vb = reinterpret_cast<T*>(smem_raw);           // NBUF x (IB x nb)
+  T* Tb = Vb + NBUF * (size_t)IB * nb;              // NBUF x (IB x IB)
+  T* xs = Tb + NBUF * IB * IB;                      // nb: row i
   T* xe = xs + nb;                                  // nb: eliminator row / read row
   T* w = xe + nb;                                   // IB
   T* w2 = w + IB;                                   // IB
@@ -326,8 +342,21 @@ __global__ void __launch_bounds__(NT) k_replay(ReplayArgs<T> a) {
     if (run && q.type != RT_SCALE) {
       // the factor data do not depend on x: stage a QR task's first inner block and start
       // the rest of its tile towards L2 while thread 0 waits for the task's inputs
-      if (qr) rp_stage<T>(tile, a.ld, Tslot, nb, pair, q.type == RT_PAIR_TT, 0, 0, Vb, Tb);
-      rp_prefetch_task<T>(q.type, tile, a.ld, nb, Tslot);
+      // a QR task's first NBUF - 1 inner blocks into the ring (one commit group each, empty
+      // groups past the last block keep the count uniform), the rest towards L2
+      if (qr)
+        for (int blk = 0; blk < NBUF - 1; ++blk) {
+          if (blk * IB < nb)
+            rp_stage<T>(tile, a.ld, Tslot, nb, pair, q.type == RT_PAIR_TT, blk * IB, blk, Vb, Tb);
+          else
+            rp_commit();
+        }
+      if (q.type == RT_GEMV_TRSV) {
+        rp_prefetch_task<T>(RT_GEMV, tile, a.ld, nb, nullptr, 0);
+        rp_prefetch_task<T>(RT_TRSV, a.W + (int64_t)q.i * nb * (1 + a.ld), a.ld, nb, nullptr, 0);
+      } else {
+        rp_prefetch_task<T>(q.type, tile, a.ld, nb, Tslot, qr ? NBUF - 1 : 0);
+      }
     }
     if (tid == 0) {
       bool ok = rp_wait(a.done + q.i, q.ni, a.budget, abort_flag, a.status, q.k);
@@ -361,12 +390,12 @@ __global__ void __launch_bounds__(NT) k_replay(ReplayArgs<T> a) {
         for (int r = tid; r < nb; r += NT) xs[r] *= (T)0x1.0p-27;
         break;
       case RT_SINGLE:
-        rp_qr_vec<T>(tile, a.ld, Tslot, nb, false, false, Vb, Tb, xs, xe, w, w2, true);
+        rp_qr_vec<T, NBUF>(tile, a.ld, Tslot, nb, false, false, Vb, Tb, xs, xe, w, w2);
         break;
       case RT_PAIR_TS:
       case RT_PAIR_TT:
-        rp_qr_vec<T>(tile, a.ld, Tslot, nb, true, q.type == RT_PAIR_TT, Vb, Tb, xs, xe, w, w2,
-                     true);
+        rp_qr_vec<T, NBUF>(tile, a.ld, Tslot, nb, true, q.type == RT_PAIR_TT, Vb, Tb, xs, xe, w,
+                           w2);
         write_e = true;
         break;
       case RT_LUAPPLY:
@@ -381,6 +410,18 @@ __global__ void __launch_bounds__(NT) k_replay(ReplayArgs<T> a) {
           if (tid == 0 && atomicCAS(&a.status[ST_CODE], 0, -4) == 0) {
             a.status[ST_STEP] = q.k;
             a.status[ST_ROW] = q.k * nb + bad;
+          }
+        }
+        break;
+      }
+      case RT_GEMV_TRSV: {
+        rp_gemv<T>(tile, a.ld, nb, xe, xs, Vb);   // tile (i, i+1); xe holds x_{i+1}
+        __syncthreads();
+        const int bad = rp_trsv<T>(a.W + (int64_t)q.i * nb * (1 + a.ld), a.ld, nb, xs, &s_bad);
+        if (bad >= 0) {
+          if (tid == 0 && atomicCAS(&a.status[ST_CODE], 0, -4) == 0) {
+            a.status[ST_STEP] = q.i;
+            a.status[ST_ROW] = q.i * nb + bad;
           }
         }
         break;
@@ -403,24 +444,45 @@ __global__ void __launch_bounds__(NT) k_replay(ReplayArgs<T> a) {
 
 template <typename T>
 bool replay_fits(int nb) {
-  return replay_smem<T>(nb) <= (size_t)SMEM_MAX && (nb % 32) == 0;
+  return replay_nbuf<T>(nb) >= 2 && (nb % 32) == 0;
+}
+
+template <typename T, int NBUF>
+void launch_replay_n(const ReplayArgs<T>& a, int grid, cudaStream_t s) {
+  const size_t smem = replay_smem<T>(a.nb, NBUF);
+  ensure_dyn_smem<k_replay<T, NBUF>>(smem);
+  ProfScope ps_("k_replay", s);
+  k_replay<T, NBUF><<<grid, NT, smem, s>>>(a);
 }
 
 template <typename T>
 void launch_replay(const ReplayArgs<T>& a, int grid, cudaStream_t s) {
-  const size_t smem = replay_smem<T>(a.nb);
-  ensure_dyn_smem<k_replay<T>>(smem);
-  ProfScope ps_("k_replay", s);
-  k_replay<T><<<grid, NT, smem, s>>>(a);
+  switch (replay_nbuf<T>(a.nb)) {
+    case 6: launch_replay_n<T, 6>(a, grid, s); break;
+    case 4: launch_replay_n<T, 4>(a, grid, s); break;
+    case 3: launch_replay_n<T, 3>(a, grid, s); break;
+    default: launch_replay_n<T, 2>(a, grid, s); break;
+  }
 }
 
+// Resident CTAs per SM of the launch (1 when its ring takes most of the shared memory).
 template <typename T>
 int replay_blocks_per_sm(int nb) {
-  const size_t smem = replay_smem<T>(nb);
-  ensure_dyn_smem<k_replay<T>>(smem);
+  const int q = replay_nbuf<T>(nb);
+  const size_t smem = replay_smem<T>(nb, q);
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_replay<T>, NT, smem) != cudaSuccess)
-    return 1;
+  cudaError_t e;
+  switch (q) {
+    case 6: ensure_dyn_smem<k_replay<T, 6>>(smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_replay<T, 6>, NT, smem); break;
+    case 4: ensure_dyn_smem<k_replay<T, 4>>(smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_replay<T, 4>, NT, smem); break;
+    case 3: ensure_dyn_smem<k_replay<T, 3>>(smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_replay<T, 3>, NT, smem); break;
+    default: ensure_dyn_smem<k_replay<T, 2>>(smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_replay<T, 2>, NT, smem); break;
+  }
+  if (e != cudaSuccess) return 1;
   return b > 0 ? b : 1;
 }
 

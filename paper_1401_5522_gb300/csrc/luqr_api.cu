@@ -285,9 +285,12 @@ void rq_build(luqr_handle* h, const uint8_t* dec = nullptr) {
       for (int i = k + 1; i < n; ++i) push(RT_GEMV, k, i, -1, k, gl);
     }
   }
-  for (int k = n - 1; k >= 0; --k) {   // row k-1 first: its solve is the next on the chain
-    push(RT_TRSV, k, k, -1, -1, 0);
-    for (int i = k - 1; i >= 0; --i) push(RT_GEMV, k, i, -1, k, 0);
+  // back substitution: row k's solve takes the update from x_{k+1} with it; the other
+  // updates from x_k are tasks of their own (row k-1's is the next fused solve)
+  for (int k = n - 1; k >= 0; --k) {
+    if (k == n - 1) push(RT_TRSV, k, k, -1, -1, 0);
+    else push(RT_GEMV_TRSV, k + 1, k, -1, k + 1, 0);
+    for (int i = k - 2; i >= 0; --i) push(RT_GEMV, k, i, -1, k, 0);
   }
   // Claim order: by depth in the dependency graph (1 + the deepest earlier writer of any row
   // the task touches), stable.  A task's dependencies are shallower, so the order stays a
@@ -996,7 +999,9 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int bps = h->prec == LUQR_PREC_FP64 ? replay_blocks_per_sm<double>(nb)
                                               : replay_blocks_per_sm<float>(nb);
-    h->rq_grid = (int)std::min<size_t>(h->rq_host.size(), (size_t)std::max(1, sms) * bps);
+    // one CTA per SM: each claimed task stages and prefetches its tile while it waits, and
+    // more waiting CTAs per SM would push other tasks' prefetched tiles out of L2
+    h->rq_grid = (int)std::min<size_t>(h->rq_host.size(), (size_t)std::max(1, sms) * std::min(bps, 1));
     if (e == cudaSuccess)
       e = cudaMemcpy(h->rq, h->rq_host.data(), sizeof(ReplayTask) * h->rq_host.size(),
                      cudaMemcpyHostToDevice);

@@ -34,6 +34,7 @@ TREE = {"flat_ts": 0, "binary_tt": 1, "grouped": 2}
 C2 = dict(N=16384, nb=256)
 C3 = dict(N=32768, nb=256, recipe="conditioned", kappa=1e5, seed=0, criterion="max",
           tree="binary_tt")
+C3P = dict(C3, tree="grouped", group=4, tree_small="binary_tt", tree_switch=64)
 RUNS = {
     "c2_max_a100_tt": dict(C2, recipe="gaussian", seed=0, criterion="max", alpha=100.0,
                            tree="binary_tt"),
@@ -53,6 +54,10 @@ RUNS = {
                                    tree="binary_tt", inject=[5]),
     "c3_fp64_a100": dict(C3, alpha=100.0, dtype="float64"),
     "c3_fp32_a100": dict(C3, alpha=100.0, dtype="float32"),
+    # the benchmark's tree policy: grouped tree (groups of 4) while a step has 64 or more
+    # sub-diagonal tiles, binary TT below
+    "c3p_fp64_a100": dict(C3P, alpha=100.0, dtype="float64"),
+    "c3p_fp32_a100": dict(C3P, alpha=100.0, dtype="float32"),
 }
 
 

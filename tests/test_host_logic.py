@@ -49,8 +49,9 @@ def test_bench_defaults_follow_the_measurement_contract():
     a = bench.parse([])
     assert a.gpus == 1 and a.impl == "luqr"
     assert a.warmup >= 3 and a.steps >= 1
-    assert (a.N, a.nb, a.kappa, a.criterion, a.alpha, a.tree) == (32768, 256, 1e5, "max", 100.0,
-                                                                     "binary_tt")
+    assert (a.N, a.nb, a.kappa, a.criterion, a.alpha) == (32768, 256, 1e5, "max", 100.0)
+    # the tree policy whose full-size decisions are stored (tests/golden/large_c3p_*.json)
+    assert (a.tree, a.tree_small, a.tree_switch, a.group) == ("grouped", "binary_tt", 64, 4)
     assert a.tol == 1e-13 and a.e2e_steps >= 1
 
 
