@@ -196,6 +196,9 @@ struct TcArgs {
   // packed A known to be triangular (exact zeros): 1 lower (A[m][q] = 0 for q > m), 2 upper
   // (A[m][q] = 0 for q < m); the persistent kernel skips the products of zero blocks
   int a_tri;
+  // the C (EPI_SUB) or C1 (EPI_ADD_OUT) blocks an epilogue reads may be brought into shared
+  // memory by bulk copies (set by launch_tc2 when every column segment is 16-byte aligned)
+  int c_bulk;
 };
 void launch_tc(const TcArgs& a, int batch, const char* name, cudaStream_t s);
 // Packed-A form: pack A once (launch_tc_pack), then launch_tc2 with a.Apk/a.sApk set.

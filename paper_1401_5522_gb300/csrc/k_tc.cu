@@ -611,6 +611,9 @@ __device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
 //   warp 0      raw B chunks (cp.async) into a 4-slot ring
 //   warp 1      tcgen05.mma issue (one thread) into accumulator (tile parity)
 //   warp 2      packed A chunks (cp.async.bulk) into a 3-stage ring
+//   warp 3      C loader: the C (or C1) blocks an accumulating epilogue reads, one
+//               128-row x 32-column segment at a time (a column per lane, one bulk copy of
+//               512 bytes each), into a 3-slot ring running ahead of the epilogue
 //   warps 4-7   TF32 hi/lo split of B into the stage
 //   warps 8-11  epilogue: TMEM -> registers -> C, then free the accumulator
 // Chunks are numbered across tiles (g = tile_iter * nK + c) for the ring slots and parities.
@@ -622,7 +625,9 @@ constexpr int T4_ABYTES = 2 * 2 * P_ABLK;                   // two M halves x (h
 constexpr int T4_BBYTES = 2 * T4_BN * P_BK * 4;             // hi + lo
 constexpr int T4_STAGE = T4_ABYTES + T4_BBYTES;             // 48 KB
 constexpr int T4_RAWB = T4_BN * P_BK * 4;                   // 8 KB
-constexpr int T4_SMEM = T4_STG * T4_STAGE + T4_RAW * T4_RAWB + 512;
+constexpr int T4_CSLOTS = 3;
+constexpr int T4_CBOX = 128 * 32 * 4;                        // 16 KB: one epilogue segment
+constexpr int T4_SMEM = T4_STG * T4_STAGE + T4_RAW * T4_RAWB + T4_CSLOTS * T4_CBOX + 512;
 static_assert(T4_SMEM <= SMEM_MAX, "persistent GEMM stages exceed the shared memory of a CTA");
 
 __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles, int ntiles,
@@ -631,14 +636,18 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
   if (a.status != nullptr && a.status[ST_CODE] != 0) return;
   extern __shared__ __align__(1024) unsigned char smem_p4[];
   unsigned char* rawbase = smem_p4 + T4_STG * T4_STAGE;
-  uint64_t* raw_full = reinterpret_cast<uint64_t*>(rawbase + T4_RAW * T4_RAWB);
+  float* cbox = reinterpret_cast<float*>(rawbase + T4_RAW * T4_RAWB);   // T4_CSLOTS boxes
+  uint64_t* raw_full =
+      reinterpret_cast<uint64_t*>(rawbase + T4_RAW * T4_RAWB + T4_CSLOTS * T4_CBOX);
   uint64_t* raw_empty = raw_full + T4_RAW;
   uint64_t* a_full = raw_empty + T4_RAW;
   uint64_t* b_full = a_full + T4_STG;
   uint64_t* st_empty = b_full + T4_STG;
   uint64_t* acc_full = st_empty + T4_STG;
   uint64_t* acc_empty = acc_full + 2;
-  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* c_full = acc_empty + 2;
+  uint64_t* c_empty = c_full + T4_CSLOTS;
+  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(c_empty + T4_CSLOTS);
   volatile int* fail = reinterpret_cast<volatile int*>(taddr_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nK = a.K / P_BK;
@@ -672,6 +681,10 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
     for (int q = 0; q < 2; ++q) {
       mbar_init(&acc_full[q], 1);
       mbar_init(&acc_empty[q], 4);
+    }
+    for (int q = 0; q < T4_CSLOTS; ++q) {
+      mbar_init(&c_full[q], 1);
+      mbar_init(&c_empty[q], 4);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -784,6 +797,40 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
       for (int q = last_g; q >= 0 && q > last_g - T4_STG; --q)
         wwait(&a_full[q % T4_STG], (uint32_t)(q / T4_STG) & 1, fail, false);
     }
+  } else if (warp == 3) {
+    // ---- C loader (accumulating epilogues with aligned segments only)
+    if (a.c_bulk && a.epi != TC_EPI_OUT) {
+      const bool sub = a.epi == TC_EPI_SUB;
+      const int64_t ldr = sub ? a.ldc : a.ldc1;
+      int seg = 0;
+      bool stop = false;
+      for (int it = 0; it < ntile_cta && !stop; ++it) {
+        int64_t t, m0, n0;
+        tile_of(it, t, m0, n0);
+        const float* Cr = sub ? a.C + t * a.sC : a.C1 + t * a.sC1;
+        const int mh = (a.M - m0) > 128 ? 2 : 1;
+        for (int h = 0; h < mh && !stop; ++h) {
+          const int64_t r0 = m0 + h * 128;
+          const int rows = (int)min((int64_t)128, a.M - r0);
+          for (int cc = 0; cc < T4_BN; cc += 32, ++seg) {
+            if (n0 + cc >= a.N) break;
+            const int slot = seg % T4_CSLOTS;
+            bool ok = seg < T4_CSLOTS ||
+                      wwait(&c_empty[slot], (uint32_t)((seg / T4_CSLOTS) - 1) & 1, fail);
+            if (!__all_sync(0xffffffffu, ok ? 1 : 0)) { stop = true; break; }
+            const int cols = (int)min((int64_t)32, a.N - (n0 + cc));
+            if (lane == 0) mbar_expect_tx(&c_full[slot], (uint32_t)(rows * 4 * cols));
+            __syncwarp();
+            if (lane < cols)
+              bulk_g2s(cbox + (size_t)slot * (T4_CBOX / 4) + lane * 128,
+                       Cr + r0 + (n0 + cc + lane) * ldr, (uint32_t)(rows * 4), &c_full[slot]);
+          }
+        }
+      }
+      // copies still in flight land before the CTA exits
+      for (int q = seg - 1; q >= 0 && q > seg - 1 - T4_CSLOTS; --q)
+        wwait(&c_full[q % T4_CSLOTS], (uint32_t)(q / T4_CSLOTS) & 1, fail, false);
+    }
   } else if (warp >= 4 && warp < 8) {
     // ---- converters
     const int ct = tid - 128;
@@ -797,7 +844,10 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
         const unsigned char* raw = rawbase + slot * T4_RAWB;
         unsigned char* bhi = smem_p4 + st * T4_STAGE + T4_ABYTES;
         unsigned char* blo = bhi + T4_BN * P_BK * 4;
-        for (int idx = ct; idx < T4_BN * (P_BK / 4); idx += 128) {
+        static_assert(T4_BN * (P_BK / 4) == 4 * 128, "four 16-byte pieces per converter thread");
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int idx = ct + 128 * j;
           const int q = idx & 3, col = idx >> 2;
           const float4 x = *reinterpret_cast<const float4*>(raw + idx * 16);
           uint4 hh, ll;
@@ -820,7 +870,10 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
   } else if (warp >= 8) {
     // ---- epilogue (warp 8 + e owns TMEM lanes 32e..32e+31 of each half)
     const int e = warp - 8;
-    for (int it = 0; it < ntile_cta; ++it) {
+    const bool boxed = a.c_bulk && a.epi != TC_EPI_OUT;
+    int seg = 0;
+    bool stop = false;
+    for (int it = 0; it < ntile_cta && !stop; ++it) {
       int64_t t, m0, n0;
       tile_of(it, t, m0, n0);
       const int mh = (a.M - m0) > 128 ? 2 : 1;
@@ -830,18 +883,41 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
       tc_fence_after();
       float* C = a.C + t * a.sC;
       const float* C1 = a.C1 ? a.C1 + t * a.sC1 : nullptr;
-      for (int h = 0; h < mh; ++h) {
+      for (int h = 0; h < mh && !stop; ++h) {
         const int64_t row = m0 + h * 128 + e * 32 + lane;
-        for (int cc = 0; cc < T4_BN; cc += 32) {
+        for (int cc = 0; cc < T4_BN; cc += 32, ++seg) {
           if (n0 + cc >= a.N) break;
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(e * 32) << 16) + (uint32_t)(buf * 256 + h * T4_BN + cc), v);
-          tc_epi32(a, C, C1, row, n0 + cc, v);
+          if (!boxed) {
+            tc_epi32(a, C, C1, row, n0 + cc, v);
+            continue;
+          }
+          // the segment's old values come from the loader's box (column c at c * 128)
+          const int slot = seg % T4_CSLOTS;
+          ok = wwait(&c_full[slot], (uint32_t)(seg / T4_CSLOTS) & 1, fail);
+          if (!__all_sync(0xffffffffu, ok ? 1 : 0)) { stop = true; break; }
+          const float* bx = cbox + (size_t)slot * (T4_CBOX / 4) + e * 32 + lane;
+          if (row < a.M) {
+            const int64_t lim = a.N - (n0 + cc);
+            float* Cr = C + row + (n0 + cc) * a.ldc;
+            if (a.epi == TC_EPI_SUB) {
+#pragma unroll
+              for (int i = 0; i < 32; ++i)
+                if (i < lim) Cr[(int64_t)i * a.ldc] = bx[i * 128] - v[i];
+            } else {
+#pragma unroll
+              for (int i = 0; i < 32; ++i)
+                if (i < lim) Cr[(int64_t)i * a.ldc] = v[i] + bx[i * 128];
+            }
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive1(&c_empty[slot]);
         }
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive1(&acc_empty[buf]);
+      if (lane == 0 && !stop) mbar_arrive1(&acc_empty[buf]);
     }
   }
   tc_fence_before();
@@ -897,8 +973,17 @@ void launch_tc2(const TcArgs& a, int batch, const char* name, cudaStream_t s) {
     // and operand kernels of the next steps keep SMs of their own (a grid over every SM held
     // them off for whole launches; short-lived CTAs cost the pipeline fill and drain of each)
     const int ctas = (int)std::min<int64_t>(total, std::max(1, sms - sms / 9));
+    // bulk copies of the accumulating epilogue's column segments need every segment start
+    // 16-byte aligned and a whole number of 16 bytes per column
+    TcArgs b = a;
+    const bool sub = a.epi == TC_EPI_SUB;
+    const float* Cr = sub ? a.C : a.C1;
+    const int64_t ldr = sub ? a.ldc : a.ldc1, sr = sub ? a.sC : a.sC1;
+    b.c_bulk = a.epi != TC_EPI_OUT && Cr != nullptr &&
+               (reinterpret_cast<uintptr_t>(Cr) % 16) == 0 && (ldr % 4) == 0 &&
+               (batch == 1 || (sr % 4) == 0) && (a.M % 4) == 0;
     ensure_dyn_smem<k_gemm_tc4>(T4_SMEM);
-    k_gemm_tc4<<<ctas, T4_THREADS, T4_SMEM, s>>>(a, mtiles, ntiles, (int)total);
+    k_gemm_tc4<<<ctas, T4_THREADS, T4_SMEM, s>>>(b, mtiles, ntiles, (int)total);
   } else {
     ensure_dyn_smem<k_gemm_tc2>(P_SMEM);
     k_gemm_tc2<<<grid, TC_THREADS, P_SMEM, s>>>(a);
