@@ -209,6 +209,19 @@ int luqr_refine_gmres(luqr_handle_t h, const double* dA, int64_t lda, const doub
 int luqr_debug_replay_skip(luqr_handle_t h, int task);
 
 /*
+ * luqr_debug_tc_skip - test hook for the failure path of the bounded waits of the
+ * persistent tensor-core update kernel (the FP32 factorization's trailing updates).  While
+ * chunk >= 0, CTA 0 of every launch of that kernel leaves the arrival of its raw B chunk
+ * number `chunk` unsignalled, so the waits on it run out after the timeout_ms budget of the
+ * factorization's options: the kernel records LUQR_ERR_TIMEOUT in the handle's status word,
+ * waits (bounded) for its own copies and tensor-core operations, frees its tensor memory
+ * and returns, and the later kernels of the factorization exit at once.  Process-wide,
+ * applies to launches enqueued after the call; -1 restores normal operation.
+ * LUQR_ERR_INVALID for chunk < -1.  Not for production use.
+ */
+int luqr_debug_tc_skip(int chunk);
+
+/*
  * luqr_accuracy - accuracy of the solution that the last luqr_refine / luqr_refine_gmres
  * call returned (Sec. V-A), from the FP64 infinity norms that refinement computed on the
  * GPU: eta = ||b - A x|| / (||A|| ||x|| + ||b||) (normwise backward error) and

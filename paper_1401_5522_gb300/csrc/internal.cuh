@@ -199,7 +199,14 @@ struct TcArgs {
   // the C (EPI_SUB) or C1 (EPI_ADD_OUT) blocks an epilogue reads may be brought into shared
   // memory by bulk copies (set by launch_tc2 when every column segment is 16-byte aligned)
   int c_bulk;
+  // budget of each bounded wait of the persistent kernel in clock cycles (0: the default,
+  // about 0.5 s)
+  long long wait_cycles;
 };
+// Test hook of the persistent tensor-core kernel: while >= 0, CTA 0 of every launch does not
+// signal the arrival of its raw B chunk with this index, so the converters' wait on it runs
+// out (see luqr_debug_tc_skip).
+void tc_set_debug_skip(int chunk);
 void launch_tc(const TcArgs& a, int batch, const char* name, cudaStream_t s);
 // Packed-A form: pack A once (launch_tc_pack), then launch_tc2 with a.Apk/a.sApk set.
 size_t tc_packed_bytes(int64_t M, int K);
@@ -312,8 +319,12 @@ void launch_features_spec(const T* W, int64_t ldw, int k, int n, int nb, double 
                           const unsigned long long* away, const uint8_t* dec, const double* margin,
                           float* feat, int mode, const float* params, uint8_t* spec,
                           cudaStream_t s);
+// After the decision of step k: qrfac / commit as below for QR; lufac[k] = LU when LU was
+// chosen and not speculated (TRSM in place), lucmt[k] = LU when LU was chosen and the
+// speculative TRSM on the shadow copy is committed (lu_spec: the LU branch is speculated).
 void launch_spec_resolve(int k, const uint8_t* dec, const uint8_t* spec, uint8_t* qrfac,
-                         uint8_t* commit, cudaStream_t s);
+                         uint8_t* commit, uint8_t* lufac, uint8_t* lucmt, bool lu_spec,
+                         cudaStream_t s);
 template <typename T>
 void launch_gated_copy(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t rows, int cols,
                        const uint8_t* gate, int k, uint8_t want, const char* name, cudaStream_t s);

@@ -287,18 +287,25 @@ template void launch_features_spec<double>(const double*, int64_t, int, int, int
 // ---------------------------------------------------------------- speculation helpers
 // qrfac[k] = QR when the criterion chose QR and the step was not speculated (the panel is
 // factored in place); commit[k] = QR when it chose QR and the speculative copy is used.
+// lufac[k] = LU when it chose LU and the LU branch was not speculated (the panel's TRSM runs
+// in place); lucmt[k] = LU when it chose LU and the speculative TRSM's copy is used.
 __global__ void k_spec_resolve(int k, const uint8_t* __restrict__ dec,
                                const uint8_t* __restrict__ spec, uint8_t* __restrict__ qrfac,
-                               uint8_t* __restrict__ commit) {
+                               uint8_t* __restrict__ commit, uint8_t* __restrict__ lufac,
+                               uint8_t* __restrict__ lucmt, bool lu_spec) {
   const bool qr = dec[k] == DEC_QR, sp = spec[k] == DEC_QR;
+  const bool lu = dec[k] == DEC_LU, splu = lu_spec && spec[k] == DEC_LU;
   qrfac[k] = (qr && !sp) ? DEC_QR : DEC_LU;
   commit[k] = (qr && sp) ? DEC_QR : DEC_LU;
+  lufac[k] = (lu && !splu) ? DEC_LU : DEC_QR;
+  lucmt[k] = (lu && splu) ? DEC_LU : DEC_QR;
 }
 
 void launch_spec_resolve(int k, const uint8_t* dec, const uint8_t* spec, uint8_t* qrfac,
-                         uint8_t* commit, cudaStream_t s) {
+                         uint8_t* commit, uint8_t* lufac, uint8_t* lucmt, bool lu_spec,
+                         cudaStream_t s) {
   ProfScope ps_("k_spec_resolve", s);
-  k_spec_resolve<<<1, 1, 0, s>>>(k, dec, spec, qrfac, commit);
+  k_spec_resolve<<<1, 1, 0, s>>>(k, dec, spec, qrfac, commit, lufac, lucmt, lu_spec);
 }
 
 // dst(r, c) = src(r, c) for r < rows, c < cols when gate[k] == want (16-byte vectors when

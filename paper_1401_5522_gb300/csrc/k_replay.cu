@@ -126,10 +126,12 @@ __device__ void rp_qr_vec(const T* __restrict__ V, int64_t ldv, const T* __restr
       if (lane == 0) w[j] = pair ? acc + xe[jb + j] : acc;
     }
     __syncthreads();
-    if (warp == 0) {
-      T acc = (T)0;
-      for (int a = 0; a <= lane; ++a) acc += ts[(size_t)lane * IB + a] * w[a];
-      w2[lane] = acc;
+    // w2 = T_b^T w: column c of T_b (T(a, c) at ts[c * IB + a], a <= c) is read by the lanes
+    // of one warp (lane = a, consecutive words), then summed across the warp
+    for (int c = warp; c < IB; c += nw) {
+      const T t = (lane <= c) ? ts[(size_t)c * IB + lane] * w[lane] : (T)0;
+      const T acc = warp_sum<T>(t);
+      if (lane == 0) w2[c] = acc;
     }
     __syncthreads();
     for (int r = r0 + tid; r < r1; r += NT) {

@@ -15,6 +15,7 @@
 // Every wait on an mbarrier is bounded; on expiry the kernel records LUQR_ERR_TIMEOUT in
 // the status word, waits (bounded) for its own MMAs, frees its TMEM and returns.
 #include <algorithm>
+#include <atomic>
 
 #include "internal.cuh"
 
@@ -579,7 +580,8 @@ __device__ __forceinline__ void cp_async_wait_group() {
 constexpr long long W_WAIT_CYCLES = 1000000000LL;   // ~0.5 s
 
 __device__ __forceinline__ bool wwait(uint64_t* bar, uint32_t parity, volatile int* fail,
-                                      bool honour_fail = true) {
+                                      bool honour_fail = true,
+                                      long long budget = W_WAIT_CYCLES) {
   const uint32_t a = smem_u32(bar);
   const long long t0 = clock64();
   for (;;) {
@@ -592,7 +594,7 @@ __device__ __forceinline__ bool wwait(uint64_t* bar, uint32_t parity, volatile i
         : "memory");
     if (done) return true;
     if (honour_fail && *fail) return false;
-    if (clock64() - t0 > W_WAIT_CYCLES) {
+    if (clock64() - t0 > budget) {
       *fail = 1;
       return false;
     }
@@ -631,7 +633,7 @@ constexpr int T4_SMEM = T4_STG * T4_STAGE + T4_RAW * T4_RAWB + T4_CSLOTS * T4_CB
 static_assert(T4_SMEM <= SMEM_MAX, "persistent GEMM stages exceed the shared memory of a CTA");
 
 __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles, int ntiles,
-                                                     int total) {
+                                                     int total, int skip) {
   if (a.dec != nullptr && a.dec[a.k_step] != a.want) return;
   if (a.status != nullptr && a.status[ST_CODE] != 0) return;
   extern __shared__ __align__(1024) unsigned char smem_p4[];
@@ -692,6 +694,7 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *taddr_slot;
+  const long long budget = a.wait_cycles > 0 ? a.wait_cycles : W_WAIT_CYCLES;
 
   if (warp == 0) {
     // ---- raw B producer
@@ -702,7 +705,7 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
       const float* B = a.B + t * a.sB;
       for (int c = 0; c < nK; ++c) {
         const int g = it * nK + c, slot = g % T4_RAW;
-        bool ok = g < T4_RAW || wwait(&raw_empty[slot], (uint32_t)((g / T4_RAW) - 1) & 1, fail);
+        bool ok = g < T4_RAW || wwait(&raw_empty[slot], (uint32_t)((g / T4_RAW) - 1) & 1, fail, true, budget);
         if (!__all_sync(0xffffffffu, ok ? 1 : 0)) { stop = true; break; }
         unsigned char* raw = rawbase + slot * T4_RAWB;
         const int k0 = c * P_BK;
@@ -713,9 +716,10 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
           const float* src = in ? B + (k0 + 4 * q) + gc * a.ldb : B;
           cp_async16_zfill(raw + idx * 16, src, in ? 16u : 0u);
         }
-        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
-                         smem_u32(&raw_full[slot]))
-                     : "memory");
+        if (g != skip || blockIdx.x != 0)   // skip: test hook, normally -1
+          asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                           smem_u32(&raw_full[slot]))
+                       : "memory");
       }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
@@ -730,13 +734,13 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
         tile_of(it, t, m0, n0);
         const int mh = (a.M - m0) > 128 ? 2 : 1;
         const int buf = it & 1;
-        if (it >= 2 && !wwait(&acc_empty[buf], (uint32_t)((it / 2) - 1) & 1, fail)) break;
+        if (it >= 2 && !wwait(&acc_empty[buf], (uint32_t)((it / 2) - 1) & 1, fail, true, budget)) break;
         tc_fence_after();
         bool started[2] = {false, false};
         for (int c = 0; c < nK; ++c) {
           const int g = it * nK + c, st = g % T4_STG;
           const uint32_t ph = (uint32_t)(g / T4_STG) & 1;
-          if (!wwait(&a_full[st], ph, fail) || !wwait(&b_full[st], ph, fail)) { stop = true; break; }
+          if (!wwait(&a_full[st], ph, fail, true, budget) || !wwait(&b_full[st], ph, fail, true, budget)) { stop = true; break; }
           tc_fence_after();
           unsigned char* sa = smem_p4 + st * T4_STAGE;
           const uint32_t sbase = smem_u32(sa + T4_ABYTES);
@@ -767,7 +771,7 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
         tc_commit(&acc_full[buf]);
       }
       if (last_g >= 0)
-        wwait(&st_empty[last_g % T4_STG], (uint32_t)(last_g / T4_STG) & 1, fail, false);
+        wwait(&st_empty[last_g % T4_STG], (uint32_t)(last_g / T4_STG) & 1, fail, false, budget);
     }
   } else if (warp == 2) {
     // ---- packed A producer
@@ -781,7 +785,7 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
         const unsigned char* Apk = a.Apk + t * a.sApk;
         for (int c = 0; c < nK; ++c) {
           const int g = it * nK + c, st = g % T4_STG;
-          if (g >= T4_STG && !wwait(&st_empty[st], (uint32_t)((g / T4_STG) - 1) & 1, fail)) {
+          if (g >= T4_STG && !wwait(&st_empty[st], (uint32_t)((g / T4_STG) - 1) & 1, fail, true, budget)) {
             stop = true;
             break;
           }
@@ -795,7 +799,7 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
         }
       }
       for (int q = last_g; q >= 0 && q > last_g - T4_STG; --q)
-        wwait(&a_full[q % T4_STG], (uint32_t)(q / T4_STG) & 1, fail, false);
+        wwait(&a_full[q % T4_STG], (uint32_t)(q / T4_STG) & 1, fail, false, budget);
     }
   } else if (warp == 3) {
     // ---- C loader (accumulating epilogues with aligned segments only)
@@ -816,7 +820,7 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
             if (n0 + cc >= a.N) break;
             const int slot = seg % T4_CSLOTS;
             bool ok = seg < T4_CSLOTS ||
-                      wwait(&c_empty[slot], (uint32_t)((seg / T4_CSLOTS) - 1) & 1, fail);
+                      wwait(&c_empty[slot], (uint32_t)((seg / T4_CSLOTS) - 1) & 1, fail, true, budget);
             if (!__all_sync(0xffffffffu, ok ? 1 : 0)) { stop = true; break; }
             const int cols = (int)min((int64_t)32, a.N - (n0 + cc));
             if (lane == 0) mbar_expect_tx(&c_full[slot], (uint32_t)(rows * 4 * cols));
@@ -829,7 +833,7 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
       }
       // copies still in flight land before the CTA exits
       for (int q = seg - 1; q >= 0 && q > seg - 1 - T4_CSLOTS; --q)
-        wwait(&c_full[q % T4_CSLOTS], (uint32_t)(q / T4_CSLOTS) & 1, fail, false);
+        wwait(&c_full[q % T4_CSLOTS], (uint32_t)(q / T4_CSLOTS) & 1, fail, false, budget);
     }
   } else if (warp >= 4 && warp < 8) {
     // ---- converters
@@ -838,8 +842,8 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
     for (int it = 0; it < ntile_cta && !stop; ++it) {
       for (int c = 0; c < nK; ++c) {
         const int g = it * nK + c, slot = g % T4_RAW, st = g % T4_STG;
-        bool ok = wwait(&raw_full[slot], (uint32_t)(g / T4_RAW) & 1, fail);
-        if (ok && g >= T4_STG) ok = wwait(&st_empty[st], (uint32_t)((g / T4_STG) - 1) & 1, fail);
+        bool ok = wwait(&raw_full[slot], (uint32_t)(g / T4_RAW) & 1, fail, true, budget);
+        if (ok && g >= T4_STG) ok = wwait(&st_empty[st], (uint32_t)((g / T4_STG) - 1) & 1, fail, true, budget);
         if (!__all_sync(0xffffffffu, ok ? 1 : 0)) { stop = true; break; }
         const unsigned char* raw = rawbase + slot * T4_RAWB;
         unsigned char* bhi = smem_p4 + st * T4_STAGE + T4_ABYTES;
@@ -878,7 +882,7 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
       tile_of(it, t, m0, n0);
       const int mh = (a.M - m0) > 128 ? 2 : 1;
       const int buf = it & 1;
-      bool ok = wwait(&acc_full[buf], (uint32_t)(it / 2) & 1, fail);
+      bool ok = wwait(&acc_full[buf], (uint32_t)(it / 2) & 1, fail, true, budget);
       if (!__all_sync(0xffffffffu, ok ? 1 : 0)) break;
       tc_fence_after();
       float* C = a.C + t * a.sC;
@@ -895,7 +899,7 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
           }
           // the segment's old values come from the loader's box (column c at c * 128)
           const int slot = seg % T4_CSLOTS;
-          ok = wwait(&c_full[slot], (uint32_t)(seg / T4_CSLOTS) & 1, fail);
+          ok = wwait(&c_full[slot], (uint32_t)(seg / T4_CSLOTS) & 1, fail, true, budget);
           if (!__all_sync(0xffffffffu, ok ? 1 : 0)) { stop = true; break; }
           const float* bx = cbox + (size_t)slot * (T4_CBOX / 4) + e * 32 + lane;
           if (row < a.M) {
@@ -928,6 +932,9 @@ __global__ void __launch_bounds__(T4_THREADS, 1) k_gemm_tc4(TcArgs a, int mtiles
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
 }
+
+static std::atomic<int> g_tc_skip{-1};
+void tc_set_debug_skip(int chunk) { g_tc_skip.store(chunk < 0 ? -1 : chunk); }
 
 size_t tc_packed_bytes(int64_t M, int K) {
   const int64_t mb = (M + 127) / 128, nK = (K + P_BK - 1) / P_BK;
@@ -983,7 +990,8 @@ void launch_tc2(const TcArgs& a, int batch, const char* name, cudaStream_t s) {
                (reinterpret_cast<uintptr_t>(Cr) % 16) == 0 && (ldr % 4) == 0 &&
                (batch == 1 || (sr % 4) == 0) && (a.M % 4) == 0;
     ensure_dyn_smem<k_gemm_tc4>(T4_SMEM);
-    k_gemm_tc4<<<ctas, T4_THREADS, T4_SMEM, s>>>(b, mtiles, ntiles, (int)total);
+    k_gemm_tc4<<<ctas, T4_THREADS, T4_SMEM, s>>>(b, mtiles, ntiles, (int)total,
+                                                  g_tc_skip.load(std::memory_order_relaxed));
   } else {
     ensure_dyn_smem<k_gemm_tc2>(P_SMEM);
     k_gemm_tc2<<<grid, TC_THREADS, P_SMEM, s>>>(a);

@@ -76,6 +76,8 @@ struct luqr_handle {
   uint8_t* spec = nullptr;      // predicted decision per step
   uint8_t* qrfac = nullptr;     // QR chosen and not speculated: factor in place
   uint8_t* cmt = nullptr;       // QR chosen and speculated: commit the shadow copy
+  uint8_t* lufac = nullptr;     // LU chosen and not speculated: TRSM in place
+  uint8_t* lucmt = nullptr;     // LU chosen and speculated: commit the shadow TRSM
   void* shadow = nullptr;       // Npad x nb copy of the panel column (same leading dimension)
   cudaStream_t spec_stream = nullptr;
   cudaStream_t panel_stream = nullptr;   // high priority; the caller's stream waits on it
@@ -83,7 +85,7 @@ struct luqr_handle {
   cudaStream_t extra_stream = nullptr;   // tensor-core operand preparation of QR steps
   std::vector<cudaEvent_t> ev_lvl;       // per tile list of the current step (reused)
   std::vector<cudaEvent_t> ev_extra, ev_la;
-  std::vector<cudaEvent_t> ev_stats, ev_spec;
+  std::vector<cudaEvent_t> ev_stats, ev_spec, ev_getrf, ev_luspec;
   cudaEvent_t ev_end = nullptr;
   // second pass / refinement scratch
   void* rhs_ws = nullptr;
@@ -132,6 +134,7 @@ void tc_factor_extra(luqr_handle* h, int k, TileList tl, int kind, int mask, cud
   float* Tf = h->Tfull[k & 1];
   float* Vt = h->Vt[k & 1];
   TcArgs a{};
+  a.wait_cycles = h->wait_cycles;
   a.dec = h->dec; a.k_step = k; a.want = DEC_QR; a.status = h->status;
   a.M = nb; a.N = nb; a.K = nb; a.epi = TC_EPI_OUT;
   // G = V^T V
@@ -168,6 +171,7 @@ void tc_apply_single(luqr_handle* h, int k, TileList tl, Mat<float> C, int64_t c
   const unsigned char* pk = h->Apk[k & 1] + (((size_t)tl.i0 * 2 + 0) * 3) * h->pk_tile;
   const int64_t spk = (int64_t)tl.istride * 2 * 3 * (int64_t)h->pk_tile;
   TcArgs a{};
+  a.wait_cycles = h->wait_cycles;
   a.dec = h->dec; a.k_step = k; a.want = DEC_QR; a.status = h->status;
   a.M = nb; a.N = c1 - c0; a.K = nb; a.sApk = spk;
   // W = V^T C  (V unit lower triangular: V^T upper)
@@ -192,6 +196,7 @@ void tc_apply_pair(luqr_handle* h, int k, TileList tl, bool tri, Mat<float> C, i
   const unsigned char* pk = h->Apk[k & 1] + (((size_t)tl.i0 * 2 + 1) * 3) * h->pk_tile;
   const int64_t spk = (int64_t)tl.istride * 2 * 3 * (int64_t)h->pk_tile;
   TcArgs a{};
+  a.wait_cycles = h->wait_cycles;
   a.dec = h->dec; a.k_step = k; a.want = DEC_QR; a.status = h->status;
   a.M = nb; a.N = c1 - c0; a.K = nb; a.sApk = spk;
   // W = C1 + V2^T C2  (TT: V2 upper triangular, V2^T lower)
@@ -398,6 +403,7 @@ void enqueue_lu_apply(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, c
   if constexpr (std::is_same<T, float>::value) {
     if (tc_apply && h->Xpk[k & 1] != nullptr && c1 - c0 >= 64) {
       TcArgs a{};
+      a.wait_cycles = h->wait_cycles;
       a.dec = h->dec; a.k_step = k; a.want = DEC_LU; a.status = h->status;
       a.M = nb; a.N = c1 - c0; a.K = nb;
       a.Apk = h->Xpk[k & 1];
@@ -422,6 +428,7 @@ void enqueue_lu_apply(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, c
   if constexpr (std::is_same<T, float>::value) {
     if (tc && h->use_tc) {
       TcArgs a{};
+      a.wait_cycles = h->wait_cycles;
       a.dec = h->dec; a.k_step = k; a.want = DEC_LU; a.status = h->status;
       a.M = h->Npad - r1; a.N = c1 - c0; a.K = nb;
       a.Apk = h->Lpk[k & 1];   // packed by the factor phase (pack_lu_panel)
@@ -466,6 +473,7 @@ void enqueue_factor(luqr_handle* h) {
       launch_scale_rows<T>(W, ld, r0, nb, r0, h->Wc, std::ldexp(1.0, -27), s);
     }
     const int dd = std::min(h->domain, n - k);   // tiles of this step's pivot domain
+    const bool lu_spec = spec && h->lu_variant == 0 && dd <= 1;
     int* dpiv_k = h->dpiv_all ? h->dpiv_all + (size_t)k * nb : nullptr;
     if (dd > 1) {
       // Factor over the diagonal domain: the exchanges reach every column >= k, so the
@@ -507,6 +515,19 @@ void enqueue_factor(luqr_handle* h) {
         launch_qt_cols<T>(S, nb, nb, Tkk, 0, h->colsum, nullptr, h->status, h->gate_all, k, s);
     } else {
       if (dd <= 1) launch_getrf<T>(W, ld, k, nb, S, h->piv_s, h->status, s);
+      if (lu_spec) {
+        // predicted LU: the panel's TRSM (A_ik U^-1, i > k) with the scratch LU on a copy of
+        // the sub-diagonal tiles, while the inverse norm and the decision run
+        cudaEventRecord(h->ev_getrf[k], s);
+        cudaStreamWaitEvent(sp, h->ev_getrf[k], 0);
+        if (r1 < h->Npad) {
+          launch_gated_copy<T>(W + r1 + r0 * ld, ld, shadow + r1, ld, h->Npad - r1, nb, h->spec,
+                               k, DEC_LU, "k_spec_copy_lu", sp);
+          launch_trsm<T>(Mat<const T>{S, nb}, nb, Mat<T>{shadow, ld}, r1, h->Npad, 0, h->spec,
+                         k, sp);
+        }
+        cudaEventRecord(h->ev_luspec[k], sp);
+      }
       if (need_inv) {
         if (h->norm_mode == 1) launch_invnorm_est<T>(S, nb, h->piv_s, h->colsum, h->status, s);
         else launch_invnorm<T>(S, nb, h->piv_s, h->colsum, h->status, s);
@@ -517,14 +538,21 @@ void enqueue_factor(luqr_handle* h) {
                   h->dec,   h->margin, h->lhs,   h->rhs,       h->status};
     da.seed = h->seed;
     launch_decide<T>(da, S, s);
-    if (spec) launch_spec_resolve(k, h->dec, h->spec, h->qrfac, h->cmt, s);
+    if (spec)
+      launch_spec_resolve(k, h->dec, h->spec, h->qrfac, h->cmt, h->lufac, h->lucmt, lu_spec, s);
     if (h->lu_variant == 1) launch_a2_gate(h->dec, h->a2gate, k, s);
     if (dd > 1)   // an LU step applies the domain's exchanges to columns k.. and b first
       launch_domain_swap<T>(W, ld, k, nb, dd * nb, r0, h->Wc, dpiv_k, h->dec, s);
     // ---- factor the panel: LU (Alg. 2: commit + TRSM) or QR (GEQRT + TS/TT chain)
     launch_lu_commit<T>(W, ld, k, nb, S, h->piv_s, h->piv_all + (size_t)k * nb, h->dec, s);
+    if (lu_spec) {   // the speculative TRSM is done (and S is free for the next step)
+      cudaStreamWaitEvent(s, h->ev_luspec[k], 0);
+      if (r1 < h->Npad)
+        launch_gated_copy<T>(shadow + r1, ld, W + r1 + r0 * ld, ld, h->Npad - r1, nb, h->lucmt,
+                             k, DEC_LU, "k_spec_commit_lu", s);
+    }
     Mat<const T> LU{W + r0 + r0 * ld, ld};
-    launch_trsm<T>(LU, nb, F, r1, h->Npad, r0, h->dec, k, s);
+    launch_trsm<T>(LU, nb, F, r1, h->Npad, r0, spec ? h->lufac : h->dec, k, s);
     if constexpr (std::is_same<T, float>::value) {
       if (h->use_tc && r1 < h->Npad)   // pack A_ik U^-1 for the tensor-core trailing GEMM
         launch_tc_pack(reinterpret_cast<float*>(W) + r1 + r0 * ld, ld, 0, 0, TC_MASK_NONE,
@@ -678,6 +706,8 @@ void free_handle(luqr_handle* h) {
   if (h->ev_start) cudaEventDestroy(h->ev_start);
   for (cudaEvent_t e : h->ev_stats) if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : h->ev_spec) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_getrf) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_luspec) if (e) cudaEventDestroy(e);
   if (h->ev_end) cudaEventDestroy(h->ev_end);
   if (h->upd_stream) cudaStreamDestroy(h->upd_stream);
   if (h->spec_stream) cudaStreamDestroy(h->spec_stream);
@@ -693,7 +723,8 @@ void free_handle(luqr_handle* h) {
                   h->Gbuf,   h->Tfull[0], h->Tfull[1], h->Vt[0], h->Vt[1], h->gm,
                   h->Apk[0], h->Apk[1],   h->Lpk[0],   h->Lpk[1], h->feat, h->spec,
                   h->Linv[0], h->Linv[1], h->Xpk[0],   h->Xpk[1],
-                  h->qrfac,  h->cmt,      h->shadow, h->gate_all, h->a2gate, h->rq,
+                  h->qrfac,  h->cmt,      h->lufac,    h->lucmt, h->shadow, h->gate_all,
+                  h->a2gate, h->rq,
                   h->rq_ctl, h->St, h->dpiv_all};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -948,6 +979,8 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
     A((void**)&h->spec, (size_t)n);
     A((void**)&h->qrfac, (size_t)n);
     A((void**)&h->cmt, (size_t)n);
+    A((void**)&h->lufac, (size_t)n);
+    A((void**)&h->lucmt, (size_t)n);
     A(&h->shadow, (size_t)h->Npad * nb * h->elt);
   }
   int prio_low = 0, prio_high = 0;
@@ -982,9 +1015,14 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
   if (o.speculate) {
     h->ev_stats.assign(n, nullptr);
     h->ev_spec.assign(n, nullptr);
+    h->ev_getrf.assign(n, nullptr);
+    h->ev_luspec.assign(n, nullptr);
     for (int q = 0; q < n && e == cudaSuccess; ++q) {
       e = cudaEventCreateWithFlags(&h->ev_stats[q], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_spec[q], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_getrf[q], cudaEventDisableTiming);
+      if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&h->ev_luspec[q], cudaEventDisableTiming);
     }
   }
   if (o.timeout_ms > 0) h->wait_cycles = (long long)o.timeout_ms * 2070000LL;  // cycles at 2.07 GHz
@@ -1136,6 +1174,12 @@ int luqr_refine_gmres(luqr_handle_t h, const double* dA, int64_t lda, const doub
   if (h->prec == LUQR_PREC_FP64)
     return refine_gmres_impl<double>(h, dA, lda, db, dx, tol, max_iter, restart, iters, eta);
   return refine_gmres_impl<float>(h, dA, lda, db, dx, tol, max_iter, restart, iters, eta);
+}
+
+int luqr_debug_tc_skip(int chunk) {
+  if (chunk < -1) return LUQR_ERR_INVALID;
+  luqr::tc_set_debug_skip(chunk);
+  return LUQR_OK;
 }
 
 int luqr_debug_replay_skip(luqr_handle_t h, int task) {

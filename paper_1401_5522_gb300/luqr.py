@@ -67,6 +67,7 @@ _SIGS = {
     "luqr_decisions": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
     "luqr_accuracy": (ctypes.c_int, [_P, _P, _P, _P]),
     "luqr_debug_replay_skip": (ctypes.c_int, [_P, ctypes.c_int]),
+    "luqr_debug_tc_skip": (ctypes.c_int, [ctypes.c_int]),
     "luqr_step_stats": (ctypes.c_int, [_P, _P, _P]),
     "luqr_factor_data": (ctypes.c_int, [_P, _P, _I64]),
     "luqr_sync": (ctypes.c_int, [_P]),

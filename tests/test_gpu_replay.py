@@ -10,6 +10,8 @@ its bounded waits.
   a 2 ms budget the next task on that tile row gives up, the call reports
   LUQR_ERR_TIMEOUT, and the device stays usable (a following normal solve on a new handle
   is correct).  Nothing faults: the wait is a polling loop with a clock budget.
+* The same for the persistent tensor-core update kernel of the FP32 factorization (one raw
+  operand chunk left unsignalled).
 """
 import ctypes
 
@@ -117,3 +119,34 @@ def test_bounded_wait_runs_out_and_device_stays_usable():
     h2.close()
     assert O.backward_error(A, db.cpu().numpy(), b) <= 1e-13
     assert O.backward_error(A, x2.cpu().numpy(), b) <= 1e-13
+
+
+def test_tensor_core_wait_runs_out_and_device_stays_usable():
+    """The persistent tensor-core update kernel's bounded waits: a test hook leaves one raw B
+    chunk of CTA 0 unsignalled, so with a 2 ms budget the converters' wait runs out; the
+    factorization reports LUQR_ERR_TIMEOUT (the kernel freed its tensor memory and returned),
+    and after the hook is cleared a new FP32 factorization and solve on the same device are
+    correct.  Nothing faults: every wait is a polling loop with a clock budget."""
+    from paper_1401_5522_gb300 import luqr
+    N, nb = 1024, 128
+    A = inputs.gaussian(N, 15).numpy()
+    b = A @ np.ones(N)
+    dA = colmajor(A)
+    L = luqr.lib()
+    assert L.luqr_debug_tc_skip(-2) == luqr.ERR_INVALID
+    assert L.luqr_debug_tc_skip(0) == luqr.OK
+    try:
+        h = luqr.factor(dA, nb, "max", 100.0, tree="binary_tt", precision="fp32", timeout_ms=2)
+        st = h.sync()
+        status, step, _ = h.info()
+        h.close()
+    finally:
+        assert L.luqr_debug_tc_skip(-1) == luqr.OK
+    assert st == luqr.ERR_TIMEOUT and status == luqr.ERR_TIMEOUT, (st, status)
+    torch.cuda.synchronize()
+    h2 = luqr.factor(dA, nb, "max", 100.0, tree="binary_tt", precision="fp32")
+    x = torch.zeros(N, dtype=torch.float64, device="cuda")
+    st2, its, eta = h2.refine(dA, torch.from_numpy(b).cuda(), x, tol=1e-13, max_iter=30)
+    h2.close()
+    assert st2 == luqr.OK and eta <= 1e-13, (st2, its, eta)
+    assert O.backward_error(A, x.cpu().numpy(), b) <= 1e-13
