@@ -6,6 +6,8 @@
 
 #include <mutex>
 
+#include "smem_record.h"
+
 namespace luqr {
 
 constexpr int IB = 32;              // inner block of the Householder kernels (T is IB x IB per block)
@@ -78,28 +80,18 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // Raises kernel K's dynamic shared-memory limit to `bytes` when a launch needs more than
-// the limit already set on the current device.  cudaFuncSetAttribute acts on the current
-// device only, so the record is kept per device (up to ENSURE_SMEM_DEVICES; beyond that the
-// attribute is set on every launch), under a lock shared by the host threads.  The request
-// is the launch's own size, so kernels that also use static shared memory stay within the
-// per-block maximum.
-constexpr int ENSURE_SMEM_DEVICES = 64;
+// the limit already set on the current device (the record is per device and locked:
+// smem_record.h).  The request is the launch's own size, so kernels that also use static
+// shared memory stay within the per-block maximum.
 template <auto K>
 inline void ensure_dyn_smem(size_t bytes) {
-  static std::mutex mu;
-  static size_t cur[ENSURE_SMEM_DEVICES] = {};   // 0: the 48 KB default
+  static SmemRecord rec;
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= ENSURE_SMEM_DEVICES) {
-    if (bytes > 48 * 1024)
-      cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    return;
-  }
-  std::lock_guard<std::mutex> lk(mu);
-  const size_t have = cur[dev] ? cur[dev] : (size_t)48 * 1024;
-  if (bytes > have &&
-      cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
-          cudaSuccess)
-    cur[dev] = bytes;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  rec.ensure(dev, bytes, [](size_t b) {
+    return cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b) ==
+           cudaSuccess;
+  });
 }
 
 // ---------------------------------------------------------------- launch profiler

@@ -1,6 +1,7 @@
 """Host-side logic of the Python package that needs no GPU: folding the feature
 standardisation into the MLP's first layer, the repeat-previous predictor, and the batched
 solver's size buckets."""
+import os
 import numpy as np
 import pytest
 
@@ -100,3 +101,57 @@ def test_bench_tree_counts_cover_every_tile():
                 assert s - 1 == tt
     assert bench.tree_at(("grouped", "binary_tt", 16, 4), 15) == "binary_tt"
     assert bench.tree_at(("grouped", "binary_tt", 16, 4), 16) == "grouped"
+
+
+SMEM_RECORD_CHECK = r"""
+#include <cassert>
+#include <cstdio>
+#include <thread>
+#include <vector>
+#include "smem_record.h"
+int main() {
+  luqr::SmemRecord rec;
+  int calls = 0;
+  auto ok = [&](size_t) { ++calls; return true; };
+  auto bad = [&](size_t) { ++calls; return false; };
+  assert(rec.ensure(0, 40 * 1024, ok) && calls == 0);        // below the default
+  assert(rec.ensure(0, 100 * 1024, ok) && calls == 1);       // raised on device 0
+  assert(rec.ensure(0, 100 * 1024, ok) && calls == 1);       // recorded
+  assert(rec.ensure(0, 64 * 1024, ok) && calls == 1);        // below the record
+  assert(rec.ensure(1, 100 * 1024, ok) && calls == 2);       // device 1 has its own record
+  assert(!rec.ensure(2, 200 * 1024, bad) && calls == 3);     // a failed raise is not recorded
+  assert(rec.ensure(2, 200 * 1024, ok) && calls == 4);
+  assert(rec.ensure(99, 100 * 1024, ok) && calls == 5);      // beyond the table: every time
+  assert(rec.ensure(99, 100 * 1024, ok) && calls == 6);
+  assert(rec.ensure(-1, 40 * 1024, ok) && calls == 6);
+  // many host threads on one device: the attribute is set once
+  luqr::SmemRecord r2;
+  int n = 0;
+  std::vector<std::thread> th;
+  for (int t = 0; t < 16; ++t)
+    th.emplace_back([&] { for (int i = 0; i < 1000; ++i) r2.ensure(3, 120 * 1024, [&](size_t) { ++n; return true; }); });
+  for (auto& x : th) x.join();
+  assert(n == 1);
+  std::puts("ok");
+  return 0;
+}
+"""
+
+
+def test_dynamic_smem_record_is_per_device(tmp_path):
+    """The record behind ensure_dyn_smem (csrc/smem_record.h) keeps one limit per device,
+    records only successful raises, and sets the attribute once under concurrent callers."""
+    import shutil
+    import subprocess
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not found")
+    src = tmp_path / "check.cpp"
+    src.write_text(SMEM_RECORD_CHECK)
+    exe = tmp_path / "check"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                       "paper_1401_5522_gb300", "csrc")
+    subprocess.run([gxx, "-std=c++17", "-O1", "-pthread", "-I", inc, str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True)
+    assert out.stdout.strip() == "ok"
