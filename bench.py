@@ -455,7 +455,7 @@ def train_decision_mlp(args):
     from paper_1401_5522_gb300 import speculation as S
     N0, nb0 = 4096, 256
     runs = []
-    for seed in range(12):
+    for seed in range(48):   # 768 logged steps
         A0 = inputs.gaussian(N0, 500 + seed, device="cuda")
         A0 = inputs.scale_diag_tiles(A0, nb0, inputs.choose_panels(N0 // nb0, 0.2, seed), 1e-8)
         runs.append(dict(A=A0, nb=nb0, criterion="max", alpha=(1e4, 3e4, 1e5)[seed % 3],
