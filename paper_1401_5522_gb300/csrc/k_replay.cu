@@ -119,11 +119,23 @@ __device__ void rp_qr_vec(const T* __restrict__ V, int64_t ldv, const T* __restr
     const T* vs = Vb + (size_t)b * IB * nb;
     const T* ts = Tb + b * IB * IB;
     const int r0 = lo(jb), r1 = hi(jb);
-    for (int j = warp; j < IB; j += nw) {
-      T acc = (T)0;
-      for (int r = r0 + lane; r < r1; r += 32) acc += vval(vs, jb, r, j) * xs[r];
-      acc = warp_sum<T>(acc);
-      if (lane == 0) w[j] = pair ? acc + xe[jb + j] : acc;
+    // w = V_b^T x (+ x_e): each warp takes its IB / nw columns together (independent
+    // accumulators, so the loads of one row serve several columns and overlap)
+    static_assert(IB == 4 * (NT / 32), "four columns per warp");
+    {
+      T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll 2
+      for (int r = r0 + lane; r < r1; r += 32) {
+        const T xr = xs[r];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] += vval(vs, jb, r, warp + nw * c) * xr;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const T sum = warp_sum<T>(acc[c]);
+        const int j = warp + nw * c;
+        if (lane == 0) w[j] = pair ? sum + xe[jb + j] : sum;
+      }
     }
     __syncthreads();
     // w2 = T_b^T w: column c of T_b (T(a, c) at ts[c * IB + a], a <= c) is read by the lanes
@@ -134,11 +146,11 @@ __device__ void rp_qr_vec(const T* __restrict__ V, int64_t ldv, const T* __restr
       if (lane == 0) w2[c] = acc;
     }
     __syncthreads();
-    for (int r = r0 + tid; r < r1; r += NT) {
-      T acc = (T)0;
-#pragma unroll 8
-      for (int j = 0; j < IB; ++j) acc += vval(vs, jb, r, j) * w2[j];
-      xs[r] -= acc;
+    for (int r = r0 + tid; r < r1; r += NT) {   // x -= V_b w2, four partial sums per row
+      T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll
+      for (int j = 0; j < IB; ++j) acc[j & 3] += vval(vs, jb, r, j) * w2[j];
+      xs[r] -= (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
     if (pair && tid < IB) xe[jb + tid] -= w2[tid];
     __syncthreads();
@@ -173,11 +185,11 @@ __device__ void rp_lu_apply(const T* __restrict__ L, int64_t ldl, const int* __r
       xs[b0 + lane] = x;
     }
     __syncthreads();
-    for (int r = b0 + 32 + tid; r < nb; r += NT) {
-      T acc = (T)0;
-#pragma unroll 8
-      for (int c = 0; c < 32; ++c) acc += L[r + (int64_t)(b0 + c) * ldl] * xs[b0 + c];
-      xs[r] -= acc;
+    for (int r = b0 + 32 + tid; r < nb; r += NT) {   // four partial sums: loads overlap
+      T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll
+      for (int c = 0; c < 32; ++c) acc[c & 3] += L[r + (int64_t)(b0 + c) * ldl] * xs[b0 + c];
+      xs[r] -= (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
     __syncthreads();
   }
@@ -211,11 +223,11 @@ __device__ int rp_trsv(const T* __restrict__ U, int64_t ldu, int nb, T* xs, int*
     }
     __syncthreads();
     if (*s_bad >= 0) return *s_bad;
-    for (int i = tid; i < b0; i += NT) {
-      T acc = (T)0;
-#pragma unroll 8
-      for (int q = 0; q < 32; ++q) acc += U[i + (int64_t)(b0 + q) * ldu] * xs[b0 + q];
-      xs[i] -= acc;
+    for (int i = tid; i < b0; i += NT) {   // four partial sums: loads overlap
+      T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll
+      for (int q = 0; q < 32; ++q) acc[q & 3] += U[i + (int64_t)(b0 + q) * ldu] * xs[b0 + q];
+      xs[i] -= (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
     __syncthreads();
   }
