@@ -140,10 +140,18 @@ __device__ void rp_qr_vec(const T* __restrict__ V, int64_t ldv, const T* __restr
     __syncthreads();
     // w2 = T_b^T w: column c of T_b (T(a, c) at ts[c * IB + a], a <= c) is read by the lanes
     // of one warp (lane = a, consecutive words), then summed across the warp
-    for (int c = warp; c < IB; c += nw) {
-      const T t = (lane <= c) ? ts[(size_t)c * IB + lane] * w[lane] : (T)0;
-      const T acc = warp_sum<T>(t);
-      if (lane == 0) w2[c] = acc;
+    {
+      T t[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = warp + nw * q;
+        t[q] = (lane <= c) ? ts[(size_t)c * IB + lane] * w[lane] : (T)0;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T acc = warp_sum<T>(t[q]);
+        if (lane == 0) w2[warp + nw * q] = acc;
+      }
     }
     __syncthreads();
     for (int r = r0 + tid; r < r1; r += NT) {   // x -= V_b w2, four partial sums per row
@@ -212,9 +220,12 @@ __device__ int rp_trsv(const T* __restrict__ U, int64_t ldu, int nb, T* xs, int*
       int bad = -1;
 #pragma unroll
       for (int r = 31; r >= 0; --r) {
+        // the diagonal and its reciprocal do not depend on x: only the multiply, the
+        // broadcast and the update are on the dependency chain
         const T d = __shfl_sync(0xffffffffu, u[r], r);
         if (d == (T)0) { bad = b0 + r; break; }
-        if (lane == r) x = x / d;
+        const T inv = (T)1 / d;
+        if (lane == r) x = x * inv;
         const T xr = __shfl_sync(0xffffffffu, x, r);
         if (lane < r) x -= u[r] * xr;
       }
