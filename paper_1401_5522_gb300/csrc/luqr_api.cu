@@ -84,6 +84,8 @@ struct luqr_handle {
   cudaStream_t la_stream = nullptr;      // look-ahead column, one tree level behind the panel
   cudaStream_t extra_stream = nullptr;   // tensor-core operand preparation of QR steps
   std::vector<cudaEvent_t> ev_lvl;       // per tile list of the current step (reused)
+  std::vector<cudaEvent_t> ev_splvl;     // the same for the speculative chain
+  std::vector<cudaEvent_t> ev_dec;       // per step: decision and speculation gates written
   std::vector<cudaEvent_t> ev_extra, ev_la;
   std::vector<cudaEvent_t> ev_stats, ev_spec, ev_getrf, ev_luspec;
   cudaEvent_t ev_end = nullptr;
@@ -327,17 +329,21 @@ void rq_build(luqr_handle* h, const uint8_t* dec = nullptr) {
 // the decision).  extras = false leaves the tensor-core operand preparation to
 // enqueue_qr_extras.
 // rec / wait (optional, one event per tile list in tree order): record after each tile
-// list's factorization, or wait before each tile list's application.
+// list's factorization, or wait before each tile list's application.  vbase / adec
+// (optional): where the application reads V (the shadow copy of a speculated panel, base
+// shifted like fbase) and the gate it runs under.
 template <typename T>
 void enqueue_qr(luqr_handle* h, int k, Mat<T> C, int64_t c0, int64_t c1, bool do_factor,
                 bool do_apply, cudaStream_t s, bool tc = false, T* fbase = nullptr,
                 const uint8_t* fdec = nullptr, bool extras = true,
-                const cudaEvent_t* rec = nullptr, const cudaEvent_t* wait = nullptr) {
+                const cudaEvent_t* rec = nullptr, const cudaEvent_t* wait = nullptr,
+                const T* vbase = nullptr, const uint8_t* adec = nullptr) {
   const int n = h->n, nb = h->nb;
   Mat<T> F{fbase ? fbase : wsT<T>(h), h->Npad};
-  Mat<const T> Fc{wsT<T>(h), h->Npad};
+  // the application reads V from vbase (default: the workspace) and runs when adec[k] = QR
+  Mat<const T> Fc{vbase ? vbase : wsT<T>(h), h->Npad};
   T* Tk = static_cast<T*>(h->Tbuf) + (size_t)k * t_step_elems(h);
-  const uint8_t* dec = h->dec;
+  const uint8_t* dec = adec ? adec : h->dec;
   const uint8_t* fd = fdec ? fdec : h->dec;
   constexpr bool is_f32 = std::is_same<T, float>::value;
   tc = tc && is_f32 && h->use_tc_qr;
@@ -500,7 +506,8 @@ void enqueue_factor(luqr_handle* h) {
       cudaStreamWaitEvent(sp, h->ev_stats[k], 0);
       launch_gated_copy<T>(W + r0 + r0 * ld, ld, shadow + r0, ld, h->Npad - r0, nb, h->spec, k,
                            DEC_QR, "k_spec_copy", sp);
-      enqueue_qr<T>(h, k, F, 0, 0, true, false, sp, true, shadow - r0 * ld, h->spec, false);
+      enqueue_qr<T>(h, k, F, 0, 0, true, false, sp, true, shadow - r0 * ld, h->spec, false,
+                    r1 < la_end ? h->ev_splvl.data() : nullptr);
       cudaEventRecord(h->ev_spec[k], sp);
     }
     T* Tkk = static_cast<T*>(h->Tbuf) + (size_t)k * t_step_elems(h) +
@@ -538,8 +545,10 @@ void enqueue_factor(luqr_handle* h) {
                   h->dec,   h->margin, h->lhs,   h->rhs,       h->status};
     da.seed = h->seed;
     launch_decide<T>(da, S, s);
-    if (spec)
+    if (spec) {
       launch_spec_resolve(k, h->dec, h->spec, h->qrfac, h->cmt, h->lufac, h->lucmt, lu_spec, s);
+      cudaEventRecord(h->ev_dec[k], s);
+    }
     if (h->lu_variant == 1) launch_a2_gate(h->dec, h->a2gate, k, s);
     if (dd > 1)   // an LU step applies the domain's exchanges to columns k.. and b first
       launch_domain_swap<T>(W, ld, k, nb, dd * nb, r0, h->Wc, dpiv_k, h->dec, s);
@@ -562,7 +571,8 @@ void enqueue_factor(luqr_handle* h) {
     // that the look-ahead stream applies level l to column k+1 while level l+1 factors.
     const bool piped = !spec && r1 < la_end;
     if (spec) {
-      enqueue_qr<T>(h, k, F, 0, 0, true, false, s, true, nullptr, h->qrfac, false);
+      enqueue_qr<T>(h, k, F, 0, 0, true, false, s, true, nullptr, h->qrfac, false,
+                    r1 < la_end ? h->ev_lvl.data() : nullptr);
       cudaStreamWaitEvent(s, h->ev_spec[k], 0);
       launch_gated_copy<T>(shadow + r0, ld, W + r0 + r0 * ld, ld, h->Npad - r0, nb, h->cmt, k,
                            DEC_QR, "k_spec_commit", s);
@@ -602,8 +612,22 @@ void enqueue_factor(luqr_handle* h) {
     cudaEventRecord(h->ev_rest[k], su);
     // ---- look-ahead: column k+1 needs step k-1's bulk update, then step k's transform
     //      (CUDA-core QR kernels: they need only the stored V and the IB x IB T blocks)
-    if (r1 < la_end) {
-      cudaStreamWaitEvent(sl, spec ? h->ev_fact[k] : h->ev_lvl[0], 0);
+    if (r1 < la_end && spec) {
+      // speculation: once the decision is known, a QR step's transformations reach column
+      // k+1 level by level behind whichever chain factors the panel (the speculative one,
+      // V still in the shadow, or the in-place one); an LU step's after its TRSM
+      cudaStreamWaitEvent(sl, h->ev_dec[k], 0);
+      if (k > 0) cudaStreamWaitEvent(sl, h->ev_rest[k - 1], 0);
+      enqueue_qr<T>(h, k, F, r1, la_end, false, true, sl, false, nullptr, nullptr, true, nullptr,
+                    h->ev_splvl.data(), shadow - r0 * ld, h->cmt);
+      enqueue_qr<T>(h, k, F, r1, la_end, false, true, sl, false, nullptr, nullptr, true, nullptr,
+                    h->ev_lvl.data(), nullptr, h->qrfac);
+      cudaStreamWaitEvent(sl, h->ev_fact[k], 0);
+      enqueue_lu_apply<T>(h, k, F, r1, la_end, sl, true);
+      cudaEventRecord(h->ev_la[k], sl);
+      cudaStreamWaitEvent(s, h->ev_la[k], 0);
+    } else if (r1 < la_end) {
+      cudaStreamWaitEvent(sl, h->ev_lvl[0], 0);
       if (k > 0) cudaStreamWaitEvent(sl, h->ev_rest[k - 1], 0);
       enqueue_lu_apply<T>(h, k, F, r1, la_end, sl, true);
       enqueue_qr<T>(h, k, F, r1, la_end, false, true, sl, false, nullptr, nullptr, true, nullptr,
@@ -715,6 +739,8 @@ void free_handle(luqr_handle* h) {
   if (h->la_stream) cudaStreamDestroy(h->la_stream);
   if (h->extra_stream) cudaStreamDestroy(h->extra_stream);
   for (cudaEvent_t e : h->ev_lvl) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_splvl) if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_dec) if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : h->ev_extra) if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : h->ev_la) if (e) cudaEventDestroy(e);
   void* ptrs[] = {h->W,      h->Tbuf,     h->S,        h->piv_s, h->piv_all, h->norms,
@@ -1017,12 +1043,17 @@ int luqr_factor(const double* dA, int64_t lda, double* db, int64_t N, int nb, in
     h->ev_spec.assign(n, nullptr);
     h->ev_getrf.assign(n, nullptr);
     h->ev_luspec.assign(n, nullptr);
+    h->ev_dec.assign(n, nullptr);
+    h->ev_splvl.assign(n + 2, nullptr);
+    for (size_t q = 0; q < h->ev_splvl.size() && e == cudaSuccess; ++q)
+      e = cudaEventCreateWithFlags(&h->ev_splvl[q], cudaEventDisableTiming);
     for (int q = 0; q < n && e == cudaSuccess; ++q) {
       e = cudaEventCreateWithFlags(&h->ev_stats[q], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_spec[q], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_getrf[q], cudaEventDisableTiming);
       if (e == cudaSuccess)
         e = cudaEventCreateWithFlags(&h->ev_luspec[q], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_dec[q], cudaEventDisableTiming);
     }
   }
   if (o.timeout_ms > 0) h->wait_cycles = (long long)o.timeout_ms * 2070000LL;  // cycles at 2.07 GHz
