@@ -127,17 +127,16 @@ void launch_panel_stats(const T* W, int64_t ldw, int k, int n, int nb, double* n
 constexpr int GP = 32;        // panel width
 constexpr int GT = 512;       // threads
 constexpr int GCH = 64;       // column chunk of the trailing update
-constexpr int GCG = 32;       // column chunk of the row gather: 2*GP moved rows x GCG <= GP*GCH
-static_assert(2 * GP * GCG <= GP * GCH, "gather buffer must fit in the U12 staging area");
 
 template <typename T>
 __global__ void __launch_bounds__(GT) k_getrf(const T* __restrict__ W, int64_t ldw, int k, int nb,
                                               T* __restrict__ S, int* __restrict__ piv,
-                                              int* status) {
+                                              int* status, int gbuf_elems) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* P = reinterpret_cast<T*>(smem_raw);          // nb x GP panel, row stride GP+1
   T* U12 = P + (size_t)nb * (GP + 1);              // GP x GCH chunk, row stride GCH
-  int* perm = reinterpret_cast<int*>(U12 + GP * GCH);   // nb
+  T* gbuf = U12 + GP * GCH;                        // gather buffer, gbuf_elems values
+  int* perm = reinterpret_cast<int*>(gbuf + gbuf_elems);   // nb
   int* moved = perm + nb;                          // <= 2*GP moved rows
   __shared__ int s_nmoved, s_zero;
   __shared__ T s_piv_val;
@@ -206,31 +205,31 @@ __global__ void __launch_bounds__(GT) k_getrf(const T* __restrict__ W, int64_t l
       const int r = idx % nr, j = idx / nr;
       S[(jb + r) + (jb + j) * nb] = P[r * PST + j];
     }
-    // ---- (b) gather the moved rows of the columns outside the panel
-    if (tid == 0) {
-      int cnt = 0;
-      for (int i = 0; i < nr && cnt < 2 * GP; ++i)
-        if (perm[i] != i) moved[cnt++] = i;
-      s_nmoved = cnt;
-    }
+    // ---- (b) gather the moved rows of the columns outside the panel (the moved rows are
+    //      listed by all threads at once, their order does not matter: a permutation)
+    if (tid == 0) s_nmoved = 0;
+    __syncthreads();
+    for (int i = tid; i < nr; i += GT)
+      if (perm[i] != i) moved[atomicAdd(&s_nmoved, 1)] = i;   // at most 2*GP rows move
     __syncthreads();
     const int nm = s_nmoved;
     const int nother = nb - GP;   // columns outside the panel
-    for (int c0 = 0; c0 < nother; c0 += GCG) {
-      const int cw = min(GCG, nother - c0);
-      T* buf = U12;   // reuse of the staging area: nm x cw <= 2*GP x GCG values
+    // as many columns per pass as the gather buffer holds (every column at nb = 256 FP32)
+    const int gcw = nm > 0 ? max(1, gbuf_elems / nm) : nother;
+    for (int c0 = 0; c0 < nother; c0 += gcw) {
+      const int cw = min(gcw, nother - c0);
       for (int idx = tid; idx < nm * cw; idx += GT) {
         const int a = idx % nm, cc = idx / nm;
         int col = c0 + cc;
         col = col < jb ? col : col + GP;
-        buf[idx] = S[(jb + perm[moved[a]]) + col * nb];
+        gbuf[idx] = S[(jb + perm[moved[a]]) + col * nb];
       }
       __syncthreads();
       for (int idx = tid; idx < nm * cw; idx += GT) {
         const int a = idx % nm, cc = idx / nm;
         int col = c0 + cc;
         col = col < jb ? col : col + GP;
-        S[(jb + moved[a]) + col * nb] = buf[idx];
+        S[(jb + moved[a]) + col * nb] = gbuf[idx];
       }
       __syncthreads();
     }
@@ -285,9 +284,21 @@ __global__ void __launch_bounds__(GT) k_getrf(const T* __restrict__ W, int64_t l
   if (tid == 0) status[ST_ZERO_ROW] = s_zero;
 }
 
+// Gather buffer of k_getrf: every moved row (at most 2*GP) of every column outside the panel
+// when that fits in a CTA's shared memory, else the largest multiple of 2*GP rows that does.
+template <typename T>
+int getrf_gbuf(int nb) {
+  const size_t base = sizeof(T) * ((size_t)nb * (GP + 1) + (size_t)GP * GCH) +
+                      sizeof(int) * (size_t)(nb + 2 * GP) + 16;
+  const size_t want = (size_t)2 * GP * (nb - GP);
+  const size_t room = base < (size_t)SMEM_MAX ? ((size_t)SMEM_MAX - base) / sizeof(T) : 0;
+  const size_t g = want < room ? want : room / (2 * GP) * (2 * GP);
+  return (int)(g > (size_t)2 * GP ? g : (size_t)2 * GP);
+}
 template <typename T>
 size_t getrf_smem(int nb) {
-  return sizeof(T) * ((size_t)nb * (GP + 1) + (size_t)GP * GCH) + sizeof(int) * (size_t)(nb + 2 * GP);
+  return sizeof(T) * ((size_t)nb * (GP + 1) + (size_t)GP * GCH + (size_t)getrf_gbuf<T>(nb)) +
+         sizeof(int) * (size_t)(nb + 2 * GP);
 }
 
 template <typename T>
@@ -296,7 +307,8 @@ void launch_getrf(const T* W, int64_t ldw, int k, int nb, T* S, int* piv_s, int*
   ensure_dyn_smem<k_getrf<T>>(getrf_smem<T>(nb));
   {
     ProfScope ps_("k_getrf", s);
-    k_getrf<T><<<1, GT, getrf_smem<T>(nb), s>>>(W, ldw, k, nb, S, piv_s, status);
+    k_getrf<T><<<1, GT, getrf_smem<T>(nb), s>>>(W, ldw, k, nb, S, piv_s, status,
+                                                 getrf_gbuf<T>(nb));
   }
 }
 
