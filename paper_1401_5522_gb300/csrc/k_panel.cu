@@ -160,14 +160,15 @@ __global__ void __launch_bounds__(GT) k_getrf(const T* __restrict__ W, int64_t l
     __syncthreads();
     for (int j = 0; j < GP; ++j) {
       if (warp == 0) {
-        double bv = -1.0;
+        // |a| compares exactly in the working precision
+        T bv = (T)-1;
         int bi = nr;
         for (int r = j + lane; r < nr; r += 32) {
-          const double v = fabs((double)P[r * PST + j]);
+          const T v = fabs(P[r * PST + j]);
           if (v > bv) { bv = v; bi = r; }
         }
         for (int o = 16; o > 0; o >>= 1) {
-          const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+          const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
           const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
           if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
         }
@@ -191,12 +192,12 @@ __global__ void __launch_bounds__(GT) k_getrf(const T* __restrict__ W, int64_t l
       __syncthreads();
       const T d = s_piv_val;
       if (d != (T)0) {
-        for (int r = j + 1 + tid; r < nr; r += GT) P[r * PST + j] = P[r * PST + j] / d;
-        __syncthreads();
-        const int mr = nr - j - 1, mc = GP - j - 1;
-        for (int idx = tid; idx < mr * mc; idx += GT) {
-          const int r = j + 1 + idx % mr, c = j + 1 + idx / mr;
-          P[r * PST + c] -= P[r * PST + j] * P[j * PST + c];
+        // one thread per row below the pivot: its multiplier, then its entries right of j
+        // (the pivot row is final after the barrier; no other thread touches this row)
+        for (int r = j + 1 + tid; r < nr; r += GT) {
+          const T l = P[r * PST + j] / d;
+          P[r * PST + j] = l;
+          for (int c = j + 1; c < GP; ++c) P[r * PST + c] -= l * P[j * PST + c];
         }
       }
       __syncthreads();
@@ -380,11 +381,18 @@ __global__ void __launch_bounds__(32 * INV_WARPS) k_invnorm(const T* __restrict_
     fetch(nb - (g + 2) * INV_CH, (g + 1) & 1);
     const T* base = colbuf + (size_t)(g & 1) * INV_CH * nb;
     if (c < nb) {
+      // reciprocals of the group's diagonal entries first, off the dependency chain
+      double dinv = 0.0;
+      if (lane < INV_CH) {
+        const int r = nb - (g + 1) * INV_CH + lane;
+        dinv = 1.0 / (double)base[(size_t)lane * nb + r];
+      }
       for (int cc = INV_CH - 1; cc >= 0; --cc) {
         const int r = nb - (g + 1) * INV_CH + cc;
         const T* col = base + (size_t)cc * nb;
+        const double inv = __shfl_sync(0xffffffffu, dinv, cc);
         __syncwarp();
-        if (lane == 0) ys[r] = ys[r] / (double)col[r];
+        if (lane == 0) ys[r] = ys[r] * inv;
         __syncwarp();
         const double xr = ys[r];
         if (xr != 0.0)
