@@ -28,7 +28,7 @@ TREE_NAMES = ("flat_ts", "binary_tt", "grouped")
 
 
 def candidates(n_tiles, trees=("binary_tt", "grouped"), small=("binary_tt", "grouped"),
-               switches=None, groups=(4, 8)):
+               switches=None, groups=(2, 4, 8)):
     """Candidate policies (tree, tree_small, tree_switch, group) for a matrix of n_tiles tile
     rows: every big tree alone, and every (big, small) pair with the switch at 1/8, 1/4, 1/2
     and 3/4 of the tile count (at least 2 tiles); the grouped tree with groups of each size
@@ -39,7 +39,7 @@ def candidates(n_tiles, trees=("binary_tt", "grouped"), small=("binary_tt", "gro
     for t, s, w in [(t, "binary_tt", 0) for t in trees] + \
             [(t, s, int(w)) for t, s, w in itertools.product(trees, small, switches) if s != t]:
         uses_group = "grouped" in (t, s if w else t)
-        for g in (groups if uses_group else groups[:1]):
+        for g in (groups if uses_group else (4,)):   # the group size is unused there
             out.append((t, s, w, g))
     return out
 
