@@ -67,7 +67,10 @@ __device__ __forceinline__ float vstk(const float* Vtop, const float* Vbot, bool
   return (unit_top && k > j) ? Vtop[k * VST + j] : 0.0f;
 }
 
-template <int SW>
+// XV: V is stored explicitly and contiguously, [Vtop; Vbot] = Vtop[0 .. IB + nbot) with its
+// unit diagonal and the zeros above it written out (Vbot == Vtop + IB * VST), so its entries
+// are plain loads instead of the stacked-operand selection.
+template <int SW, bool XV = false>
 __device__ void apply_block_mma(const float* Vtop, const float* Vbot, int nbot, const float* Ts,
                                 float* Ctop, float* Cbot, float* Ws, float* W2s, bool unit_top) {
   constexpr int CST = SW + 1;
@@ -80,6 +83,10 @@ __device__ void apply_block_mma(const float* Vtop, const float* Vbot, int nbot, 
   auto cstk = [&](int k, int c) -> float {
     return k < IB ? Ctop[k * CST + c] : Cbot[(k - IB) * CST + c];
   };
+  auto vv = [&](int k, int j) -> float {
+    if constexpr (XV) return Vtop[k * VST + j];
+    else return vstk(Vtop, Vbot, unit_top, k, j);
+  };
   // ---- W (IB x SW) = [Vtop; Vbot]^T [Ctop; Cbot]
   {
     const int m0 = (warp & 1) * 16;
@@ -89,10 +96,10 @@ __device__ void apply_block_mma(const float* Vtop, const float* Vbot, int nbot, 
     for (int q = 0; q < NPW; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
     for (int k0 = 0; k0 < K1; k0 += 8) {
       float a[4];
-      a[0] = vstk(Vtop, Vbot, unit_top, k0 + t, m0 + g);
-      a[1] = vstk(Vtop, Vbot, unit_top, k0 + t, m0 + g + 8);
-      a[2] = vstk(Vtop, Vbot, unit_top, k0 + t + 4, m0 + g);
-      a[3] = vstk(Vtop, Vbot, unit_top, k0 + t + 4, m0 + g + 8);
+      a[0] = vv(k0 + t, m0 + g);
+      a[1] = vv(k0 + t, m0 + g + 8);
+      a[2] = vv(k0 + t + 4, m0 + g);
+      a[3] = vv(k0 + t + 4, m0 + g + 8);
       uint32_t ah[4], al[4];
       split_a(a, ah, al);
 #pragma unroll
@@ -165,10 +172,8 @@ __device__ void apply_block_mma(const float* Vtop, const float* Vbot, int nbot, 
       const uint32_t* W2l = reinterpret_cast<const uint32_t*>(Ws);
 #pragma unroll
       for (int k0 = 0; k0 < IB; k0 += 8) {
-        float a[4] = {-vstk(Vtop, Vbot, unit_top, m0 + g, k0 + t),
-                      -vstk(Vtop, Vbot, unit_top, m0 + g + 8, k0 + t),
-                      -vstk(Vtop, Vbot, unit_top, m0 + g, k0 + t + 4),
-                      -vstk(Vtop, Vbot, unit_top, m0 + g + 8, k0 + t + 4)};
+        float a[4] = {-vv(m0 + g, k0 + t), -vv(m0 + g + 8, k0 + t), -vv(m0 + g, k0 + t + 4),
+                      -vv(m0 + g + 8, k0 + t + 4)};
         uint32_t ah[4], al[4];
         split_a(a, ah, al);
 #pragma unroll
@@ -195,12 +200,14 @@ __device__ void apply_block_mma(const float* Vtop, const float* Vbot, int nbot, 
 // ---------------------------------------------------------------- block application
 // [Ctop; Cbot] <- (I - V T V^T)^T [Ctop; Cbot] for V = [Vtop; Vbot].
 // Vtop is unit lower triangular (entries below its diagonal) when unit_top, else I.
-template <typename T, int SW>
+// XV (tensor-core path only): V is explicit and contiguous as apply_block_mma states; the
+// CUDA-core path reads the same matrix through unit_top.
+template <typename T, int SW, bool XV = false>
 __device__ void apply_block(const T* Vtop, const T* Vbot, int nbot, const T* Ts, T* Ctop, T* Cbot,
                             int w, T* Ws, T* W2s, bool unit_top) {
   if constexpr (std::is_same<T, float>::value && SW >= 32) {
     (void)w;
-    apply_block_mma<SW>(Vtop, Vbot, nbot, Ts, Ctop, Cbot, Ws, W2s, unit_top);
+    apply_block_mma<SW, XV>(Vtop, Vbot, nbot, Ts, Ctop, Cbot, Ws, W2s, unit_top);
     return;
   }
   constexpr int CST = Cst<SW>::v;
@@ -433,9 +440,10 @@ __device__ void panel_qr_reg(T* Rs, T* Ps, int nrows, bool tri, int jb, T* tau_s
     rc = Rs[c];
   }
   __syncthreads();
+#pragma unroll 1
   for (int j = 0; j < IB; ++j) {
     const int cur = j & 1, nxt = cur ^ 1;
-    const int l0 = lo(j), h0 = hi(j);
+    const int l0 = lo(j);
     const T* pc = part + cur * 8 * IB;
     // reflector of column j (every warp, identical arithmetic)
     T ss = (T)0, dsum = (T)0;
@@ -460,19 +468,28 @@ __device__ void panel_qr_reg(T* Rs, T* Ps, int nrows, bool tri, int jb, T* tau_s
         else if (c > j && tau != (T)0) Rs[j * VST + c] -= tau * wc;
       }
     }
-    // update of the columns right of j on this warp's rows, then the partials of j+1
+    // update of the columns right of j on this warp's rows, then the partials of j+1.
+    // Rows at or past hi(j) hold exact zeros in every column from j on (the zero padding
+    // past nrows; for TT also the rows below the triangle, which no earlier reflector
+    // reaches), so the update leaves them at zero and they add zeros to the sums: only
+    // rows above the reflector need a test, and those exist only in GEQRT with r <= j < IB,
+    // i.e. q < IB / 8.  Same bits as testing every row, for finite panels.
     const T f = tau * inv * wc;
     const bool upd = c > j && tau != (T)0;
-    const int l1 = lo(j + 1), h1 = hi(j + 1);
+    const int l1 = lo(j + 1);
     T d = (T)0, sq = (T)0;
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
       const int r = w + 8 * q;
       const T xj = __shfl_sync(0xffffffffu, x[q], j);
-      if (upd && r >= l0 && r < h0) x[q] -= f * xj;
-      if (SINGLE && r == j) {
-        if (c == j) x[q] = beta;
-        else if (upd) x[q] -= tau * wc;
+      if (SINGLE && q < IB / 8) {
+        if (upd && r >= l0) x[q] -= f * xj;
+        if (r == j) {
+          if (c == j) x[q] = beta;
+          else if (upd) x[q] -= tau * wc;
+        }
+      } else if (upd) {
+        x[q] -= f * xj;
       }
     }
     if (j + 1 < IB) {
@@ -480,11 +497,16 @@ __device__ void panel_qr_reg(T* Rs, T* Ps, int nrows, bool tri, int jb, T* tau_s
       for (int q = 0; q < RPT; ++q) {
         const int r = w + 8 * q;
         const T xj1 = __shfl_sync(0xffffffffu, x[q], j + 1);
-        if (r >= l1 && r < h1) {
+        if (SINGLE && q < IB / 8) {
+          if (r >= l1) {
+            d += xj1 * x[q];
+            sq += x[q] * x[q];
+          }
+          if (r == j + 1) topbuf[nxt * IB + c] = x[q];
+        } else {
           d += xj1 * x[q];
           sq += x[q] * x[q];
         }
-        if (SINGLE && r == j + 1) topbuf[nxt * IB + c] = x[q];
       }
       part[nxt * 8 * IB + w * IB + c] = (c != j + 1) ? d : (T)0;
       if (c == j + 1) nrm[nxt * 8 + w] = sq;
@@ -495,23 +517,20 @@ __device__ void panel_qr_reg(T* Rs, T* Ps, int nrows, bool tri, int jb, T* tau_s
     }
     __syncthreads();
   }
-  // T, one row per lane of warp 0 (reads G below the diagonal, writes on and above it)
+  // T, one row per lane of warp 0 (reads G below the diagonal, writes on and above it).
+  // Lane c runs only its own terms b = c .. j-1 of each entry, reading its row of T back
+  // from shared memory (row c on and above the diagonal: written and read by lane c
+  // alone, never one of the G entries below the diagonal that the other lanes read).
   if (w == 0) {
-    T trow[IB];
-#pragma unroll
-    for (int j = 0; j < IB; ++j) {
-      T v = (T)0;
-      if (j == c) {
-        v = tau_s[j];
-      } else if (j > c) {
-        T acc = (T)0;
-#pragma unroll
-        for (int b = 0; b < IB; ++b)
-          if (b >= c && b < j) acc += trow[b] * Ts[j * TST + b];
-        v = -tau_s[j] * acc;
-      }
-      trow[j] = v;
-      if (j >= c) Ts[c * TST + j] = v;
+    const T* trow = Ts + c * TST;
+#pragma unroll 1
+    for (int j = c; j < IB; ++j) {
+      const T* gj = Ts + j * TST;          // G[b][j] parked at Ts[j][b], b < j
+      T acc = (T)0;
+#pragma unroll 4
+      for (int b = c; b < j; ++b) acc += trow[b] * gj[b];
+      const T tj = tau_s[j];
+      Ts[c * TST + j] = (j == c) ? tj : -tj * acc;
     }
     __syncwarp();
 #pragma unroll
@@ -622,6 +641,14 @@ __global__ void __launch_bounds__(NT) k_geqrt(Mat<T> F, int k, int nb, TileList 
       const int a = idx % IB, j = idx / IB;
       Tslot[a + (size_t)(jb + j) * IB] = Ts[a * TST + j];
     }
+    if (jb + IB < nb) {
+      // R is stored: the top block becomes V's explicit unit-lower part for the updates
+      __syncthreads();
+      for (int idx = tid; idx < IB * IB; idx += NT) {
+        const int a = idx % IB, j = idx / IB;
+        if (a <= j) Ps[a * VST + j] = (a == j) ? (T)1 : (T)0;
+      }
+    }
     for (int cc = jb + IB; cc < nb; cc += SW) {
       const int w = min(SW, nb - cc);
       __syncthreads();
@@ -630,7 +657,8 @@ __global__ void __launch_bounds__(NT) k_geqrt(Mat<T> F, int k, int nb, TileList 
       });
       cp_async_wait_all();
       __syncthreads();
-      apply_block<T, SW>(Ps, Ps + IB * VST, nrows - IB, Ts, Cs, Cs + IB * CST, w, Ws, W2s, true);
+      apply_block<T, SW, true>(Ps, Ps + IB * VST, nrows - IB, Ts, Cs, Cs + IB * CST, w, Ws, W2s,
+                               true);
       walk_rc(nrows, SW, [&](int r, int c) {
         if (c < w) tile[(jb + r) + (int64_t)(cc + c) * F.ld] = Cs[r * CST + c];
       });
@@ -727,6 +755,14 @@ __global__ void __launch_bounds__(NT) k_pair_qrt(Mat<T> F, int k, int nb, TileLi
     walk_rc(rl, IB, [&](int r, int j) {
       if (!tri || r <= jb + j) A[r + (int64_t)(jb + j) * F.ld] = Ps[r * VST + j];
     });
+    if (jb + IB < nb) {
+      // R is stored: Rs becomes the identity on top of V = [I; Ps] for the updates
+      __syncthreads();
+      for (int idx = tid; idx < IB * IB; idx += NT) {
+        const int a = idx % IB, j = idx / IB;
+        Rs[a * VST + j] = (a == j) ? (T)1 : (T)0;
+      }
+    }
     for (int cc = jb + IB; cc < nb; cc += SW) {
       const int w = min(SW, nb - cc);
       __syncthreads();
@@ -739,7 +775,7 @@ __global__ void __launch_bounds__(NT) k_pair_qrt(Mat<T> F, int k, int nb, TileLi
       });
       cp_async_wait_all();
       __syncthreads();
-      apply_block<T, SW>(nullptr, Ps, rl, Ts, Ct, Cb, w, Ws, W2s, false);
+      apply_block<T, SW, true>(Rs, Ps, rl, Ts, Ct, Cb, w, Ws, W2s, false);
       for (int idx = tid; idx < IB * SW; idx += NT) {
         const int a = idx % IB, c = idx / IB;
         if (c < w) R[(jb + a) + (int64_t)(cc + c) * F.ld] = Ct[a * CST + c];
